@@ -1,0 +1,248 @@
+"""CPU oracle of the Swendsen-Wang / PCC hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The product path (``paper_0808_2109_gb300``)
+never imports it and shares no code with it.
+
+The arithmetic lives in ``sw_oracle.c`` (plain single-threaded C, one
+function per step of the method, each citing the paper's section); this module
+only builds it with gcc and marshals numpy arrays through ctypes.
+
+Pins (what ties this oracle to something other than itself) are in
+``tests/test_oracle_*.py``: Philox against triton's library routine, the
+threshold against the exact identity 1 - exp(-2/T_c) = 2 - sqrt(2), labels
+against scipy's connected components, the exact 3x3 Swendsen-Wang transition
+matrix, brute-force 4x4 enumeration, Kaufman's finite-L energy at L=64, and
+the paper's worked example of the range operator (Sec. III).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libswo.so")
+_SRC = os.path.join(_HERE, "sw_oracle.c")
+_HDR = os.path.join(_HERE, "sw_oracle.h")
+
+STREAM_INIT, STREAM_BOND, STREAM_SPIN = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Obs(ctypes.Structure):
+    """Per-sweep observables (mirrors ``swo_obs``)."""
+
+    _fields_ = [
+        ("bond_sum", ctypes.c_int64),
+        ("mag", ctypes.c_int64),
+        ("nclusters", ctypes.c_int64),
+        ("nbonds", ctypes.c_int64),
+        ("spans_x", ctypes.c_int32),
+        ("spans_y", ctypes.c_int32),
+        ("threshold", ctypes.c_uint64),
+    ]
+
+
+OBS_DTYPE = np.dtype(
+    [
+        ("bond_sum", "<i8"),
+        ("mag", "<i8"),
+        ("nclusters", "<i8"),
+        ("nbonds", "<i8"),
+        ("spans_x", "<i4"),
+        ("spans_y", "<i4"),
+        ("threshold", "<u8"),
+    ]
+)
+assert OBS_DTYPE.itemsize == ctypes.sizeof(Obs) == 48
+
+
+def build(force: bool = False) -> str:
+    """Compile ``sw_oracle.c`` into ``_build/libswo.so`` (plain gcc, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest_src = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest_src:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            L.swo_philox_batch.argtypes = [i64, P, P, P]
+            L.swo_philox_batch.restype = None
+            L.swo_threshold_T.argtypes = [dbl, dbl]
+            L.swo_threshold_T.restype = u64
+            L.swo_threshold_p.argtypes = [dbl]
+            L.swo_threshold_p.restype = u64
+            L.swo_hot_start.argtypes = [i32, u64, P]
+            L.swo_hot_start.restype = None
+            L.swo_bonds.argtypes = [i32, u64, u64, u64, P, P]
+            L.swo_bonds.restype = i64
+            L.swo_label.argtypes = [i32, P, P]
+            L.swo_label.restype = i64
+            L.swo_count_clusters_batch.argtypes = [i32, i64, P, P]
+            L.swo_count_clusters_batch.restype = None
+            L.swo_assign.argtypes = [i32, u64, u64, P, P]
+            L.swo_assign.restype = None
+            L.swo_measure.argtypes = [i32, P, P, P]
+            L.swo_measure.restype = None
+            L.swo_spans.argtypes = [i32, P, P, P]
+            L.swo_spans.restype = ctypes.c_int
+            L.swo_pcc_delta.argtypes = [u64]
+            L.swo_pcc_delta.restype = u64
+            L.swo_pcc_update.argtypes = [u64, u64, i32]
+            L.swo_pcc_update.restype = u64
+            L.swo_run.argtypes = [i32, u64, u64, i32, i32, P, P, P, P, P]
+            L.swo_run.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------------- API
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of blocks ``ctr[..., 4]`` (uint32) under ``key[..., 2]``."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(np.broadcast_to(np.asarray(key, dtype=np.uint32),
+                                               (ctr.shape[0], 2)))
+    out = np.empty_like(ctr)
+    lib().swo_philox_batch(ctr.shape[0], _ptr(ctr), _ptr(key), _ptr(out))
+    return out
+
+
+def threshold_T(J: float, T: float) -> int:
+    return int(lib().swo_threshold_T(float(J), float(T)))
+
+
+def threshold_p(p: float) -> int:
+    return int(lib().swo_threshold_p(float(p)))
+
+
+def hot_start(L: int, seed: int) -> np.ndarray:
+    spin = np.empty(L * L, dtype=np.uint8)
+    lib().swo_hot_start(L, seed, _ptr(spin))
+    return spin
+
+
+def bonds(L: int, seed: int, sweep: int, thr: int, spin: np.ndarray):
+    spin = np.ascontiguousarray(spin, dtype=np.uint8)
+    bond = np.empty(L * L, dtype=np.uint8)
+    nb = lib().swo_bonds(L, seed, sweep, thr, _ptr(spin), _ptr(bond))
+    return bond, int(nb)
+
+
+def label(L: int, bond: np.ndarray):
+    bond = np.ascontiguousarray(bond, dtype=np.uint8)
+    lab = np.empty(L * L, dtype=np.int32)
+    nc = lib().swo_label(L, _ptr(bond), _ptr(lab))
+    return lab, int(nc)
+
+
+def count_clusters_batch(L: int, bond_sets: np.ndarray) -> np.ndarray:
+    bond_sets = np.ascontiguousarray(bond_sets, dtype=np.uint8).reshape(-1, L * L)
+    counts = np.empty(bond_sets.shape[0], dtype=np.int64)
+    lib().swo_count_clusters_batch(L, bond_sets.shape[0], _ptr(bond_sets), _ptr(counts))
+    return counts
+
+
+def assign(L: int, seed: int, sweep: int, lab: np.ndarray) -> np.ndarray:
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    spin = np.empty(L * L, dtype=np.uint8)
+    lib().swo_assign(L, seed, sweep, _ptr(lab), _ptr(spin))
+    return spin
+
+
+def measure(L: int, spin: np.ndarray):
+    spin = np.ascontiguousarray(spin, dtype=np.uint8)
+    bs = np.zeros(1, dtype=np.int64)
+    m = np.zeros(1, dtype=np.int64)
+    lib().swo_measure(L, _ptr(spin), _ptr(bs), _ptr(m))
+    return int(bs[0]), int(m[0])
+
+
+def spans(L: int, lab: np.ndarray):
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    sx = np.zeros(1, dtype=np.int32)
+    sy = np.zeros(1, dtype=np.int32)
+    if lib().swo_spans(L, _ptr(lab), _ptr(sx), _ptr(sy)) != 0:
+        raise MemoryError("swo_spans")
+    return int(sx[0]), int(sy[0])
+
+
+def pcc_delta(sweep: int) -> int:
+    return int(lib().swo_pcc_delta(sweep))
+
+
+def pcc_update(thr: int, sweep: int, flag: bool) -> int:
+    return int(lib().swo_pcc_update(thr, sweep, 1 if flag else 0))
+
+
+class Chain:
+    """A lattice state advanced by the oracle: (spins, seed, sweep, threshold)."""
+
+    def __init__(self, L: int, seed: int, thr: int, pcc: bool = False,
+                 spin: np.ndarray | None = None, sweep: int = 0):
+        if L < 2:
+            raise ValueError("L must be >= 2")
+        self.L, self.seed, self.pcc = int(L), int(seed), bool(pcc)
+        self.thr = np.array([thr], dtype=np.uint64)
+        self.sweep = int(sweep)
+        self.spin = hot_start(L, seed) if spin is None else np.array(spin, dtype=np.uint8).ravel()
+        self.label = np.arange(L * L, dtype=np.int32)
+        self.bond = np.zeros(L * L, dtype=np.uint8)
+
+    @property
+    def threshold(self) -> int:
+        return int(self.thr[0])
+
+    def run(self, nsweeps: int) -> np.ndarray:
+        obs = np.zeros(nsweeps, dtype=OBS_DTYPE)
+        if nsweeps <= 0:
+            return obs
+        rc = lib().swo_run(self.L, self.seed, self.sweep, nsweeps, 1 if self.pcc else 0,
+                           _ptr(self.thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond),
+                           _ptr(obs))
+        if rc != 0:
+            raise MemoryError("swo_run")
+        self.sweep += nsweeps
+        return obs
+
+
+def sw_chain(L: int, J: float, T: float, seed: int) -> Chain:
+    return Chain(L, seed, threshold_T(J, T))
+
+
+def sw_chain_p(L: int, p: float, seed: int) -> Chain:
+    return Chain(L, seed, threshold_p(p))
+
+
+def pcc_chain(L: int, seed: int) -> Chain:
+    return Chain(L, seed, 1 << 31, pcc=True)
+
+
+def energy_per_site(obs: np.ndarray, L: int, J: float = 1.0) -> np.ndarray:
+    """E/N = -J * bond_sum / N per sweep, in float64."""
+    return -J * obs["bond_sum"].astype(np.float64) / float(L * L)

@@ -1,0 +1,379 @@
+/*
+ * sw_oracle.c -- plain, single-threaded CPU oracle of one Swendsen-Wang sweep
+ * of the periodic 2D Ising model and of the PCC feedback built on it.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the package smoke check and
+ * the benchmark's CPU-baseline leg, never by the product path.  It shares no
+ * code with the CUDA path.
+ *
+ * Every function states what the method computes in the most direct way
+ * available; nothing here is blocked, fused or reordered for speed.
+ *
+ * Paper: S. Lin and B. Zheng, "Two Parallel Swendsen-Wang Cluster Algorithms
+ * Using Message-Passing Paradigm" (arXiv:0808.2109):
+ *   Sec. I, steps 1-4      -- the Swendsen-Wang update (bond, cluster, flip);
+ *   Sec. II.A slave step 1 -- Hoshen-Kopelman cluster counting;
+ *   Sec. II.B steps 4-6    -- the smaller label wins: root = minimum index;
+ *   Sec. III               -- extension rule, range operator under PBC;
+ *   Sec. I (PCC, cited)    -- feedback on the bond probability.
+ */
+#include "sw_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon et al., SC'11, Sec. 3: the Philox S-box is two
+ * 32x32->64 multiplications whose high halves are xored with the other two
+ * counter words and the key; the key is bumped by a Weyl sequence between
+ * rounds).
+ * ---------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c[0];
+    uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    uint32_t n3 = lo0;
+    c[0] = n0;
+    c[1] = n1;
+    c[2] = n2;
+    c[3] = n3;
+}
+
+void swo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k[0] += PHILOX_W0;
+            k[1] += PHILOX_W1;
+        }
+        philox_round(c, k);
+    }
+    out[0] = c[0];
+    out[1] = c[1];
+    out[2] = c[2];
+    out[3] = c[3];
+}
+
+void swo_philox_batch(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    for (int64_t i = 0; i < n; i++)
+        swo_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+/* One Philox block of the method's streams: counter (word, k lo, k hi, stream). */
+static void stream_block(uint64_t seed, uint64_t word, uint64_t sweep, uint32_t stream,
+                         uint32_t out[4])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)word, (uint32_t)sweep, (uint32_t)(sweep >> 32), stream};
+    swo_philox4x32_10(ctr, key, out);
+}
+
+/* Bit b (0..127) of a 128-bit block: bit (b mod 32) of word floor(b/32). */
+static int block_bit(const uint32_t w[4], uint64_t b)
+{
+    return (int)((w[b / 32] >> (b % 32)) & 1u);
+}
+
+/* ------------------------------------------------------------------------
+ * Bond probability (Sec. I step 1): P = 1 - exp(-2J/T), held as the integer
+ * threshold t = floor(P * 2^32); a link with uniform 32-bit word u is
+ * activated iff u < t.  P = 0 never bonds and P = 1 (t = 2^32) always does.
+ * ---------------------------------------------------------------------- */
+uint64_t swo_threshold_p(double p)
+{
+    if (!(p > 0.0))
+        return 0;
+    if (p >= 1.0)
+        return (uint64_t)1 << 32;
+    return (uint64_t)floor(ldexp(p, 32));
+}
+
+uint64_t swo_threshold_T(double J, double T)
+{
+    double P = 1.0 - exp(-2.0 * J / T);
+    return swo_threshold_p(P);
+}
+
+/* ------------------------------------------------------------------------
+ * Hot start: every spin an independent fair bit of the INIT stream.
+ * ---------------------------------------------------------------------- */
+void swo_hot_start(int32_t L, uint64_t seed, uint8_t *spin)
+{
+    uint64_t N = (uint64_t)L * (uint64_t)L;
+    for (uint64_t i = 0; i < N; i++) {
+        uint32_t w[4];
+        stream_block(seed, i / 128, 0, SWO_STREAM_INIT, w);
+        spin[i] = (uint8_t)block_bit(w, i % 128);
+    }
+}
+
+/* Neighbour of site i across its link d (periodic). */
+static uint64_t neighbour(int32_t L, uint64_t i, int d)
+{
+    uint64_t x = i % (uint64_t)L, y = i / (uint64_t)L;
+    if (d == 0)
+        return y * (uint64_t)L + (x + 1) % (uint64_t)L;
+    return ((y + 1) % (uint64_t)L) * (uint64_t)L + x;
+}
+
+/* ------------------------------------------------------------------------
+ * Step 1 (Sec. I; also DPM step 1 of Sec. II.B): traverse every link; a link
+ * between equal spins becomes a bond with probability P.  Link l = 2i + d
+ * draws word (l mod 4) of Philox(floor(l/4), k, BOND).
+ * ---------------------------------------------------------------------- */
+int64_t swo_bonds(int32_t L, uint64_t seed, uint64_t sweep, uint64_t thr,
+                  const uint8_t *spin, uint8_t *bond)
+{
+    uint64_t N = (uint64_t)L * (uint64_t)L;
+    int64_t nb = 0;
+    for (uint64_t i = 0; i < N; i++) {
+        uint8_t b = 0;
+        for (int d = 0; d < 2; d++) {
+            uint64_t j = neighbour(L, i, d);
+            uint64_t l = 2 * i + (uint64_t)d;
+            uint32_t w[4];
+            stream_block(seed, l / 4, sweep, SWO_STREAM_BOND, w);
+            if (spin[i] == spin[j] && (uint64_t)w[l % 4] < thr) {
+                b |= (uint8_t)(1u << d);
+                nb++;
+            }
+        }
+        bond[i] = b;
+    }
+    return nb;
+}
+
+/* ------------------------------------------------------------------------
+ * Step 2 (Sec. I): two spins are in one cluster iff a path of bonds joins
+ * them.  Hoshen-Kopelman (Sec. II.A slave step 1): a raster scan in which
+ * each site looks back at its left and upper neighbour and records label
+ * equivalences in a union-find forest; the periodic wrap links are joined
+ * after the scan.  Unions always hang the larger root under the smaller, so
+ * every root is the minimum site index of its cluster: the smaller label
+ * wins, as in the DPM label exchange (Sec. II.B steps 4-6).
+ * ---------------------------------------------------------------------- */
+static int32_t uf_find(int32_t *parent, int32_t a)
+{
+    int32_t r = a;
+    while (parent[r] != r)
+        r = parent[r];
+    while (parent[a] != r) { /* path compression: does not change any root */
+        int32_t next = parent[a];
+        parent[a] = r;
+        a = next;
+    }
+    return r;
+}
+
+static void uf_unite(int32_t *parent, int32_t a, int32_t b)
+{
+    int32_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+    if (ra < rb)
+        parent[rb] = ra;
+    else if (rb < ra)
+        parent[ra] = rb;
+}
+
+int64_t swo_label(int32_t L, const uint8_t *bond, int32_t *label)
+{
+    int64_t N = (int64_t)L * (int64_t)L;
+    for (int64_t i = 0; i < N; i++)
+        label[i] = (int32_t)i;
+    /* raster scan over the links that do not wrap */
+    for (int64_t y = 0; y < L; y++) {
+        for (int64_t x = 0; x < L; x++) {
+            int64_t i = y * L + x;
+            if (x > 0 && (bond[i - 1] & 1u))
+                uf_unite(label, (int32_t)(i - 1), (int32_t)i);
+            if (y > 0 && (bond[i - L] & 2u))
+                uf_unite(label, (int32_t)(i - L), (int32_t)i);
+        }
+    }
+    /* periodic wrap links: right edge -> column 0, bottom edge -> row 0 */
+    for (int64_t y = 0; y < L; y++) {
+        int64_t i = y * L + (L - 1);
+        if (bond[i] & 1u)
+            uf_unite(label, (int32_t)i, (int32_t)(y * L));
+    }
+    for (int64_t x = 0; x < L; x++) {
+        int64_t i = (int64_t)(L - 1) * L + x;
+        if (bond[i] & 2u)
+            uf_unite(label, (int32_t)i, (int32_t)x);
+    }
+    int64_t nclusters = 0;
+    for (int64_t i = 0; i < N; i++) {
+        label[i] = uf_find(label, (int32_t)i);
+        if (label[i] == i)
+            nclusters++;
+    }
+    return nclusters;
+}
+
+void swo_count_clusters_batch(int32_t L, int64_t nsets, const uint8_t *bonds, int64_t *counts)
+{
+    int64_t N = (int64_t)L * (int64_t)L;
+    int32_t *label = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!label) {
+        for (int64_t s = 0; s < nsets; s++)
+            counts[s] = -1;
+        return;
+    }
+    for (int64_t s = 0; s < nsets; s++)
+        counts[s] = swo_label(L, bonds + s * N, label);
+    free(label);
+}
+
+/* ------------------------------------------------------------------------
+ * Step 3 (Sec. I): every cluster gets one new random spin, shared by all of
+ * its sites; the old spin is not used.  The bit is keyed by the cluster's
+ * root r: bit (r mod 128) of Philox(floor(r/128), k, SPIN).
+ * ---------------------------------------------------------------------- */
+void swo_assign(int32_t L, uint64_t seed, uint64_t sweep, const int32_t *label, uint8_t *spin)
+{
+    uint64_t N = (uint64_t)L * (uint64_t)L;
+    for (uint64_t i = 0; i < N; i++) {
+        uint64_t r = (uint64_t)label[i];
+        uint32_t w[4];
+        stream_block(seed, r / 128, sweep, SWO_STREAM_SPIN, w);
+        spin[i] = (uint8_t)block_bit(w, r % 128);
+    }
+}
+
+/* Energy E = -J * bond_sum with bond_sum = sum over links of sigma_i sigma_j
+ * (the Hamiltonian of Sec. I), magnetisation M = sum of sigma_i. */
+void swo_measure(int32_t L, const uint8_t *spin, int64_t *bond_sum, int64_t *mag)
+{
+    uint64_t N = (uint64_t)L * (uint64_t)L;
+    int64_t bs = 0, m = 0;
+    for (uint64_t i = 0; i < N; i++) {
+        int64_t si = 2 * (int64_t)spin[i] - 1;
+        m += si;
+        for (int d = 0; d < 2; d++) {
+            int64_t sj = 2 * (int64_t)spin[neighbour(L, i, d)] - 1;
+            bs += si * sj;
+        }
+    }
+    *bond_sum = bs;
+    *mag = m;
+}
+
+/* ------------------------------------------------------------------------
+ * Extension rule under periodic boundaries (Sec. III): project every cluster
+ * onto the x axis (and the y axis); it spans x iff its projection P_x(C) is
+ * the whole range [0, L-1], i.e. iff it occupies every one of the L columns.
+ * Each cluster's number of distinct columns is counted by scanning column by
+ * column and stamping each root with the last column it was seen in.
+ * ---------------------------------------------------------------------- */
+static int32_t spans_axis(int32_t L, const int32_t *label, int32_t *stamp, int32_t *count,
+                          int columns)
+{
+    int64_t N = (int64_t)L * (int64_t)L;
+    for (int64_t i = 0; i < N; i++) {
+        stamp[i] = -1;
+        count[i] = 0;
+    }
+    int32_t spans = 0;
+    for (int32_t a = 0; a < L; a++) {         /* the line: column a (or row a) */
+        for (int32_t b = 0; b < L; b++) {     /* the sites along that line     */
+            int64_t i = columns ? (int64_t)b * L + a : (int64_t)a * L + b;
+            int32_t r = label[i];
+            if (stamp[r] != a) {
+                stamp[r] = a;
+                count[r]++;
+                if (count[r] == L)
+                    spans = 1;
+            }
+        }
+    }
+    return spans;
+}
+
+int swo_spans(int32_t L, const int32_t *label, int32_t *spans_x, int32_t *spans_y)
+{
+    int64_t N = (int64_t)L * (int64_t)L;
+    int32_t *stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t *count = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!stamp || !count) {
+        free(stamp);
+        free(count);
+        return -1;
+    }
+    *spans_x = spans_axis(L, label, stamp, count, 1);
+    *spans_y = spans_axis(L, label, stamp, count, 0);
+    free(stamp);
+    free(count);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * PCC feedback (the probability-changing cluster method the paper builds
+ * on, Sec. I and Sec. III): after sweep k lower p if the clusters of that
+ * sweep percolate, raise it otherwise.  The step is 2^-8 in p for sweeps
+ * 0..999 and halves every 1000 sweeps down to 2^-20; in threshold units
+ * delta_k = 2^(32 - min(8 + floor(k/1000), 20)).  t stays in [0, 2^32].
+ * ---------------------------------------------------------------------- */
+uint64_t swo_pcc_delta(uint64_t sweep)
+{
+    uint64_t e = 8 + sweep / 1000;
+    if (e > 20)
+        e = 20;
+    return (uint64_t)1 << (32 - e);
+}
+
+uint64_t swo_pcc_update(uint64_t thr, uint64_t sweep, int32_t flag)
+{
+    uint64_t d = swo_pcc_delta(sweep);
+    uint64_t top = (uint64_t)1 << 32;
+    if (flag)
+        return thr > d ? thr - d : 0;
+    return thr + d < top ? thr + d : top;
+}
+
+/* ------------------------------------------------------------------------
+ * Whole sweeps, step by step in the paper's order (Sec. I steps 1-4).
+ * ---------------------------------------------------------------------- */
+int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc,
+            uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
+{
+    int64_t N = (int64_t)L * (int64_t)L;
+    uint8_t *b = bond ? bond : (uint8_t *)malloc((size_t)N);
+    if (!b)
+        return -1;
+    int rc = 0;
+    for (int32_t n = 0; n < nsweeps; n++) {
+        uint64_t k = sweep0 + (uint64_t)n;
+        uint64_t t = *thr;
+        swo_obs o;
+        memset(&o, 0, sizeof(o));
+        o.threshold = t;
+        o.nbonds = swo_bonds(L, seed, k, t, spin, b);    /* step 1 */
+        o.nclusters = swo_label(L, b, label);            /* step 2 */
+        swo_assign(L, seed, k, label, spin);             /* step 3 */
+        swo_measure(L, spin, &o.bond_sum, &o.mag);
+        if (pcc) {
+            if (swo_spans(L, label, &o.spans_x, &o.spans_y) != 0) {
+                rc = -1;
+                break;
+            }
+            *thr = swo_pcc_update(t, k, o.spans_x || o.spans_y);
+        }
+        obs[n] = o;
+    }
+    if (!bond)
+        free(b);
+    return rc;
+}
