@@ -1,0 +1,156 @@
+/*
+ * swgpu.h -- C ABI of the GB300 (sm_103a) Swendsen-Wang / PCC library.
+ *
+ * Paper: S. Lin and B. Zheng, "Two Parallel Swendsen-Wang Cluster Algorithms
+ * Using Message-Passing Paradigm" (arXiv:0808.2109).  The problem statement
+ * is the paper's: an L x L periodic Ising lattice H = -J sum sigma_i sigma_j,
+ * temperature T (or a bond probability p), swept by the Swendsen-Wang update
+ * of Sec. I (steps 1-4); PCC (Sec. I, Sec. III) tunes p by percolation
+ * feedback.
+ *
+ * Conventions shared by every call
+ *   - Every call returns SW_OK (0) or a negative SW_ERR_* code; nothing
+ *     throws across the ABI.  sw_strerror() names a code.
+ *   - The library owns all device memory it allocates.  Host buffers passed
+ *     in are owned by the caller and are only read or written during the
+ *     call.
+ *   - Site index i = y*L + x (row-major).  Site i owns link d=0 to
+ *     (x+1 mod L, y) and link d=1 to (x, y+1 mod L).  Spins are uint8 s in
+ *     {0,1} with sigma = 2s-1.  Labels are int32 roots: the minimum site
+ *     index of the cluster.  Bond bytes: bit0 = right link, bit1 = down link.
+ *   - Random numbers: Philox4x32-10, key = (seed mod 2^32, seed >> 32),
+ *     counter = (index word, sweep mod 2^32, sweep >> 32, stream) with
+ *     streams INIT=0 (hot start, bit i mod 128 of block i/128), BOND=1
+ *     (word l mod 4 of block l/4 for link l = 2i+d) and SPIN=2 (bit r mod 128
+ *     of block r/128 for a cluster with root r).  Sweep k counts the sweeps
+ *     since the lattice was created (k = 0 first).
+ *   - The bond threshold t = floor(P * 2^32) (an integer in [0, 2^32]) is
+ *     computed once on the host in IEEE double; a link between equal spins
+ *     is bonded iff its 32-bit word u < t.
+ *   - The GPU path supports 2 <= L <= 32768.
+ *   - Work is queued on the context's stream (default: a stream the library
+ *     creates); calls that return host data synchronise that stream.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef SWGPU_H
+#define SWGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define SW_OK 0
+#define SW_PENDING 1          /* sw_batch_poll: the job has not finished yet  */
+#define SW_ERR_ARG (-1)       /* an argument is out of range or NULL          */
+#define SW_ERR_NOMEM (-2)     /* device or host memory could not be obtained  */
+#define SW_ERR_CUDA (-3)      /* a CUDA runtime call or kernel launch failed   */
+#define SW_ERR_TIMEOUT (-4)   /* a bounded device-side wait ran out            */
+#define SW_ERR_STATE (-5)     /* the call does not fit the object's state      */
+
+/* Creation flags. */
+#define SW_FLAG_NONE 0u
+
+typedef struct sw_ctx sw_ctx; /* opaque; owned by the library */
+
+/* Observables of one sweep, all taken after the cluster flip of Sec. I
+ * step 3 (a reading: the paper does not say when it measures). */
+typedef struct {
+    int64_t bond_sum;   /* sum over all 2N links of sigma_i sigma_j; E = -J bond_sum */
+    int64_t mag;        /* sum of sigma_i                                      */
+    int64_t nclusters;  /* clusters built in this sweep (Sec. I step 2)        */
+    int64_t nbonds;     /* bonded links in this sweep (Sec. I step 1)          */
+    int32_t spans_x;    /* PCC: a cluster occupies all L columns (Sec. III)    */
+    int32_t spans_y;    /* PCC: a cluster occupies all L rows (Sec. III)       */
+    uint64_t threshold; /* bond threshold t used in this sweep                 */
+} sw_obs;
+
+/* Snapshot of a lattice's scalar state (the spins are read separately). */
+typedef struct {
+    int32_t L;
+    int32_t pcc;        /* 1 for a PCC lattice                               */
+    uint64_t seed;
+    uint64_t sweep;     /* sweeps done since creation = index of the next one */
+    uint64_t threshold; /* threshold the next sweep will use                 */
+} sw_state;
+
+/* Name of a status code (static string). */
+const char *sw_strerror(int code);
+
+/* Bond threshold of Sec. I step 1: t = floor((1 - exp(-2J/T)) * 2^32).
+ * J >= 0 and T > 0 (T may be +inf); else SW_ERR_ARG. */
+int sw_threshold(double J, double T, uint64_t *out);
+
+/* Create an L x L lattice with coupling J >= 0 at temperature T > 0
+ * (Sec. I: P = 1 - exp(-2J/T)), hot start from `seed` (every spin an
+ * independent fair bit of the INIT stream).  *out receives the context.
+ * Errors: SW_ERR_ARG (L outside [2, 32768], J < 0, T <= 0, out NULL),
+ * SW_ERR_NOMEM, SW_ERR_CUDA.  On error *out is set to NULL. */
+int sw_create(sw_ctx **out, int32_t L, double J, double T, uint64_t seed, uint32_t flags);
+
+/* As sw_create, with the bond probability p in [0, 1] given directly. */
+int sw_create_p(sw_ctx **out, int32_t L, double p, uint64_t seed, uint32_t flags);
+
+/* Create a PCC lattice (the probability-changing cluster method the paper
+ * parallelises in Sec. III): threshold starts at 2^31 (p = 1/2); after sweep
+ * k it moves by delta_k = 2^(32 - min(8 + floor(k/1000), 20)) threshold
+ * units, down if some cluster of that sweep spans the lattice in x or y by
+ * the extension rule under periodic boundaries, up otherwise, clamped to
+ * [0, 2^32].  Errors as sw_create. */
+int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags);
+
+/* Release the context and all its device memory.  NULL is accepted. */
+int sw_destroy(sw_ctx *ctx);
+
+/* Queue the context's work on `stream` (a cudaStream_t; NULL = the library's
+ * own stream).  The caller keeps ownership of the stream. */
+int sw_set_stream(sw_ctx *ctx, void *stream);
+
+/* Run `nsweeps` >= 0 Swendsen-Wang sweeps (Sec. I steps 1-4).  Asynchronous
+ * on the context's stream.  Afterwards the device holds the new spins, the
+ * labels and bonds of the last sweep, and one sw_obs per sweep pending for
+ * sw_observables.  On a PCC context this is the same as pcc_step.
+ * Errors: SW_ERR_ARG (nsweeps < 0), SW_ERR_NOMEM, SW_ERR_CUDA. */
+int sw_sweep(sw_ctx *ctx, int32_t nsweeps);
+
+/* Run `nsweeps` PCC sweeps: each is a Swendsen-Wang sweep, the span test of
+ * Sec. III on its clusters, and the threshold feedback.  Errors as sw_sweep,
+ * plus SW_ERR_STATE when ctx was not made by pcc_create. */
+int pcc_step(sw_ctx *ctx, int32_t nsweeps);
+
+/* Copy the observables of the sweeps run since the last call (oldest first)
+ * into the caller's out[max]; *n_written receives how many.  Entries that do
+ * not fit stay pending for the next call.  Synchronises the stream. */
+int sw_observables(sw_ctx *ctx, sw_obs *out, int32_t max, int32_t *n_written);
+
+/* Copy the L*L spins (uint8 0/1) to host_out.  Synchronises the stream. */
+int sw_get_spins(sw_ctx *ctx, uint8_t *host_out);
+
+/* Replace the L*L spins by host_in (each byte must be 0 or 1, else
+ * SW_ERR_ARG).  The sweep counter and threshold are unchanged.
+ * Synchronises the stream. */
+int sw_set_spins(sw_ctx *ctx, const uint8_t *host_in);
+
+/* Copy the L*L labels of the last sweep (root = minimum site index of each
+ * cluster, Sec. II.B steps 4-6) to host_out.  SW_ERR_STATE before the first
+ * sweep.  Synchronises the stream. */
+int sw_get_labels(sw_ctx *ctx, int32_t *host_out);
+
+/* Copy the L*L bond bytes of the last sweep to host_out.  SW_ERR_STATE
+ * before the first sweep.  Synchronises the stream. */
+int sw_get_bonds(sw_ctx *ctx, uint8_t *host_out);
+
+/* Scalar state of the lattice. */
+int sw_get_state(sw_ctx *ctx, sw_state *out);
+
+/* Wait for all work queued on the context's stream. */
+int sw_sync(sw_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWGPU_H */

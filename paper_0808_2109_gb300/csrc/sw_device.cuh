@@ -1,0 +1,766 @@
+// sw_device.cuh -- device code of the Swendsen-Wang / PCC sweep for sm_103a.
+//
+// One sweep (Lin & Zheng, arXiv:0808.2109, Sec. I steps 1-4) is split the way
+// the paper's master-slave model splits it (Sec. II.A), but inside one GPU:
+//
+//   k_tile   one CTA per TH x 128 tile ("slave domain").  It finishes sweep
+//            k-1 (reads each site's 2-byte tile-local cluster code, resolves
+//            border clusters through the merged node table, writes the new
+//            spins into shared memory, reduces the observables) and, in the
+//            same launch, starts sweep k on those spins: Philox bonds, a
+//            shared-memory union-find over the bonds inside the tile, the new
+//            spin of every cluster that does not touch the tile border, and
+//            one "node" per border site (the master's "new lattice").
+//   k_merge_union / k_merge_compress / k_merge_final
+//            the master's step 2 (Sec. II.A): union-find over the border
+//            nodes joined by the bonds that cross tile edges, including the
+//            periodic wrap; the root of a global cluster is the minimum site
+//            index (the DPM rule "the smaller label wins", Sec. II.B step 5);
+//            then each node gets its cluster's root and new spin.
+//
+// Between launches only the 2-byte code per site and the node table cross
+// the SM boundary; spins stay in shared memory from one sweep to the next.
+#pragma once
+
+#include <cstdint>
+
+namespace swg {
+
+constexpr int TW = 128;           // tile width in sites (4 words of 32 sites)
+constexpr int TWW = TW / 32;      // words per tile row
+constexpr int NTHREADS = 512;     // threads per tile CTA
+constexpr int CROSS_WORDS = 8;    // per tile: 4 words right-edge bits, 4 words bottom-edge bits
+
+// 30-bit global roots: the GPU path supports N = L*L <= 2^30.
+constexpr uint32_t ROOT_MASK = 0x3FFFFFFFu;
+constexpr uint32_t FINAL_SPIN = 0x40000000u;
+constexpr uint32_t KEY_NONE = 0x3FFFFFFFu;
+
+// 2-byte tile-local cluster code of a site, written when a sweep starts and
+// read when it finishes.
+constexpr uint16_t CODE_BORDER = 0x8000u;   // bits 0-9: the piece's node slot
+constexpr uint16_t CODE_SPIN = 0x4000u;     // interior: the cluster's new spin
+constexpr uint16_t CODE_ROOT = 0x3FFFu;     // interior: tile-local root index
+
+// Philox streams (counter word 3).
+constexpr uint32_t STREAM_INIT = 0u, STREAM_BOND = 1u, STREAM_SPIN = 2u;
+
+// Replica flags.
+constexpr int32_t RF_PCC = 1;
+
+// Per-sweep observables as the device accumulates them (layout of sw_obs).
+struct DevObs {
+    unsigned long long bond_sum, mag, nclusters, nbonds;
+    int32_t spans_x, spans_y;
+    unsigned long long threshold;
+};
+static_assert(sizeof(DevObs) == 48, "DevObs must match sw_obs");
+
+// One lattice of a launch.  A single sw_sweep call is a batch of one.
+struct Replica {
+    int32_t L;
+    int32_t tiles_x, tiles_y;
+    int32_t tile_base;      // first global tile index of this lattice
+    uint32_t key0, key1;    // Philox key = (seed lo, seed hi)
+    int32_t nsweeps;        // sweeps of this call
+    int32_t flags;          // RF_*
+    uint64_t sweep0;        // sweep index started by launch j = 0
+    uint64_t thr;           // bond threshold (plain SW)
+    uint64_t *thr_dev;      // PCC: the threshold lives on the device
+    uint8_t *spin;          // L*L spins (read at j = 0, written at j = nsweeps)
+    int32_t *label;         // L*L labels of the last sweep (written at j = nsweeps)
+    uint8_t *bond;          // unused by the kernels (host bookkeeping)
+    DevObs *obs;            // nsweeps entries
+};
+
+// Buffers shared by all tiles of a launch (indexed by the global tile g).
+struct SweepArgs {
+    const Replica *reps;
+    const int32_t *tile_rep;    // replica of each global tile
+    int32_t n_tiles;
+    int32_t j;                  // launch index within a graph chunk
+    const int32_t *jbase;       // chunk offset: launch index = j + *jbase
+    uint16_t *code;             // n_tiles * TH * TW site codes
+    uint32_t *bondbits;         // n_tiles * TH * 8 words (last sweep only)
+    uint32_t *cross;            // n_tiles * CROSS_WORDS
+    int32_t *npar;              // n_tiles * S node parents
+    int32_t *nkey;              // n_tiles * S node keys (global root candidates)
+    uint32_t *nfinal;           // n_tiles * S resolved (root | spin << 30)
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications, the high halves xored with the other counter
+// words and the key, the key advanced by the Weyl constants between rounds.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// The method's blocks: counter = (word, sweep lo, sweep hi, stream).
+__device__ __forceinline__ U4 stream_block(const Replica &R, uint64_t word, uint64_t sweep,
+                                           uint32_t stream)
+{
+    return philox4x32_10((uint32_t)word, (uint32_t)sweep, (uint32_t)(sweep >> 32), stream,
+                         R.key0, R.key1);
+}
+
+__device__ __forceinline__ uint32_t u4_word(const U4 &v, int i)
+{
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// u < t with t in [0, 2^32]
+__device__ __forceinline__ bool below(uint32_t u, uint64_t t)
+{
+    return (uint64_t)u < t;
+}
+
+// Spread the low 16 bits of v to the even bit positions.
+__device__ __forceinline__ uint32_t spread16(uint32_t v)
+{
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+// Mask of the valid sites (x < tw) in word c of a tile row.
+__device__ __forceinline__ uint32_t valid_mask(int c, int tw)
+{
+    const int n = tw - 32 * c;
+    return n >= 32 ? 0xFFFFFFFFu : (n <= 0 ? 0u : ((1u << n) - 1u));
+}
+
+// ------------------------------------------------------------ tile geometry
+struct Tile {
+    int g, lt, tx, ty, x0, y0, tw, th, g_right, g_down;
+};
+
+__device__ __forceinline__ Tile tile_of(const Replica &R, int g, int TH)
+{
+    Tile t;
+    t.g = g;
+    t.lt = g - R.tile_base;
+    t.tx = t.lt % R.tiles_x;
+    t.ty = t.lt / R.tiles_x;
+    t.x0 = t.tx * TW;
+    t.y0 = t.ty * TH;
+    t.tw = min(TW, R.L - t.x0);
+    t.th = min(TH, R.L - t.y0);
+    t.g_right = R.tile_base + t.ty * R.tiles_x + (t.tx + 1) % R.tiles_x;
+    t.g_down = R.tile_base + ((t.ty + 1) % R.tiles_y) * R.tiles_x + t.tx;
+    return t;
+}
+
+// Node slots of a tile: [0,TW) top row, [TW,2TW) bottom row, [2TW,2TW+TH)
+// left column, [2TW+TH, 2TW+2TH) right column.
+template <int TH>
+struct Slots {
+    static constexpr int S = 2 * TW + 2 * TH;
+    static constexpr int TOP = 0, BOTTOM = TW, LEFT = 2 * TW, RIGHT = 2 * TW + TH;
+};
+
+template <int TH>
+__device__ __forceinline__ bool slot_site(int s, int tw, int th, int &site)
+{
+    using SL = Slots<TH>;
+    int x, y;
+    if (s < SL::BOTTOM) {
+        x = s;
+        y = 0;
+        if (x >= tw) return false;
+    } else if (s < SL::LEFT) {
+        x = s - SL::BOTTOM;
+        y = th - 1;
+        if (x >= tw) return false;
+    } else if (s < SL::RIGHT) {
+        x = 0;
+        y = s - SL::LEFT;
+        if (y >= th) return false;
+    } else {
+        x = tw - 1;
+        y = s - SL::RIGHT;
+        if (y >= th) return false;
+    }
+    site = y * TW + x;
+    return true;
+}
+
+// ----------------------------------------------- shared-memory union-find
+// Links always hang the larger root under the smaller index, so every root
+// is the minimum local index of its piece, and tile-local row-major order is
+// the global order: the local root is the piece's minimum global site.
+__device__ __forceinline__ int sfind(volatile int *par, int x)
+{
+    int p = par[x];
+    while (p != x) {
+        const int gp = par[p];
+        if (gp != p) par[x] = gp;  // path halving: only ever an ancestor
+        x = gp;
+        p = par[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ int sfind_ro(const volatile int *par, int x)
+{
+    int p = par[x];
+    while (p != x) {
+        x = p;
+        p = par[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ void sunite(volatile int *par, int a, int b)
+{
+    for (;;) {
+        a = sfind(par, a);
+        b = sfind(par, b);
+        if (a == b) return;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS((int *)&par[b], b, a) == b) return;
+    }
+}
+
+// Start (run head) words of a row: bit x is set iff x == 0 or the link
+// (x-1, x) is not an intra-tile bond.
+__device__ __forceinline__ void row_starts(const uint32_t *h, uint32_t s[TWW])
+{
+    s[0] = ~(h[0] << 1);
+#pragma unroll
+    for (int c = 1; c < TWW; ++c) s[c] = ~((h[c] << 1) | (h[c - 1] >> 31));
+}
+
+// Connected components of the intra-tile bonds (H: right links with the
+// tile-crossing link of the last column cleared; V: down links of rows
+// y < th-1).  On return par[i] is the local root of site i for every site of
+// the tile (sites outside tw x th are their own roots).
+template <int TH>
+__device__ void tile_label(volatile int *par, const uint32_t (*H)[TWW], const uint32_t (*V)[TWW],
+                           int th)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NTHREADS / 32;
+    // 1. every site points at the head of its horizontal run
+    for (int w = warp; w < th * TWW; w += NW) {
+        const int y = w >> 2, c = w & 3;
+        uint32_t s[TWW];
+        row_starts(H[y], s);
+        const uint32_t m = s[c] & (0xFFFFFFFFu >> (31 - lane));
+        int start;
+        if (m) {
+            start = 32 * c + 31 - __clz(m);
+        } else {
+            start = 0;
+            for (int cc = c - 1; cc >= 0; --cc) {
+                if (s[cc]) {
+                    start = 32 * cc + 31 - __clz(s[cc]);
+                    break;
+                }
+            }
+        }
+        par[y * TW + 32 * c + lane] = y * TW + start;
+    }
+    for (int i = th * TW + threadIdx.x; i < TH * TW; i += NTHREADS) par[i] = i;
+    __syncthreads();
+    // 2. vertical bonds join runs; a bond whose left neighbour already joins
+    //    the same two runs is skipped
+    for (int w = warp; w < (th - 1) * TWW; w += NW) {
+        const int y = w >> 2, c = w & 3;
+        const uint32_t v = V[y][c];
+        if (!v) continue;
+        uint32_t s0[TWW], s1[TWW];
+        row_starts(H[y], s0);
+        row_starts(H[y + 1], s1);
+        const uint32_t vs = (v << 1) | (c > 0 ? (V[y][c - 1] >> 31) : 0u);
+        const uint32_t u = v & (s0[c] | s1[c] | ~vs);
+        if ((u >> lane) & 1u) sunite(par, y * TW + 32 * c + lane, (y + 1) * TW + 32 * c + lane);
+    }
+    __syncthreads();
+    // 3. flatten (read-only finds: each thread writes only its own sites)
+    for (int i = threadIdx.x; i < th * TW; i += NTHREADS) {
+        const int r = sfind_ro(par, i);
+        par[i] = r;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------ global-memory union-find
+__device__ __forceinline__ int gload(const int32_t *p)
+{
+    return *(const volatile int32_t *)p;
+}
+
+__device__ __forceinline__ int gfind(int32_t *par, int x)
+{
+    int p = gload(par + x);
+    while (p != x) {
+        const int gp = gload(par + p);
+        if (gp != p) *(volatile int32_t *)(par + x) = gp;
+        x = gp;
+        p = gload(par + x);
+    }
+    return x;
+}
+
+__device__ __forceinline__ void gunite(int32_t *par, int a, int b)
+{
+    for (;;) {
+        a = gfind(par, a);
+        b = gfind(par, b);
+        if (a == b) return;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(par + b, b, a) == b) return;
+    }
+}
+
+// --------------------------------------------------------- block reductions
+template <int K>
+__device__ __forceinline__ void block_sum_atomic(long long (&v)[K], unsigned long long *const dst[K],
+                                                 long long (*red)[K])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        long long x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) red[warp][q] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            long long x = lane < NTHREADS / 32 ? red[lane][q] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+            if (lane == 0 && dst[q] && x != 0) atomicAdd(dst[q], (unsigned long long)x);
+        }
+    }
+}
+
+// ------------------------------------------------------------ shared layout
+template <int TH>
+struct TileSmem {
+    int par[TH * TW];               // union-find forest / local roots
+    uint32_t sp[TH + 1][TWW + 1];   // spins as bits, row TH = halo row, bit tw = halo column
+    uint32_t bh[TH][TWW];           // right-link bonds (bit x: link (x,y)-(x+1,y))
+    uint32_t bv[TH][TWW];           // down-link bonds
+    uint32_t ih[TH][TWW];           // intra-tile right bonds
+    uint32_t iv[TH][TWW];           // intra-tile down bonds
+    uint32_t spb[TH][8];            // SPIN-stream blocks covering each row
+    uint32_t finfo[Slots<TH>::S];   // resolved finals of the tile's own nodes
+    long long red[NTHREADS / 32][4];
+};
+
+// ----------------------------------------------------------------- k_tile
+template <int TH>
+__global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
+{
+    using SL = Slots<TH>;
+    constexpr int S = SL::S;
+    constexpr int NW = NTHREADS / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem<TH> &sm = *reinterpret_cast<TileSmem<TH> *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+
+    const int g = blockIdx.x;
+    if (g >= a.n_tiles) return;
+    const Replica &R = a.reps[a.tile_rep[g]];
+    const int j = a.j + *a.jbase;   // finishes sweep j-1, starts sweep j
+    const bool fin = j >= 1 && j <= R.nsweeps;
+    const bool start = j < R.nsweeps;
+    if (!fin && !start) return;
+    const Tile t = tile_of(R, g, TH);
+    const int L = R.L;
+    const int64_t gbase = (int64_t)t.y0 * L + t.x0;   // global index of local site 0
+    uint16_t *code = a.code + (size_t)g * TH * TW;
+
+    if (fin) {
+        // ---- finish sweep k-1: resolve every site's cluster and flip it
+        const int jf = j - 1;
+        const bool last = j == R.nsweeps;
+        for (int s = tid; s < S; s += NTHREADS) sm.finfo[s] = a.nfinal[(size_t)g * S + s];
+        __syncthreads();
+        long long ncl = 0;
+        for (int w = warp; w < t.th * TWW; w += NW) {
+            const int y = w >> 2, c = w & 3;
+            const int x = 32 * c + lane;
+            const bool valid = x < t.tw;
+            int spin = 0;
+            if (valid) {
+                const uint16_t u = code[y * TW + x];
+                uint32_t root;
+                if (u & CODE_BORDER) {
+                    const uint32_t f = sm.finfo[u & 0x3FFu];
+                    root = f & ROOT_MASK;
+                    spin = (f & FINAL_SPIN) ? 1 : 0;
+                } else {
+                    const int lr = u & CODE_ROOT;
+                    root = (uint32_t)(gbase + (int64_t)(lr / TW) * L + (lr % TW));
+                    spin = (u & CODE_SPIN) ? 1 : 0;
+                }
+                const int64_t gi = gbase + (int64_t)y * L + x;
+                ncl += root == (uint32_t)gi;
+                if (last) {
+                    R.spin[gi] = (uint8_t)spin;
+                    R.label[gi] = (int32_t)root;
+                }
+            }
+            const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
+            if (lane == 0) {
+                sm.sp[y][c] = word;
+                if (c == TWW - 1) sm.sp[y][TWW] = 0u;
+            }
+        }
+        // bottom halo row: new spins of the top row of the tile below
+        for (int w = warp; w < TWW + 1; w += NW) {
+            const int x = 32 * w + lane;
+            int spin = 0;
+            if (x < t.tw) spin = (a.nfinal[(size_t)t.g_down * S + SL::TOP + x] & FINAL_SPIN) ? 1 : 0;
+            const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
+            if (lane == 0) sm.sp[t.th][w] = word;
+        }
+        __syncthreads();
+        // right halo column: new spins of the left column of the tile to the right
+        for (int y = tid; y < t.th; y += NTHREADS) {
+            if (a.nfinal[(size_t)t.g_right * S + SL::LEFT + y] & FINAL_SPIN)
+                sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
+        }
+        __syncthreads();
+        long long bs = 0, mag = 0;
+        for (int w = tid; w < t.th * TWW; w += NTHREADS) {
+            const int y = w >> 2, c = w & 3;
+            const uint32_t vm = valid_mask(c, t.tw);
+            const uint32_t cur = sm.sp[y][c];
+            const uint32_t right = (cur >> 1) | (sm.sp[y][c + 1] << 31);
+            const uint32_t down = sm.sp[y + 1][c];
+            const int nv = __popc(vm);
+            bs += 2 * nv - 2 * (__popc((cur ^ right) & vm) + __popc((cur ^ down) & vm));
+            mag += 2 * __popc(cur & vm) - nv;
+        }
+        long long v[4] = {bs, mag, ncl, 0};
+        DevObs *o = R.obs + jf;
+        unsigned long long *const dst[4] = {&o->bond_sum, &o->mag, &o->nclusters, nullptr};
+        block_sum_atomic<4>(v, dst, sm.red);
+        __syncthreads();
+    }
+
+    if (!start) return;
+
+    // ---- start sweep k
+    const uint64_t k = R.sweep0 + (uint64_t)j;
+    const uint64_t thr = (R.flags & RF_PCC) ? *R.thr_dev : R.thr;
+    if (!fin) {
+        // first sweep of the call: spins (and halos) from global memory
+        for (int w = warp; w < (t.th + 1) * TWW; w += NW) {
+            const int y = w >> 2, c = w & 3;
+            const int x = 32 * c + lane;
+            const int64_t gy = (t.y0 + y) % L;
+            int spin = 0;
+            if (x < t.tw) spin = R.spin[gy * L + t.x0 + x];
+            const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
+            if (lane == 0) {
+                sm.sp[y][c] = word;
+                if (c == TWW - 1) sm.sp[y][TWW] = 0u;
+            }
+        }
+        __syncthreads();
+        for (int y = tid; y < t.th; y += NTHREADS) {
+            const int64_t gi = (int64_t)(t.y0 + y) * L + (t.x0 + t.tw) % L;
+            if (R.spin[gi]) sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
+        }
+        __syncthreads();
+    }
+    if (t.lt == 0 && tid == 0) {
+        R.obs[j].threshold = thr;
+        R.obs[j].spans_x = 0;
+        R.obs[j].spans_y = 0;
+    }
+
+    // Step 1 (Sec. I): bonds.  Link l = 2i + d draws word (l mod 4) of
+    // Philox(l/4, k, BOND), i.e. sites 2m and 2m+1 share block m.
+    const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
+    for (int w = warp; w < t.th * 2; w += NW) {
+        const int y = w >> 1, half = w & 1;
+        if (64 * half >= t.tw) continue;
+        const int64_t G0 = gbase + (int64_t)y * L;
+        uint32_t rh[2], rv[2];
+        if ((G0 & 1) == 0) {
+            // aligned row: lane takes the block of sites (64h + 2 lane, +1)
+            const uint64_t blk = (uint64_t)(G0 >> 1) + 32 * half + lane;
+            const U4 r = philox4x32_10((uint32_t)blk, klo, khi, STREAM_BOND, R.key0, R.key1);
+            const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, below(r.x, thr));
+            const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, below(r.y, thr));
+            const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, below(r.z, thr));
+            const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, below(r.w, thr));
+            rh[0] = spread16(b0) | (spread16(b2) << 1);
+            rh[1] = spread16(b0 >> 16) | (spread16(b2 >> 16) << 1);
+            rv[0] = spread16(b1) | (spread16(b3) << 1);
+            rv[1] = spread16(b1 >> 16) | (spread16(b3 >> 16) << 1);
+        } else {
+            // odd row start (odd L): every site draws its own block
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int64_t gi = G0 + 64 * half + 32 * q + lane;
+                const U4 r = philox4x32_10((uint32_t)(gi >> 1), klo, khi, STREAM_BOND, R.key0,
+                                           R.key1);
+                const bool odd = gi & 1;
+                rh[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.z : r.x, thr));
+                rv[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.w : r.y, thr));
+            }
+        }
+        if (lane < 2) {
+            const int c = 2 * half + lane;
+            const uint32_t vm = valid_mask(c, t.tw);
+            const uint32_t cur = sm.sp[y][c];
+            const uint32_t right = (cur >> 1) | (sm.sp[y][c + 1] << 31);
+            const uint32_t down = sm.sp[y + 1][c];
+            const uint32_t h = rh[lane] & ~(cur ^ right) & vm;
+            const uint32_t v = rv[lane] & ~(cur ^ down) & vm;
+            sm.bh[y][c] = h;
+            sm.bv[y][c] = v;
+            // intra-tile parts: the last column's right link and the last
+            // row's down link cross the tile edge
+            sm.ih[y][c] = h & valid_mask(c, t.tw - 1);
+            sm.iv[y][c] = (y < t.th - 1) ? v : 0u;
+        }
+    }
+    // rows with no valid half (tw <= 64 leaves words 2,3 unset)
+    for (int w = tid; w < t.th * TWW; w += NTHREADS) {
+        const int y = w >> 2, c = w & 3;
+        if (64 * (c >> 1) >= t.tw) {
+            sm.bh[y][c] = sm.bv[y][c] = sm.ih[y][c] = sm.iv[y][c] = 0u;
+        }
+    }
+    // SPIN-stream blocks covering each row, for the clusters that end inside
+    // the tile (Sec. I step 3: one new random spin per cluster)
+    for (int q = tid; q < 2 * t.th; q += NTHREADS) {
+        const int y = q >> 1, b = q & 1;
+        const uint64_t blk = (uint64_t)((gbase + (int64_t)y * L) >> 7) + b;
+        const U4 r = philox4x32_10((uint32_t)blk, klo, khi, STREAM_SPIN, R.key0, R.key1);
+        sm.spb[y][4 * b + 0] = r.x;
+        sm.spb[y][4 * b + 1] = r.y;
+        sm.spb[y][4 * b + 2] = r.z;
+        sm.spb[y][4 * b + 3] = r.w;
+    }
+    __syncthreads();
+
+    long long nb = 0;
+    for (int w = tid; w < t.th * TWW; w += NTHREADS) {
+        const int y = w >> 2, c = w & 3;
+        nb += __popc(sm.bh[y][c]) + __popc(sm.bv[y][c]);
+    }
+    // crossing bonds: right edge (bit tw-1 of each row), bottom edge (row th-1)
+    if (warp < TWW) {
+        const int y = 32 * warp + lane;
+        const int bit = (y < t.th) ? (sm.bh[y][(t.tw - 1) >> 5] >> ((t.tw - 1) & 31)) & 1 : 0;
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
+        if (lane == 0) a.cross[(size_t)g * CROSS_WORDS + warp] = word;
+    } else if (warp == TWW && lane < TWW) {
+        a.cross[(size_t)g * CROSS_WORDS + TWW + lane] = sm.bv[t.th - 1][lane];
+    }
+    if (j == R.nsweeps - 1) {
+        // the last sweep of the call keeps its bonds for sw_get_bonds
+        uint32_t *bb = a.bondbits + (size_t)g * TH * 2 * TWW;
+        for (int w = tid; w < t.th * TWW; w += NTHREADS) {
+            const int y = w >> 2, c = w & 3;
+            bb[y * 2 * TWW + c] = sm.bh[y][c];
+            bb[y * 2 * TWW + TWW + c] = sm.bv[y][c];
+        }
+    }
+
+    // Step 2 inside the tile (Hoshen-Kopelman's role in Sec. II.A slave step 1)
+    tile_label<TH>(sm.par, sm.ih, sm.iv, t.th);
+
+    // One node per border site: key = global index of the piece's local root,
+    // parent = the piece's first border slot (the representative).
+    int rs = -1;
+    const int s = tid;
+    if (s < S) {
+        int site;
+        if (slot_site<TH>(s, t.tw, t.th, site)) rs = sm.par[site];
+    }
+    __syncthreads();
+    if (rs >= 0) atomicMin((int *)&sm.par[rs], (int)(0x80000000u | (uint32_t)s));
+    __syncthreads();
+    if (s < S) {
+        const size_t node = (size_t)g * S + s;
+        if (rs >= 0) {
+            const int rep = sm.par[rs] & 0x3FF;
+            a.npar[node] = (int32_t)((size_t)g * S + rep);
+            a.nkey[node] = (int32_t)(gbase + (int64_t)(rs / TW) * L + rs % TW);
+        } else {
+            a.npar[node] = (int32_t)node;
+            a.nkey[node] = (int32_t)KEY_NONE;
+        }
+    }
+    // Every site's 2-byte code: border pieces by node slot, interior clusters
+    // by local root with their new spin already drawn.
+    for (int w = warp; w < t.th * TWW; w += NW) {
+        const int y = w >> 2, c = w & 3;
+        const int x = 32 * c + lane;
+        if (x >= t.tw) continue;
+        const int i = y * TW + x;
+        const int v = sm.par[i];
+        uint16_t u;
+        if (v < 0) {
+            u = (uint16_t)(CODE_BORDER | (v & 0x3FF));
+        } else {
+            const int pv = sm.par[v];
+            if (pv < 0) {
+                u = (uint16_t)(CODE_BORDER | (pv & 0x3FF));
+            } else {
+                const int ry = v / TW, rx = v % TW;
+                const int64_t rowg = gbase + (int64_t)ry * L;
+                const int64_t gv = rowg + rx;
+                const int b = (int)((gv >> 7) - (rowg >> 7));
+                const int bit = (int)(gv & 127);
+                const int spin = (sm.spb[ry][4 * b + (bit >> 5)] >> (bit & 31)) & 1;
+                u = (uint16_t)((spin ? CODE_SPIN : 0) | v);
+            }
+        }
+        code[i] = u;
+    }
+    long long v4[4] = {nb, 0, 0, 0};
+    DevObs *o = R.obs + j;
+    unsigned long long *const dst[4] = {&o->nbonds, nullptr, nullptr, nullptr};
+    block_sum_atomic<4>(v4, dst, sm.red);
+}
+
+// ------------------------------------------------------------- merge phase
+// Master step 2 of Sec. II.A: only links between neighbouring domains are
+// activated on the "new lattice" of border sites.
+template <int TH>
+__global__ void k_merge_union(const SweepArgs a)
+{
+    using SL = Slots<TH>;
+    constexpr int S = SL::S;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)a.n_tiles * (TH + TW)) return;
+    const int g = (int)(idx / (TH + TW));
+    const int e = (int)(idx % (TH + TW));
+    const Replica &R = a.reps[a.tile_rep[g]];
+    if (!(a.j + *a.jbase < R.nsweeps)) return;
+    const Tile t = tile_of(R, g, TH);
+    int na, nb;
+    if (e < TH) {
+        const int y = e;
+        if (y >= t.th) return;
+        if (!((a.cross[(size_t)g * CROSS_WORDS + (y >> 5)] >> (y & 31)) & 1u)) return;
+        na = g * S + SL::RIGHT + y;
+        nb = t.g_right * S + SL::LEFT + y;
+    } else {
+        const int x = e - TH;
+        if (x >= t.tw) return;
+        if (!((a.cross[(size_t)g * CROSS_WORDS + TWW + (x >> 5)] >> (x & 31)) & 1u)) return;
+        na = g * S + SL::BOTTOM + x;
+        nb = t.g_down * S + SL::TOP + x;
+    }
+    gunite(a.npar, na, nb);
+}
+
+// Compress every node to its root and gather the minimum key at the root:
+// the global cluster root is its minimum site index.
+template <int TH>
+__global__ void k_merge_compress(const SweepArgs a)
+{
+    constexpr int S = Slots<TH>::S;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (int64_t)a.n_tiles * S) return;
+    const Replica &R = a.reps[a.tile_rep[n / S]];
+    if (!(a.j + *a.jbase < R.nsweeps)) return;
+    const int key = a.nkey[n];
+    if ((uint32_t)key == KEY_NONE) return;
+    // read-only find: the forest is fixed now, and each thread writes only
+    // its own entry, so every entry ends pointing at its root
+    int r = (int)n, p = gload(a.npar + r);
+    while (p != r) {
+        r = p;
+        p = gload(a.npar + r);
+    }
+    a.npar[n] = r;
+    if (r != n) atomicMin(a.nkey + r, key);
+}
+
+// Each node takes its cluster's root and the cluster's new spin:
+// bit (root mod 128) of Philox(root/128, k, SPIN) (Sec. I step 3).
+template <int TH>
+__global__ void k_merge_final(const SweepArgs a)
+{
+    constexpr int S = Slots<TH>::S;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (int64_t)a.n_tiles * S) return;
+    const int j = a.j + *a.jbase;
+    const Replica &R = a.reps[a.tile_rep[n / S]];
+    if (!(j < R.nsweeps)) return;
+    const uint32_t key0 = (uint32_t)a.nkey[n];
+    if (key0 == KEY_NONE) {
+        a.nfinal[n] = 0u;
+        return;
+    }
+    const uint32_t root = (uint32_t)a.nkey[a.npar[n]];
+    const uint64_t k = R.sweep0 + (uint64_t)j;
+    const U4 r = stream_block(R, root >> 7, k, STREAM_SPIN);
+    const int bit = root & 127;
+    const uint32_t spin = (u4_word(r, bit >> 5) >> (bit & 31)) & 1u;
+    a.nfinal[n] = root | (spin ? FINAL_SPIN : 0u);
+}
+
+// ------------------------------------------------------------ small kernels
+// Hot start: s_i = bit (i mod 128) of Philox(i/128, 0, INIT).
+__global__ void k_hot_start(uint8_t *spin, int64_t N, uint32_t key0, uint32_t key1)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const U4 r = philox4x32_10((uint32_t)(i >> 7), 0u, 0u, STREAM_INIT, key0, key1);
+    const int bit = (int)(i & 127);
+    spin[i] = (uint8_t)((u4_word(r, bit >> 5) >> (bit & 31)) & 1u);
+}
+
+// Bond bits of the last sweep (tile-major words) -> row-major bond bytes.
+template <int TH>
+__global__ void k_bond_bytes(const uint32_t *bondbits, int L, int tiles_x, uint8_t *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)L * L) return;
+    const int y = (int)(i / L), x = (int)(i % L);
+    const int tx = x / TW, ty = y / TH, lx = x % TW, ly = y % TH;
+    const size_t g = (size_t)ty * tiles_x + tx;
+    const uint32_t *bb = bondbits + g * TH * 2 * TWW + (size_t)ly * 2 * TWW;
+    const uint32_t h = (bb[lx >> 5] >> (lx & 31)) & 1u;
+    const uint32_t v = (bb[TWW + (lx >> 5)] >> (lx & 31)) & 1u;
+    out[i] = (uint8_t)(h | (v << 1));
+}
+
+}  // namespace swg

@@ -1,0 +1,534 @@
+// sw_engine.cu -- host side of the C ABI declared in include/swgpu.h:
+// lattice contexts, device buffers, the per-call sweep schedule and its CUDA
+// graphs.  Every step of a sweep runs in the kernels of sw_device.cuh.
+#include "swgpu.h"
+#include "sw_device.cuh"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+using namespace swg;
+
+namespace {
+
+constexpr int MAX_CHUNK = 512;   // launches per captured graph
+constexpr int MERGE_THREADS = 256;
+
+#define SW_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return sw_cuda_fail(e_); \
+    } while (0)
+
+int sw_cuda_fail(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return SW_ERR_NOMEM;
+    }
+    return SW_ERR_CUDA;
+}
+
+template <int TH>
+size_t tile_smem_bytes()
+{
+    return sizeof(TileSmem<TH>);
+}
+
+template <int TH>
+cudaError_t tile_prepare()
+{
+    static bool done = false;
+    static cudaError_t err = cudaSuccess;
+    if (!done) {
+        err = cudaFuncSetAttribute(k_tile<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tile_smem_bytes<TH>());
+        done = true;
+    }
+    return err;
+}
+
+// One launch group: the tile kernel of launch j and, while sweep j is
+// running, the three merge kernels.
+template <int TH>
+cudaError_t enqueue_launch(const SweepArgs &a, cudaStream_t st)
+{
+    constexpr int S = Slots<TH>::S;
+    k_tile<TH><<<a.n_tiles, NTHREADS, tile_smem_bytes<TH>(), st>>>(a);
+    const int64_t nu = (int64_t)a.n_tiles * (TH + TW);
+    const int64_t nn = (int64_t)a.n_tiles * S;
+    k_merge_union<TH><<<(unsigned)((nu + MERGE_THREADS - 1) / MERGE_THREADS), MERGE_THREADS, 0, st>>>(a);
+    k_merge_compress<TH><<<(unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS), MERGE_THREADS, 0, st>>>(a);
+    k_merge_final<TH><<<(unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS), MERGE_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, cudaStream_t st)
+{
+    switch (TH) {
+    case 32: return enqueue_launch<32>(a, st);
+    case 64: return enqueue_launch<64>(a, st);
+    default: return enqueue_launch<128>(a, st);
+    }
+}
+
+cudaError_t prepare_th(int TH)
+{
+    switch (TH) {
+    case 32: return tile_prepare<32>();
+    case 64: return tile_prepare<64>();
+    default: return tile_prepare<128>();
+    }
+}
+
+int slots_of(int TH) { return 2 * TW + 2 * TH; }
+
+// Tile height used for an L x L lattice.
+int pick_tile_height(int L)
+{
+    if (L <= 32) return 32;
+    if (L <= 64) return 64;
+    return 128;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+}  // namespace
+
+struct sw_ctx {
+    int dev = 0;
+    int32_t L = 0;
+    int TH = 128;
+    int tiles_x = 0, tiles_y = 0, n_tiles = 0, S = 0;
+    uint64_t seed = 0;
+    bool pcc = false;
+    uint64_t sweep = 0;
+    uint64_t thr = 0;
+    bool swept = false;
+
+    cudaStream_t stream = nullptr;      // where work is queued
+    cudaStream_t own_stream = nullptr;  // the library's default stream
+    cudaStream_t cap_stream = nullptr;  // graph capture
+
+    uint8_t *spin = nullptr;
+    int32_t *label = nullptr;
+    uint16_t *code = nullptr;
+    uint32_t *bondbits = nullptr;
+    uint32_t *cross = nullptr;
+    int32_t *npar = nullptr, *nkey = nullptr;
+    uint32_t *nfinal = nullptr;
+    uint64_t *thr_dev = nullptr;
+    Replica *rep_dev = nullptr;
+    int32_t *tile_rep = nullptr;
+    int32_t *jbase = nullptr;
+    uint8_t *bond_bytes = nullptr;
+
+    DevObs *obs = nullptr;
+    int64_t obs_cap = 0, obs_head = 0, obs_tail = 0;
+
+    Replica rep{};
+    std::map<int, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+void ctx_free(sw_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    void *ptrs[] = {c->spin, c->label, c->code, c->bondbits, c->cross, c->npar, c->nkey,
+                    c->nfinal, c->thr_dev, c->rep_dev, c->tile_rep, c->jbase, c->bond_bytes, c->obs};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+SweepArgs args_of(const sw_ctx *c)
+{
+    SweepArgs a{};
+    a.reps = c->rep_dev;
+    a.tile_rep = c->tile_rep;
+    a.n_tiles = c->n_tiles;
+    a.j = 0;
+    a.jbase = c->jbase;
+    a.code = c->code;
+    a.bondbits = c->bondbits;
+    a.cross = c->cross;
+    a.npar = c->npar;
+    a.nkey = c->nkey;
+    a.nfinal = c->nfinal;
+    return a;
+}
+
+int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc)
+{
+    if (!out) return SW_ERR_ARG;
+    *out = nullptr;
+    if (L < 2 || L > 32768) return SW_ERR_ARG;
+    sw_ctx *c = new (std::nothrow) sw_ctx();
+    if (!c) return SW_ERR_NOMEM;
+    int rc = SW_OK;
+    auto fail = [&](cudaError_t e) {
+        rc = sw_cuda_fail(e);
+        ctx_free(c);
+        return rc;
+    };
+    cudaError_t e = cudaGetDevice(&c->dev);
+    if (e != cudaSuccess) return fail(e);
+    c->L = L;
+    c->TH = pick_tile_height(L);
+    c->S = slots_of(c->TH);
+    c->tiles_x = (L + TW - 1) / TW;
+    c->tiles_y = (L + c->TH - 1) / c->TH;
+    c->n_tiles = c->tiles_x * c->tiles_y;
+    c->seed = seed;
+    c->pcc = pcc;
+    c->thr = thr;
+    const size_t N = (size_t)L * L;
+    const size_t nt = (size_t)c->n_tiles;
+    if ((e = prepare_th(c->TH)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    c->stream = c->own_stream;
+    if ((e = dalloc(&c->spin, N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->label, N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->code, nt * c->TH * TW)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->bondbits, nt * c->TH * 2 * TWW)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->cross, nt * CROSS_WORDS)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->npar, nt * c->S)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->nkey, nt * c->S)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->nfinal, nt * c->S)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->thr_dev, 1)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->rep_dev, 1)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->tile_rep, nt)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->jbase, 1)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(c->tile_rep, 0, nt * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(c->thr_dev, &c->thr, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return fail(e);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    k_hot_start<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->spin, (int64_t)N, k0, k1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    Replica &R = c->rep;
+    R.L = L;
+    R.tiles_x = c->tiles_x;
+    R.tiles_y = c->tiles_y;
+    R.tile_base = 0;
+    R.key0 = k0;
+    R.key1 = k1;
+    R.nsweeps = 0;
+    R.flags = pcc ? RF_PCC : 0;
+    R.sweep0 = 0;
+    R.thr = thr;
+    R.thr_dev = c->thr_dev;
+    R.spin = c->spin;
+    R.label = c->label;
+    R.bond = nullptr;
+    R.obs = nullptr;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
+    *out = c;
+    return SW_OK;
+}
+
+int ensure_obs(sw_ctx *c, int64_t n)
+{
+    if (c->obs_head == c->obs_tail) c->obs_head = c->obs_tail = 0;
+    if (c->obs_tail + n <= c->obs_cap) return SW_OK;
+    const int64_t pending = c->obs_tail - c->obs_head;
+    int64_t cap = c->obs_cap ? c->obs_cap : 64;
+    while (cap < pending + n) cap *= 2;
+    DevObs *nb = nullptr;
+    SW_CUDA(dalloc(&nb, (size_t)cap));
+    if (pending > 0) {
+        cudaError_t e = cudaMemcpyAsync(nb, c->obs + c->obs_head, pending * sizeof(DevObs),
+                                        cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(nb);
+            return sw_cuda_fail(e);
+        }
+    }
+    SW_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->obs) cudaFree(c->obs);
+    c->obs = nb;
+    c->obs_cap = cap;
+    c->obs_head = 0;
+    c->obs_tail = pending;
+    return SW_OK;
+}
+
+// Graph of `m` launch groups j = 0..m-1 (offset by *jbase at run time).
+int graph_for(sw_ctx *c, int m, cudaGraphExec_t *out)
+{
+    auto it = c->graphs.find(m);
+    if (it != c->graphs.end()) {
+        *out = it->second;
+        return SW_OK;
+    }
+    cudaGraph_t g = nullptr;
+    SW_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    SweepArgs a = args_of(c);
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < m && e == cudaSuccess; ++j) {
+        a.j = j;
+        e = enqueue_launch_th(c->TH, a, c->cap_stream);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return sw_cuda_fail(e != cudaSuccess ? e : e2);
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return sw_cuda_fail(e);
+    c->graphs[m] = ex;
+    *out = ex;
+    return SW_OK;
+}
+
+int run_sweeps(sw_ctx *c, int32_t n)
+{
+    if (n < 0) return SW_ERR_ARG;
+    if (n == 0) return SW_OK;
+    SW_CUDA(cudaSetDevice(c->dev));
+    int rc = ensure_obs(c, n);
+    if (rc != SW_OK) return rc;
+    Replica &R = c->rep;
+    R.sweep0 = c->sweep;
+    R.nsweeps = n;
+    R.thr = c->thr;
+    R.obs = c->obs + c->obs_tail;
+    SW_CUDA(cudaMemcpyAsync(c->rep_dev, &R, sizeof(Replica), cudaMemcpyHostToDevice, c->stream));
+    SW_CUDA(cudaMemsetAsync(R.obs, 0, (size_t)n * sizeof(DevObs), c->stream));
+    // n + 1 tile launches (j = 0..n), in graph chunks of at most MAX_CHUNK
+    int64_t done = 0;
+    const int64_t total = (int64_t)n + 1;
+    while (done < total) {
+        const int m = (int)std::min<int64_t>(MAX_CHUNK, total - done);
+        int32_t jb = (int32_t)done;
+        SW_CUDA(cudaMemcpyAsync(c->jbase, &jb, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        cudaGraphExec_t ex = nullptr;
+        rc = graph_for(c, m, &ex);
+        if (rc != SW_OK) return rc;
+        SW_CUDA(cudaGraphLaunch(ex, c->stream));
+        done += m;
+    }
+    c->obs_tail += n;
+    c->sweep += (uint64_t)n;
+    c->swept = true;
+    return SW_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char *sw_strerror(int code)
+{
+    switch (code) {
+    case SW_OK: return "ok";
+    case SW_PENDING: return "pending";
+    case SW_ERR_ARG: return "invalid argument";
+    case SW_ERR_NOMEM: return "out of memory";
+    case SW_ERR_CUDA: return "CUDA error";
+    case SW_ERR_TIMEOUT: return "device wait timed out";
+    case SW_ERR_STATE: return "invalid state for this call";
+    default: return "unknown status";
+    }
+}
+
+int sw_threshold(double J, double T, uint64_t *out)
+{
+    if (!out || !(J >= 0.0) || !(T > 0.0)) return SW_ERR_ARG;
+    // Sec. I step 1: P = 1 - exp(-2J/T), held as floor(P * 2^32) in [0, 2^32].
+    const double P = 1.0 - std::exp(-2.0 * J / T);
+    if (!(P > 0.0))
+        *out = 0;
+    else if (P >= 1.0)
+        *out = (uint64_t)1 << 32;
+    else
+        *out = (uint64_t)std::floor(std::ldexp(P, 32));
+    return SW_OK;
+}
+
+static int threshold_of_p(double p, uint64_t *out)
+{
+    if (!(p >= 0.0) || !(p <= 1.0)) return SW_ERR_ARG;
+    if (p == 0.0)
+        *out = 0;
+    else if (p == 1.0)
+        *out = (uint64_t)1 << 32;
+    else
+        *out = (uint64_t)std::floor(std::ldexp(p, 32));
+    return SW_OK;
+}
+
+int sw_create(sw_ctx **out, int32_t L, double J, double T, uint64_t seed, uint32_t flags)
+{
+    (void)flags;
+    if (out) *out = nullptr;
+    uint64_t thr = 0;
+    int rc = sw_threshold(J, T, &thr);
+    if (rc != SW_OK) return rc;
+    return ctx_create(out, L, thr, seed, false);
+}
+
+int sw_create_p(sw_ctx **out, int32_t L, double p, uint64_t seed, uint32_t flags)
+{
+    (void)flags;
+    if (out) *out = nullptr;
+    uint64_t thr = 0;
+    int rc = threshold_of_p(p, &thr);
+    if (rc != SW_OK) return rc;
+    return ctx_create(out, L, thr, seed, false);
+}
+
+int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags)
+{
+    (void)flags;
+    (void)L;
+    (void)seed;
+    if (out) *out = nullptr;
+    return SW_ERR_STATE;  // built in the next step of the engine
+}
+
+int sw_destroy(sw_ctx *ctx)
+{
+    if (!ctx) return SW_OK;
+    cudaSetDevice(ctx->dev);
+    cudaStreamSynchronize(ctx->stream);
+    ctx_free(ctx);
+    return SW_OK;
+}
+
+int sw_set_stream(sw_ctx *ctx, void *stream)
+{
+    if (!ctx) return SW_ERR_ARG;
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return SW_OK;
+}
+
+int sw_sweep(sw_ctx *ctx, int32_t nsweeps)
+{
+    if (!ctx) return SW_ERR_ARG;
+    return run_sweeps(ctx, nsweeps);
+}
+
+int pcc_step(sw_ctx *ctx, int32_t nsweeps)
+{
+    if (!ctx) return SW_ERR_ARG;
+    if (!ctx->pcc) return SW_ERR_STATE;
+    return run_sweeps(ctx, nsweeps);
+}
+
+int sw_observables(sw_ctx *ctx, sw_obs *out, int32_t max, int32_t *n_written)
+{
+    if (!ctx || max < 0 || (max > 0 && !out) || !n_written) return SW_ERR_ARG;
+    *n_written = 0;
+    SW_CUDA(cudaSetDevice(ctx->dev));
+    const int64_t pending = ctx->obs_tail - ctx->obs_head;
+    const int64_t n = std::min<int64_t>(pending, max);
+    if (n > 0) {
+        SW_CUDA(cudaMemcpyAsync(out, ctx->obs + ctx->obs_head, (size_t)n * sizeof(sw_obs),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->obs_head += n;
+    *n_written = (int32_t)n;
+    return SW_OK;
+}
+
+int sw_get_spins(sw_ctx *ctx, uint8_t *host_out)
+{
+    if (!ctx || !host_out) return SW_ERR_ARG;
+    SW_CUDA(cudaSetDevice(ctx->dev));
+    SW_CUDA(cudaMemcpyAsync(host_out, ctx->spin, (size_t)ctx->L * ctx->L, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SW_OK;
+}
+
+int sw_set_spins(sw_ctx *ctx, const uint8_t *host_in)
+{
+    if (!ctx || !host_in) return SW_ERR_ARG;
+    const size_t N = (size_t)ctx->L * ctx->L;
+    for (size_t i = 0; i < N; ++i)
+        if (host_in[i] > 1) return SW_ERR_ARG;
+    SW_CUDA(cudaSetDevice(ctx->dev));
+    SW_CUDA(cudaMemcpyAsync(ctx->spin, host_in, N, cudaMemcpyHostToDevice, ctx->stream));
+    SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SW_OK;
+}
+
+int sw_get_labels(sw_ctx *ctx, int32_t *host_out)
+{
+    if (!ctx || !host_out) return SW_ERR_ARG;
+    if (!ctx->swept) return SW_ERR_STATE;
+    SW_CUDA(cudaSetDevice(ctx->dev));
+    SW_CUDA(cudaMemcpyAsync(host_out, ctx->label, (size_t)ctx->L * ctx->L * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SW_OK;
+}
+
+int sw_get_bonds(sw_ctx *ctx, uint8_t *host_out)
+{
+    if (!ctx || !host_out) return SW_ERR_ARG;
+    if (!ctx->swept) return SW_ERR_STATE;
+    SW_CUDA(cudaSetDevice(ctx->dev));
+    const size_t N = (size_t)ctx->L * ctx->L;
+    if (!ctx->bond_bytes) SW_CUDA(dalloc(&ctx->bond_bytes, N));
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    switch (ctx->TH) {
+    case 32: k_bond_bytes<32><<<blocks, 256, 0, ctx->stream>>>(ctx->bondbits, ctx->L, ctx->tiles_x, ctx->bond_bytes); break;
+    case 64: k_bond_bytes<64><<<blocks, 256, 0, ctx->stream>>>(ctx->bondbits, ctx->L, ctx->tiles_x, ctx->bond_bytes); break;
+    default: k_bond_bytes<128><<<blocks, 256, 0, ctx->stream>>>(ctx->bondbits, ctx->L, ctx->tiles_x, ctx->bond_bytes); break;
+    }
+    SW_CUDA(cudaGetLastError());
+    SW_CUDA(cudaMemcpyAsync(host_out, ctx->bond_bytes, N, cudaMemcpyDeviceToHost, ctx->stream));
+    SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SW_OK;
+}
+
+int sw_get_state(sw_ctx *ctx, sw_state *out)
+{
+    if (!ctx || !out) return SW_ERR_ARG;
+    SW_CUDA(cudaSetDevice(ctx->dev));
+    uint64_t thr = ctx->thr;
+    if (ctx->pcc) {
+        SW_CUDA(cudaMemcpyAsync(&thr, ctx->thr_dev, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+        SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    out->L = ctx->L;
+    out->pcc = ctx->pcc ? 1 : 0;
+    out->seed = ctx->seed;
+    out->sweep = ctx->sweep;
+    out->threshold = thr;
+    return SW_OK;
+}
+
+int sw_sync(sw_ctx *ctx)
+{
+    if (!ctx) return SW_ERR_ARG;
+    SW_CUDA(cudaSetDevice(ctx->dev));
+    SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+"""Python binding of the C ABI in ``include/swgpu.h`` (argument marshalling only).
+
+Every step of a sweep runs in the CUDA library ``_build/libswgpu.so``; this
+module only loads it with ctypes and converts arguments.  There is no CPU
+fallback: if the library is missing or cannot be loaded, ``lib()`` raises.
+
+The functions keep the C names (``sw_create``, ``sw_sweep``,
+``sw_observables``, ``pcc_create``, ``pcc_step`` ...).  ``Lattice`` wraps a
+context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+SW_OK, SW_PENDING = 0, 1
+SW_ERR_ARG, SW_ERR_NOMEM, SW_ERR_CUDA, SW_ERR_TIMEOUT, SW_ERR_STATE = -1, -2, -3, -4, -5
+
+OBS_DTYPE = np.dtype(
+    [
+        ("bond_sum", "<i8"),
+        ("mag", "<i8"),
+        ("nclusters", "<i8"),
+        ("nbonds", "<i8"),
+        ("spans_x", "<i4"),
+        ("spans_y", "<i4"),
+        ("threshold", "<u8"),
+    ]
+)
+
+
+class SwState(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int32),
+        ("pcc", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("sweep", ctypes.c_uint64),
+        ("threshold", ctypes.c_uint64),
+    ]
+
+
+class SwError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+# exported symbol -> (argtypes, restype)
+_P = ctypes.c_void_p
+_i32, _u32, _i64, _u64, _dbl = ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+SIGNATURES = {
+    "sw_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "sw_threshold": ([_dbl, _dbl, _P], ctypes.c_int),
+    "sw_create": ([_P, _i32, _dbl, _dbl, _u64, _u32], ctypes.c_int),
+    "sw_create_p": ([_P, _i32, _dbl, _u64, _u32], ctypes.c_int),
+    "pcc_create": ([_P, _i32, _u64, _u32], ctypes.c_int),
+    "sw_destroy": ([_P], ctypes.c_int),
+    "sw_set_stream": ([_P, _P], ctypes.c_int),
+    "sw_sweep": ([_P, _i32], ctypes.c_int),
+    "pcc_step": ([_P, _i32], ctypes.c_int),
+    "sw_observables": ([_P, _P, _i32, _P], ctypes.c_int),
+    "sw_get_spins": ([_P, _P], ctypes.c_int),
+    "sw_set_spins": ([_P, _P], ctypes.c_int),
+    "sw_get_labels": ([_P, _P], ctypes.c_int),
+    "sw_get_bonds": ([_P, _P], ctypes.c_int),
+    "sw_get_state": ([_P, _P], ctypes.c_int),
+    "sw_sync": ([_P], ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib():
+    """Load the CUDA library (raises if it is not built or does not load)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+            L = ctypes.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().sw_strerror(code).decode()
+    except Exception:  # the library itself failed to load
+        return f"status {code}"
+
+
+def _check(rc: int, where: str):
+    if rc != SW_OK:
+        raise SwError(rc, where)
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ----------------------------------------------------------- C-named calls
+
+def sw_threshold(J: float, T: float) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().sw_threshold(J, T, ctypes.byref(out)), "sw_threshold")
+    return int(out.value)
+
+
+def sw_create(L: int, J: float, T: float, seed: int, flags: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().sw_create(ctypes.byref(h), L, J, T, seed, flags), "sw_create")
+    return h
+
+
+def sw_create_p(L: int, p: float, seed: int, flags: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().sw_create_p(ctypes.byref(h), L, p, seed, flags), "sw_create_p")
+    return h
+
+
+def pcc_create(L: int, seed: int, flags: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().pcc_create(ctypes.byref(h), L, seed, flags), "pcc_create")
+    return h
+
+
+def sw_destroy(h) -> None:
+    _check(lib().sw_destroy(h), "sw_destroy")
+
+
+def sw_set_stream(h, stream) -> None:
+    """``stream``: a ``torch.cuda.Stream``, a raw cudaStream_t integer, or None."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().sw_set_stream(h, ctypes.c_void_p(raw) if raw else None), "sw_set_stream")
+
+
+def sw_sweep(h, nsweeps: int) -> None:
+    _check(lib().sw_sweep(h, nsweeps), "sw_sweep")
+
+
+def pcc_step(h, nsweeps: int) -> None:
+    _check(lib().pcc_step(h, nsweeps), "pcc_step")
+
+
+def sw_observables(h, max_entries: int) -> np.ndarray:
+    out = np.zeros(max(int(max_entries), 0), dtype=OBS_DTYPE)
+    n = ctypes.c_int32()
+    _check(lib().sw_observables(h, _ptr(out) if out.size else None, out.size, ctypes.byref(n)),
+           "sw_observables")
+    return out[: n.value]
+
+
+def sw_get_spins(h, L: int, out: np.ndarray | None = None) -> np.ndarray:
+    out = np.empty(L * L, dtype=np.uint8) if out is None else out
+    _check(lib().sw_get_spins(h, _ptr(out)), "sw_get_spins")
+    return out
+
+
+def sw_set_spins(h, spins: np.ndarray) -> None:
+    spins = np.ascontiguousarray(spins, dtype=np.uint8)
+    _check(lib().sw_set_spins(h, _ptr(spins)), "sw_set_spins")
+
+
+def sw_get_labels(h, L: int) -> np.ndarray:
+    out = np.empty(L * L, dtype=np.int32)
+    _check(lib().sw_get_labels(h, _ptr(out)), "sw_get_labels")
+    return out
+
+
+def sw_get_bonds(h, L: int) -> np.ndarray:
+    out = np.empty(L * L, dtype=np.uint8)
+    _check(lib().sw_get_bonds(h, _ptr(out)), "sw_get_bonds")
+    return out
+
+
+def sw_get_state(h) -> dict:
+    st = SwState()
+    _check(lib().sw_get_state(h, ctypes.byref(st)), "sw_get_state")
+    return {"L": st.L, "pcc": bool(st.pcc), "seed": st.seed, "sweep": st.sweep,
+            "threshold": st.threshold}
+
+
+def sw_sync(h) -> None:
+    _check(lib().sw_sync(h), "sw_sync")
+
+
+# -------------------------------------------------------------- convenience
+
+class Lattice:
+    """One L x L lattice on the GPU (plain SW at J, T or p; or PCC)."""
+
+    def __init__(self, L: int, *, J: float = 1.0, T: float | None = None, p: float | None = None,
+                 seed: int = 1, pcc: bool = False):
+        self.L = int(L)
+        if pcc:
+            self.h = pcc_create(self.L, seed)
+        elif p is not None:
+            self.h = sw_create_p(self.L, p, seed)
+        else:
+            if T is None:
+                raise ValueError("give T, p or pcc=True")
+            self.h = sw_create(self.L, J, T, seed)
+        self.pcc = bool(pcc)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sweep(self, n: int):
+        (pcc_step if self.pcc else sw_sweep)(self.h, n)
+
+    def observables(self, max_entries: int = 1 << 20) -> np.ndarray:
+        return sw_observables(self.h, max_entries)
+
+    def spins(self) -> np.ndarray:
+        return sw_get_spins(self.h, self.L)
+
+    def set_spins(self, spins: np.ndarray):
+        sw_set_spins(self.h, spins)
+
+    def labels(self) -> np.ndarray:
+        return sw_get_labels(self.h, self.L)
+
+    def bonds(self) -> np.ndarray:
+        return sw_get_bonds(self.h, self.L)
+
+    def state(self) -> dict:
+        return sw_get_state(self.h)
+
+    def set_stream(self, stream):
+        sw_set_stream(self.h, stream)
+
+    def sync(self):
+        sw_sync(self.h)
