@@ -28,7 +28,7 @@ namespace swg {
 
 constexpr int TW = 128;           // tile width in sites (4 words of 32 sites)
 constexpr int TWW = TW / 32;      // words per tile row
-constexpr int NTHREADS = 512;     // threads per tile CTA
+constexpr int PW = TW + 1;        // padded row of the shared forest (rows fall on distinct banks)
 constexpr int CROSS_WORDS = 8;    // per tile: 4 words right-edge bits, 4 words bottom-edge bits
 
 // 30-bit global roots: the GPU path supports N = L*L <= 2^30.
@@ -128,10 +128,11 @@ __device__ __forceinline__ uint32_t u4_word(const U4 &v, int i)
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// u < t with t in [0, 2^32]
-__device__ __forceinline__ bool below(uint32_t u, uint64_t t)
+// u < t for a threshold t in [1, 2^32], given t - 1 (t = 0 is handled by the
+// caller: no link bonds)
+__device__ __forceinline__ bool below(uint32_t u, uint32_t t_minus_1)
 {
-    return (uint64_t)u < t;
+    return u <= t_minus_1;
 }
 
 // Spread the low 16 bits of v to the even bit positions.
@@ -223,16 +224,6 @@ __device__ __forceinline__ int sfind(volatile int *par, int x)
     return x;
 }
 
-__device__ __forceinline__ int sfind_ro(const volatile int *par, int x)
-{
-    int p = par[x];
-    while (p != x) {
-        x = p;
-        p = par[x];
-    }
-    return x;
-}
-
 __device__ __forceinline__ void sunite(volatile int *par, int a, int b)
 {
     for (;;) {
@@ -248,65 +239,129 @@ __device__ __forceinline__ void sunite(volatile int *par, int a, int b)
     }
 }
 
-// Start (run head) words of a row: bit x is set iff x == 0 or the link
-// (x-1, x) is not an intra-tile bond.
-__device__ __forceinline__ void row_starts(const uint32_t *h, uint32_t s[TWW])
+// Threads of a tile CTA: one warp per 32 x 32 sub-tile.
+template <int TH>
+struct TileCfg {
+    static constexpr int NT = 4 * TH;           // threads per CTA
+    static constexpr int NW = NT / 32;          // warps = sub-tiles
+    static constexpr int SUBY = TH / 32;        // sub-tile rows
+};
+
+// Root of x without writing (a forest no thread is changing any more).
+__device__ __forceinline__ int sroot(const volatile int *par, int x)
 {
-    s[0] = ~(h[0] << 1);
-#pragma unroll
-    for (int c = 1; c < TWW; ++c) s[c] = ~((h[c] << 1) | (h[c - 1] >> 31));
+    int p = par[x];
+    while (p != x) {
+        x = p;
+        p = par[x];
+    }
+    return x;
 }
 
-// Connected components of the intra-tile bonds (H: right links with the
-// tile-crossing link of the last column cleared; V: down links of rows
-// y < th-1).  On return par[i] is the local root of site i for every site of
-// the tile (sites outside tw x th are their own roots).
+// Packed per-root record written over a root's own forest entry once the
+// tile is labelled: INFO_BORDER | 0x8000 | slot for a piece that touches the
+// tile border (slot = its representative node), INFO_INTERIOR | spin << 14 |
+// local index for a cluster that ends inside the tile.  The low 16 bits are
+// the site code.  Forest indices stay below INFO_INTERIOR.
+constexpr uint32_t INFO_BORDER = 0x80008000u;
+constexpr uint32_t INFO_INTERIOR = 0x40000000u;
+
+// Run heads of a 32-site row word inside one sub-tile: bit x is set iff
+// x == 0 or the link (x-1, x) is not a bond (bit 31 of h, the link leaving
+// the sub-tile, is ignored).
+__device__ __forceinline__ uint32_t run_heads(uint32_t h)
+{
+    return ~((h & 0x7FFFFFFFu) << 1);
+}
+
+// Local index of the head of the run that holds bit x of a row word whose
+// first site has local index base.
+__device__ __forceinline__ int head_of(uint32_t heads, int base, int x)
+{
+    return base + 31 - __clz(heads & (0xFFFFFFFFu >> (31 - x)));
+}
+
+// Connected components of the intra-tile bonds (H: right links, with the
+// link leaving the tile's last column cleared; V: down links, zero in the
+// tile's last row).  The tile is cut into 32 x 32 sub-tiles, one per warp,
+// and the forest lives on run heads only (a run = maximal chain of right
+// bonds inside one sub-tile row; its head is its leftmost site):
+//   1. lane r of a warp owns row r of its sub-tile: it unites the runs of its
+//      row with the runs below at every down bond, skipping a bond when the
+//      bond to its left already joins the same two runs;
+//   2. unions across the sub-tile boundaries inside the tile.
+// Links always hang the larger root under the smaller, so par[x] < x unless x
+// is a root and every root is the minimum local index of its piece; local
+// row-major order is the global order, so the root is the piece's minimum
+// site.  Forest indices are padded, y * PW + x, which keeps row-major order
+// and puts the rows of a column on distinct shared-memory banks.
 template <int TH>
 __device__ void tile_label(volatile int *par, const uint32_t (*H)[TWW], const uint32_t (*V)[TWW],
                            int th)
 {
+    constexpr int NT = TileCfg<TH>::NT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = NTHREADS / 32;
-    // 1. every site points at the head of its horizontal run
-    for (int w = warp; w < th * TWW; w += NW) {
-        const int y = w >> 2, c = w & 3;
-        uint32_t s[TWW];
-        row_starts(H[y], s);
-        const uint32_t m = s[c] & (0xFFFFFFFFu >> (31 - lane));
-        int start;
-        if (m) {
-            start = 32 * c + 31 - __clz(m);
-        } else {
-            start = 0;
-            for (int cc = c - 1; cc >= 0; --cc) {
-                if (s[cc]) {
-                    start = 32 * cc + 31 - __clz(s[cc]);
-                    break;
-                }
+    const int sx = warp & (TWW - 1), sy = warp / TWW;
+
+    // ---- 1. inside each sub-tile, lane = row
+    {
+        const int y = 32 * sy + lane;
+        const bool row_ok = y < th;
+        const uint32_t heads = run_heads(row_ok ? H[y][sx] : 0u);
+        const uint32_t heads_below = __shfl_down_sync(0xFFFFFFFFu, heads, 1);
+        const uint32_t v = (row_ok && lane < 31) ? V[y][sx] : 0u;
+        const uint32_t u = v & (~(v << 1) | heads | heads_below);
+        const int base = y * PW + 32 * sx;
+        if (row_ok) {
+            for (uint32_t b = heads; b; b &= b - 1) {
+                const int x = __ffs(b) - 1;
+                par[base + x] = base + x;
             }
         }
-        par[y * TW + 32 * c + lane] = y * TW + start;
-    }
-    for (int i = th * TW + threadIdx.x; i < TH * TW; i += NTHREADS) par[i] = i;
-    __syncthreads();
-    // 2. vertical bonds join runs; a bond whose left neighbour already joins
-    //    the same two runs is skipped
-    for (int w = warp; w < (th - 1) * TWW; w += NW) {
-        const int y = w >> 2, c = w & 3;
-        const uint32_t v = V[y][c];
-        if (!v) continue;
-        uint32_t s0[TWW], s1[TWW];
-        row_starts(H[y], s0);
-        row_starts(H[y + 1], s1);
-        const uint32_t vs = (v << 1) | (c > 0 ? (V[y][c - 1] >> 31) : 0u);
-        const uint32_t u = v & (s0[c] | s1[c] | ~vs);
-        if ((u >> lane) & 1u) sunite(par, y * TW + 32 * c + lane, (y + 1) * TW + 32 * c + lane);
+        __syncwarp();
+        for (uint32_t b = u; b; b &= b - 1) {
+            const int x = __ffs(b) - 1;
+            sunite(par, head_of(heads, base, x), head_of(heads_below, base + PW, x));
+        }
     }
     __syncthreads();
-    // 3. flatten (read-only finds: each thread writes only its own sites)
-    for (int i = threadIdx.x; i < th * TW; i += NTHREADS) {
-        const int r = sfind_ro(par, i);
-        par[i] = r;
+
+    // ---- 2. links across sub-tile boundaries: vertical boundaries between
+    //         sub-tile columns, horizontal ones between sub-tile rows
+    {
+        constexpr int NV = (TWW - 1) * TH;
+        constexpr int NH = (TH / 32 - 1) * TW;
+        for (int q = threadIdx.x; q < NV + NH; q += NT) {
+            int a, b;
+            if (q < NV) {
+                const int bnd = q / TH + 1, y = q % TH;     // link (32 bnd - 1, y) - (32 bnd, y)
+                if (y >= th || !((H[y][bnd - 1] >> 31) & 1u)) continue;
+                // skip when the row above already joins the same two sites
+                // through down links inside the sub-tiles (united in phase 1;
+                // at a sub-tile row edge those down links are phase-2 links
+                // themselves and could justify each other in a cycle)
+                if ((y & 31) != 0 && ((H[y - 1][bnd - 1] >> 31) & 1u) &&
+                    ((V[y - 1][bnd - 1] >> 31) & 1u) && (V[y - 1][bnd] & 1u))
+                    continue;
+                a = head_of(run_heads(H[y][bnd - 1]), y * PW + 32 * (bnd - 1), 31);
+                b = y * PW + 32 * bnd;   // column 0 of a sub-tile row is always a head
+            } else {
+                const int r = q - NV;
+                const int bnd = r / TW + 1, x = r % TW;     // link (x, 32 bnd - 1) - (x, 32 bnd)
+                const int y = 32 * bnd - 1;
+                if (y + 1 >= th || !((V[y][x >> 5] >> (x & 31)) & 1u)) continue;
+                // skip when the column to the left already joins the same two
+                // sites through right links inside the sub-tiles
+                if ((x & 31) != 0 && ((V[y][(x - 1) >> 5] >> ((x - 1) & 31)) & 1u) &&
+                    ((H[y][(x - 1) >> 5] >> ((x - 1) & 31)) & 1u) &&
+                    ((H[y + 1][(x - 1) >> 5] >> ((x - 1) & 31)) & 1u))
+                    continue;
+                const int c = x >> 5;
+                a = head_of(run_heads(H[y][c]), y * PW + 32 * c, x & 31);
+                b = head_of(run_heads(H[y + 1][c]), (y + 1) * PW + 32 * c, x & 31);
+            }
+            sunite(par, a, b);
+        }
     }
     __syncthreads();
 }
@@ -345,7 +400,7 @@ __device__ __forceinline__ void gunite(int32_t *par, int a, int b)
 }
 
 // --------------------------------------------------------- block reductions
-template <int K>
+template <int NT, int K>
 __device__ __forceinline__ void block_sum_atomic(long long (&v)[K], unsigned long long *const dst[K],
                                                  long long (*red)[K])
 {
@@ -361,7 +416,7 @@ __device__ __forceinline__ void block_sum_atomic(long long (&v)[K], unsigned lon
     if (warp == 0) {
 #pragma unroll
         for (int q = 0; q < K; ++q) {
-            long long x = lane < NTHREADS / 32 ? red[lane][q] : 0;
+            long long x = lane < NT / 32 ? red[lane][q] : 0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
             if (lane == 0 && dst[q] && x != 0) atomicAdd(dst[q], (unsigned long long)x);
@@ -372,7 +427,7 @@ __device__ __forceinline__ void block_sum_atomic(long long (&v)[K], unsigned lon
 // ------------------------------------------------------------ shared layout
 template <int TH>
 struct TileSmem {
-    int par[TH * TW];               // union-find forest / local roots
+    int par[TH * PW];               // union-find forest over run heads (padded rows)
     uint32_t sp[TH + 1][TWW + 1];   // spins as bits, row TH = halo row, bit tw = halo column
     uint32_t bh[TH][TWW];           // right-link bonds (bit x: link (x,y)-(x+1,y))
     uint32_t bv[TH][TWW];           // down-link bonds
@@ -380,16 +435,20 @@ struct TileSmem {
     uint32_t iv[TH][TWW];           // intra-tile down bonds
     uint32_t spb[TH][8];            // SPIN-stream blocks covering each row
     uint32_t finfo[Slots<TH>::S];   // resolved finals of the tile's own nodes
-    long long red[NTHREADS / 32][4];
+    long long red[TileCfg<TH>::NW][4];
 };
 
 // ----------------------------------------------------------------- k_tile
 template <int TH>
-__global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
+__global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
 {
     using SL = Slots<TH>;
     constexpr int S = SL::S;
-    constexpr int NW = NTHREADS / 32;
+    constexpr int NT = TileCfg<TH>::NT;
+    constexpr int NW = TileCfg<TH>::NW;
+    constexpr int SPT = (S + NT - 1) / NT;   // node slots per thread
+    constexpr int NQ = TH * TW / 8 / NT;     // 8-site groups per thread
+    static_assert(NQ * 8 * NT == TH * TW, "tile sites must split into 8-site groups");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<TH> &sm = *reinterpret_cast<TileSmem<TH> *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
@@ -403,44 +462,67 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
     if (!fin && !start) return;
     const Tile t = tile_of(R, g, TH);
     const int L = R.L;
-    const int64_t gbase = (int64_t)t.y0 * L + t.x0;   // global index of local site 0
+    // site indices fit in 32 bits (N <= 2^30)
+    const uint32_t uL = (uint32_t)L;
+    const uint32_t gbase = (uint32_t)t.y0 * uL + (uint32_t)t.x0;   // global index of local site 0
     uint16_t *code = a.code + (size_t)g * TH * TW;
 
     if (fin) {
         // ---- finish sweep k-1: resolve every site's cluster and flip it
         const int jf = j - 1;
         const bool last = j == R.nsweeps;
-        for (int s = tid; s < S; s += NTHREADS) sm.finfo[s] = a.nfinal[(size_t)g * S + s];
+        // the tile's codes, 8 sites per 16-byte load, all issued up front
+        uint4 cv[NQ];
+        const uint4 *code4 = reinterpret_cast<const uint4 *>(code);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int idx = tid + q * NT;
+            cv[q] = ((idx * 8) / TW < t.th) ? code4[idx] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        for (int s = tid; s < S; s += NT) sm.finfo[s] = a.nfinal[(size_t)g * S + s];
+        for (int y = tid; y < t.th; y += NT) sm.sp[y][TWW] = 0u;
         __syncthreads();
-        long long ncl = 0;
-        for (int w = warp; w < t.th * TWW; w += NW) {
-            const int y = w >> 2, c = w & 3;
-            const int x = 32 * c + lane;
-            const bool valid = x < t.tw;
-            int spin = 0;
-            if (valid) {
-                const uint16_t u = code[y * TW + x];
-                uint32_t root;
-                if (u & CODE_BORDER) {
-                    const uint32_t f = sm.finfo[u & 0x3FFu];
-                    root = f & ROOT_MASK;
-                    spin = (f & FINAL_SPIN) ? 1 : 0;
-                } else {
-                    const int lr = u & CODE_ROOT;
-                    root = (uint32_t)(gbase + (int64_t)(lr / TW) * L + (lr % TW));
-                    spin = (u & CODE_SPIN) ? 1 : 0;
-                }
-                const int64_t gi = gbase + (int64_t)y * L + x;
-                ncl += root == (uint32_t)gi;
-                if (last) {
-                    R.spin[gi] = (uint8_t)spin;
-                    R.label[gi] = (int32_t)root;
-                }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int idx = tid + q * NT;
+            const int y = (idx * 8) / TW, xb = (idx * 8) % TW;
+            if (y >= t.th) continue;
+            const uint32_t wv[4] = {cv[q].x, cv[q].y, cv[q].z, cv[q].w};
+            uint32_t bits = 0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t u = (wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                const uint32_t spin =
+                    (u & CODE_BORDER) ? (sm.finfo[u & 0x3FFu] >> 30) & 1u : (u >> 14) & 1u;
+                bits |= spin << e;
             }
-            const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
-            if (lane == 0) {
-                sm.sp[y][c] = word;
-                if (c == TWW - 1) sm.sp[y][TWW] = 0u;
+            bits &= (1u << min(8, max(0, t.tw - xb))) - 1u;   // sites past tw are not spins
+            reinterpret_cast<uint8_t *>(&sm.sp[y][0])[xb >> 3] = (uint8_t)bits;
+            if (last) {
+                const uint32_t gi0 = gbase + (uint32_t)y * uL + (uint32_t)xb;
+                uint32_t roots[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t u = (wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                    const uint32_t lr = u & CODE_ROOT;
+                    roots[e] = (u & CODE_BORDER) ? sm.finfo[u & 0x3FFu] & ROOT_MASK
+                                                 : gbase + (lr / TW) * uL + (lr % TW);
+                }
+                const int nval = min(8, t.tw - xb);
+                if (nval == 8 && (gi0 & 7u) == 0) {
+                    // spread the 8 spin bits to 8 bytes
+                    const uint32_t lo = ((bits & 0xFu) * 0x00204081u) & 0x01010101u;
+                    const uint32_t hi = (((bits >> 4) & 0xFu) * 0x00204081u) & 0x01010101u;
+                    *reinterpret_cast<uint2 *>(R.spin + gi0) = make_uint2(lo, hi);
+                    int4 *lp = reinterpret_cast<int4 *>(R.label + gi0);
+                    lp[0] = make_int4((int)roots[0], (int)roots[1], (int)roots[2], (int)roots[3]);
+                    lp[1] = make_int4((int)roots[4], (int)roots[5], (int)roots[6], (int)roots[7]);
+                } else {
+                    for (int e = 0; e < nval; ++e) {
+                        R.spin[gi0 + e] = (uint8_t)((bits >> e) & 1u);
+                        R.label[gi0 + e] = (int32_t)roots[e];
+                    }
+                }
             }
         }
         // bottom halo row: new spins of the top row of the tile below
@@ -453,13 +535,13 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
         }
         __syncthreads();
         // right halo column: new spins of the left column of the tile to the right
-        for (int y = tid; y < t.th; y += NTHREADS) {
+        for (int y = tid; y < t.th; y += NT) {
             if (a.nfinal[(size_t)t.g_right * S + SL::LEFT + y] & FINAL_SPIN)
                 sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
         }
         __syncthreads();
         long long bs = 0, mag = 0;
-        for (int w = tid; w < t.th * TWW; w += NTHREADS) {
+        for (int w = tid; w < t.th * TWW; w += NT) {
             const int y = w >> 2, c = w & 3;
             const uint32_t vm = valid_mask(c, t.tw);
             const uint32_t cur = sm.sp[y][c];
@@ -469,10 +551,10 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
             bs += 2 * nv - 2 * (__popc((cur ^ right) & vm) + __popc((cur ^ down) & vm));
             mag += 2 * __popc(cur & vm) - nv;
         }
-        long long v[4] = {bs, mag, ncl, 0};
+        long long v[4] = {bs, mag, 0, 0};
         DevObs *o = R.obs + jf;
-        unsigned long long *const dst[4] = {&o->bond_sum, &o->mag, &o->nclusters, nullptr};
-        block_sum_atomic<4>(v, dst, sm.red);
+        unsigned long long *const dst[4] = {&o->bond_sum, &o->mag, nullptr, nullptr};
+        block_sum_atomic<NT, 4>(v, dst, sm.red);
         __syncthreads();
     }
 
@@ -486,9 +568,9 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
         for (int w = warp; w < (t.th + 1) * TWW; w += NW) {
             const int y = w >> 2, c = w & 3;
             const int x = 32 * c + lane;
-            const int64_t gy = (t.y0 + y) % L;
+            const uint32_t gy = (uint32_t)((t.y0 + y) % L);
             int spin = 0;
-            if (x < t.tw) spin = R.spin[gy * L + t.x0 + x];
+            if (x < t.tw) spin = R.spin[gy * uL + (uint32_t)(t.x0 + x)];
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
             if (lane == 0) {
                 sm.sp[y][c] = word;
@@ -496,8 +578,8 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
             }
         }
         __syncthreads();
-        for (int y = tid; y < t.th; y += NTHREADS) {
-            const int64_t gi = (int64_t)(t.y0 + y) * L + (t.x0 + t.tw) % L;
+        for (int y = tid; y < t.th; y += NT) {
+            const uint32_t gi = (uint32_t)(t.y0 + y) * uL + (uint32_t)((t.x0 + t.tw) % L);
             if (R.spin[gi]) sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
         }
         __syncthreads();
@@ -511,43 +593,53 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
     // Step 1 (Sec. I): bonds.  Link l = 2i + d draws word (l mod 4) of
     // Philox(l/4, k, BOND), i.e. sites 2m and 2m+1 share block m.
     const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
-    for (int w = warp; w < t.th * 2; w += NW) {
-        const int y = w >> 1, half = w & 1;
-        if (64 * half >= t.tw) continue;
-        const int64_t G0 = gbase + (int64_t)y * L;
-        uint32_t rh[2], rv[2];
-        if ((G0 & 1) == 0) {
-            // aligned row: lane takes the block of sites (64h + 2 lane, +1)
-            const uint64_t blk = (uint64_t)(G0 >> 1) + 32 * half + lane;
-            const U4 r = philox4x32_10((uint32_t)blk, klo, khi, STREAM_BOND, R.key0, R.key1);
-            const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, below(r.x, thr));
-            const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, below(r.y, thr));
-            const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, below(r.z, thr));
-            const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, below(r.w, thr));
-            rh[0] = spread16(b0) | (spread16(b2) << 1);
-            rh[1] = spread16(b0 >> 16) | (spread16(b2 >> 16) << 1);
-            rv[0] = spread16(b1) | (spread16(b3) << 1);
-            rv[1] = spread16(b1 >> 16) | (spread16(b3 >> 16) << 1);
+    const bool any_bond = thr != 0;               // t = 0: P = 0, nothing bonds
+    const uint32_t tm1 = (uint32_t)(thr - 1);     // t in [1, 2^32] -> t - 1 fits 32 bits
+    for (int y = warp; y < t.th; y += NW) {
+        const uint32_t G0 = gbase + (uint32_t)y * uL;
+        uint32_t rh[TWW], rv[TWW];
+        if (!any_bond) {
+#pragma unroll
+            for (int q = 0; q < TWW; ++q) rh[q] = rv[q] = 0u;
+        } else if ((G0 & 1u) == 0) {
+            // aligned row: lane l draws the blocks of sites (2l, 2l+1) and
+            // (64+2l, 65+2l); lane x of each 32-site word then fetches its
+            // two bits by shuffle
+            const uint32_t b0 = (G0 >> 1) + lane;
+            const U4 r0 = philox4x32_10(b0, klo, khi, STREAM_BOND, R.key0, R.key1);
+            const U4 r1 = philox4x32_10(b0 + 32, klo, khi, STREAM_BOND, R.key0, R.key1);
+            const uint32_t nib0 = (below(r0.x, tm1) ? 1u : 0u) | (below(r0.y, tm1) ? 2u : 0u) |
+                                  (below(r0.z, tm1) ? 4u : 0u) | (below(r0.w, tm1) ? 8u : 0u);
+            const uint32_t nib1 = (below(r1.x, tm1) ? 1u : 0u) | (below(r1.y, tm1) ? 2u : 0u) |
+                                  (below(r1.z, tm1) ? 4u : 0u) | (below(r1.w, tm1) ? 8u : 0u);
+#pragma unroll
+            for (int q = 0; q < TWW; ++q) {
+                const uint32_t n = __shfl_sync(0xFFFFFFFFu, q < 2 ? nib0 : nib1, 16 * (q & 1) + (lane >> 1)) >>
+                                   (2 * (lane & 1));
+                rh[q] = __ballot_sync(0xFFFFFFFFu, n & 1u);
+                rv[q] = __ballot_sync(0xFFFFFFFFu, n & 2u);
+            }
         } else {
             // odd row start (odd L): every site draws its own block
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int64_t gi = G0 + 64 * half + 32 * q + lane;
-                const U4 r = philox4x32_10((uint32_t)(gi >> 1), klo, khi, STREAM_BOND, R.key0,
-                                           R.key1);
-                const bool odd = gi & 1;
-                rh[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.z : r.x, thr));
-                rv[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.w : r.y, thr));
+            for (int q = 0; q < TWW; ++q) {
+                const uint32_t gi = G0 + 32 * q + lane;
+                const U4 r = philox4x32_10(gi >> 1, klo, khi, STREAM_BOND, R.key0, R.key1);
+                const bool odd = gi & 1u;
+                rh[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.z : r.x, tm1));
+                rv[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.w : r.y, tm1));
             }
         }
-        if (lane < 2) {
-            const int c = 2 * half + lane;
+        if (lane < TWW) {
+            const int c = lane;
+            const uint32_t rhc = c == 0 ? rh[0] : c == 1 ? rh[1] : c == 2 ? rh[2] : rh[3];
+            const uint32_t rvc = c == 0 ? rv[0] : c == 1 ? rv[1] : c == 2 ? rv[2] : rv[3];
             const uint32_t vm = valid_mask(c, t.tw);
             const uint32_t cur = sm.sp[y][c];
             const uint32_t right = (cur >> 1) | (sm.sp[y][c + 1] << 31);
             const uint32_t down = sm.sp[y + 1][c];
-            const uint32_t h = rh[lane] & ~(cur ^ right) & vm;
-            const uint32_t v = rv[lane] & ~(cur ^ down) & vm;
+            const uint32_t h = rhc & ~(cur ^ right) & vm;
+            const uint32_t v = rvc & ~(cur ^ down) & vm;
             sm.bh[y][c] = h;
             sm.bv[y][c] = v;
             // intra-tile parts: the last column's right link and the last
@@ -556,19 +648,12 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
             sm.iv[y][c] = (y < t.th - 1) ? v : 0u;
         }
     }
-    // rows with no valid half (tw <= 64 leaves words 2,3 unset)
-    for (int w = tid; w < t.th * TWW; w += NTHREADS) {
-        const int y = w >> 2, c = w & 3;
-        if (64 * (c >> 1) >= t.tw) {
-            sm.bh[y][c] = sm.bv[y][c] = sm.ih[y][c] = sm.iv[y][c] = 0u;
-        }
-    }
     // SPIN-stream blocks covering each row, for the clusters that end inside
     // the tile (Sec. I step 3: one new random spin per cluster)
-    for (int q = tid; q < 2 * t.th; q += NTHREADS) {
+    for (int q = tid; q < 2 * t.th; q += NT) {
         const int y = q >> 1, b = q & 1;
-        const uint64_t blk = (uint64_t)((gbase + (int64_t)y * L) >> 7) + b;
-        const U4 r = philox4x32_10((uint32_t)blk, klo, khi, STREAM_SPIN, R.key0, R.key1);
+        const uint32_t blk = ((gbase + (uint32_t)y * uL) >> 7) + b;
+        const U4 r = philox4x32_10(blk, klo, khi, STREAM_SPIN, R.key0, R.key1);
         sm.spb[y][4 * b + 0] = r.x;
         sm.spb[y][4 * b + 1] = r.y;
         sm.spb[y][4 * b + 2] = r.z;
@@ -577,23 +662,25 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
     __syncthreads();
 
     long long nb = 0;
-    for (int w = tid; w < t.th * TWW; w += NTHREADS) {
+    for (int w = tid; w < t.th * TWW; w += NT) {
         const int y = w >> 2, c = w & 3;
         nb += __popc(sm.bh[y][c]) + __popc(sm.bv[y][c]);
     }
     // crossing bonds: right edge (bit tw-1 of each row), bottom edge (row th-1)
-    if (warp < TWW) {
-        const int y = 32 * warp + lane;
-        const int bit = (y < t.th) ? (sm.bh[y][(t.tw - 1) >> 5] >> ((t.tw - 1) & 31)) & 1 : 0;
-        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
-        if (lane == 0) a.cross[(size_t)g * CROSS_WORDS + warp] = word;
-    } else if (warp == TWW && lane < TWW) {
-        a.cross[(size_t)g * CROSS_WORDS + TWW + lane] = sm.bv[t.th - 1][lane];
+    for (int q = warp; q <= TH / 32; q += NW) {
+        if (q < TH / 32) {
+            const int y = 32 * q + lane;
+            const int bit = (y < t.th) ? (sm.bh[y][(t.tw - 1) >> 5] >> ((t.tw - 1) & 31)) & 1 : 0;
+            const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
+            if (lane == 0) a.cross[(size_t)g * CROSS_WORDS + q] = word;
+        } else if (lane < TWW) {
+            a.cross[(size_t)g * CROSS_WORDS + TWW + lane] = sm.bv[t.th - 1][lane];
+        }
     }
     if (j == R.nsweeps - 1) {
         // the last sweep of the call keeps its bonds for sw_get_bonds
         uint32_t *bb = a.bondbits + (size_t)g * TH * 2 * TWW;
-        for (int w = tid; w < t.th * TWW; w += NTHREADS) {
+        for (int w = tid; w < t.th * TWW; w += NT) {
             const int y = w >> 2, c = w & 3;
             bb[y * 2 * TWW + c] = sm.bh[y][c];
             bb[y * 2 * TWW + TWW + c] = sm.bv[y][c];
@@ -605,57 +692,94 @@ __global__ void __launch_bounds__(NTHREADS) k_tile(const SweepArgs a)
 
     // One node per border site: key = global index of the piece's local root,
     // parent = the piece's first border slot (the representative).
-    int rs = -1;
-    const int s = tid;
-    if (s < S) {
+    int rs[SPT];
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+        const int s = tid + q * NT;
         int site;
-        if (slot_site<TH>(s, t.tw, t.th, site)) rs = sm.par[site];
+        rs[q] = -1;
+        if (s < S && slot_site<TH>(s, t.tw, t.th, site)) {
+            const int sy = site / TW, c = (site % TW) >> 5;
+            rs[q] = sroot(sm.par, head_of(run_heads(sm.ih[sy][c]), sy * PW + 32 * c, site & 31));
+        }
     }
     __syncthreads();
-    if (rs >= 0) atomicMin((int *)&sm.par[rs], (int)(0x80000000u | (uint32_t)s));
+#pragma unroll
+    for (int q = 0; q < SPT; ++q)
+        if (rs[q] >= 0) atomicMin((int *)&sm.par[rs[q]], (int)(INFO_BORDER | (uint32_t)(tid + q * NT)));
     __syncthreads();
-    if (s < S) {
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+        const int s = tid + q * NT;
+        if (s >= S) break;
         const size_t node = (size_t)g * S + s;
-        if (rs >= 0) {
-            const int rep = sm.par[rs] & 0x3FF;
+        if (rs[q] >= 0) {
+            const int rep = sm.par[rs[q]] & 0x3FF;
             a.npar[node] = (int32_t)((size_t)g * S + rep);
-            a.nkey[node] = (int32_t)(gbase + (int64_t)(rs / TW) * L + rs % TW);
+            a.nkey[node] = (int32_t)(gbase + (uint32_t)(rs[q] / PW) * uL + (uint32_t)(rs[q] % PW));
         } else {
             a.npar[node] = (int32_t)node;
             a.nkey[node] = (int32_t)KEY_NONE;
         }
     }
-    // Every site's 2-byte code: border pieces by node slot, interior clusters
-    // by local root with their new spin already drawn.
-    for (int w = warp; w < t.th * TWW; w += NW) {
-        const int y = w >> 2, c = w & 3;
-        const int x = 32 * c + lane;
-        if (x >= t.tw) continue;
-        const int i = y * TW + x;
-        const int v = sm.par[i];
-        uint16_t u;
-        if (v < 0) {
-            u = (uint16_t)(CODE_BORDER | (v & 0x3FF));
-        } else {
-            const int pv = sm.par[v];
-            if (pv < 0) {
-                u = (uint16_t)(CODE_BORDER | (pv & 0x3FF));
-            } else {
-                const int ry = v / TW, rx = v % TW;
-                const int64_t rowg = gbase + (int64_t)ry * L;
-                const int64_t gv = rowg + rx;
+    // Every run head learns its root; every interior root gets its record
+    // (the cluster's new spin, Sec. I step 3, drawn here) and is counted.
+    // A walk stops at a root, a border record or an interior record, and each
+    // thread writes only its own heads, so concurrent walks see ancestors.
+    long long ncl_interior = 0;
+    for (int w = tid; w < t.th * TWW; w += NT) {
+        const int y = w % t.th, c = w / t.th;   // a warp covers consecutive rows
+        const int base = y * PW + 32 * c;
+        for (uint32_t bits = run_heads(sm.ih[y][c]); bits; bits &= bits - 1) {
+            const int hx = __ffs(bits) - 1;
+            const int hd = base + hx;
+            int x = hd, p = sm.par[x];
+            while (p != x && p >= 0 && (uint32_t)p < INFO_INTERIOR) {
+                x = p;
+                p = sm.par[x];
+            }
+            if (x != hd) {
+                sm.par[hd] = x;
+            } else if (p == hd && 32 * c + hx < t.tw) {
+                // an interior root inside the tile
+                const uint32_t rowg = gbase + (uint32_t)y * uL;
+                const uint32_t gv = rowg + (uint32_t)(32 * c + hx);
                 const int b = (int)((gv >> 7) - (rowg >> 7));
                 const int bit = (int)(gv & 127);
-                const int spin = (sm.spb[ry][4 * b + (bit >> 5)] >> (bit & 31)) & 1;
-                u = (uint16_t)((spin ? CODE_SPIN : 0) | v);
+                const uint32_t spin = (sm.spb[y][4 * b + (bit >> 5)] >> (bit & 31)) & 1u;
+                sm.par[hd] = (int)(INFO_INTERIOR | (spin << 14) | (uint32_t)(y * TW + 32 * c + hx));
+                ++ncl_interior;
             }
         }
-        code[i] = u;
     }
-    long long v4[4] = {nb, 0, 0, 0};
+    __syncthreads();
+    // Every site's 2-byte code (the low half of its root's record): border
+    // pieces by node slot, interior clusters by local root and new spin.
+    // 8 sites per 16-byte store.
+    uint4 *code4 = reinterpret_cast<uint4 *>(code);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int idx = tid + q * NT;
+        const int y = (idx * 8) / TW, xb = (idx * 8) % TW;
+        if (y >= t.th) continue;
+        uint32_t wv[4] = {0u, 0u, 0u, 0u};
+        const int c = xb >> 5;
+        const uint32_t heads = run_heads(sm.ih[y][c]);
+        const int base = y * PW + 32 * c;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int x = xb + e;
+            if (x >= t.tw) break;
+            const int v = sm.par[head_of(heads, base, x & 31)];
+            const int info = (v < 0 || (uint32_t)v >= INFO_INTERIOR) ? v : sm.par[v];
+            wv[e >> 1] |= ((uint32_t)info & 0xFFFFu) << (16 * (e & 1));
+        }
+        code4[idx] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    long long v4[4] = {nb, ncl_interior, 0, 0};
     DevObs *o = R.obs + j;
-    unsigned long long *const dst[4] = {&o->nbonds, nullptr, nullptr, nullptr};
-    block_sum_atomic<4>(v4, dst, sm.red);
+    unsigned long long *const dst[4] = {&o->nbonds, &o->nclusters, nullptr, nullptr};
+    block_sum_atomic<NT, 4>(v4, dst, sm.red);
 }
 
 // ------------------------------------------------------------- merge phase
@@ -696,21 +820,32 @@ template <int TH>
 __global__ void k_merge_compress(const SweepArgs a)
 {
     constexpr int S = Slots<TH>::S;
+    static_assert(S % 32 == 0, "a warp's nodes must belong to one tile");
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (int64_t)a.n_tiles * S) return;
+    const int j = a.j + *a.jbase;
     const Replica &R = a.reps[a.tile_rep[n / S]];
-    if (!(a.j + *a.jbase < R.nsweeps)) return;
+    if (!(j < R.nsweeps)) return;   // uniform across the warp (one tile)
     const int key = a.nkey[n];
-    if ((uint32_t)key == KEY_NONE) return;
-    // read-only find: the forest is fixed now, and each thread writes only
-    // its own entry, so every entry ends pointing at its root
-    int r = (int)n, p = gload(a.npar + r);
-    while (p != r) {
-        r = p;
-        p = gload(a.npar + r);
+    bool is_root = false;
+    if ((uint32_t)key != KEY_NONE) {
+        // read-only find: the forest is fixed now, and each thread writes
+        // only its own entry, so every entry ends pointing at its root
+        int r = (int)n, p = gload(a.npar + r);
+        while (p != r) {
+            r = p;
+            p = gload(a.npar + r);
+        }
+        a.npar[n] = r;
+        if (r != n)
+            atomicMin(a.nkey + r, key);
+        else
+            is_root = true;
     }
-    a.npar[n] = r;
-    if (r != n) atomicMin(a.nkey + r, key);
+    // one root node per cluster that touches a tile border
+    const uint32_t roots = __ballot_sync(__activemask(), is_root);
+    if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && roots)
+        atomicAdd(&R.obs[j].nclusters, (unsigned long long)__popc(roots));
 }
 
 // Each node takes its cluster's root and the cluster's new spin:

@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -60,7 +61,7 @@ template <int TH>
 cudaError_t enqueue_launch(const SweepArgs &a, cudaStream_t st)
 {
     constexpr int S = Slots<TH>::S;
-    k_tile<TH><<<a.n_tiles, NTHREADS, tile_smem_bytes<TH>(), st>>>(a);
+    k_tile<TH><<<a.n_tiles, TileCfg<TH>::NT, tile_smem_bytes<TH>(), st>>>(a);
     const int64_t nu = (int64_t)a.n_tiles * (TH + TW);
     const int64_t nn = (int64_t)a.n_tiles * S;
     k_merge_union<TH><<<(unsigned)((nu + MERGE_THREADS - 1) / MERGE_THREADS), MERGE_THREADS, 0, st>>>(a);
@@ -89,9 +90,14 @@ cudaError_t prepare_th(int TH)
 
 int slots_of(int TH) { return 2 * TW + 2 * TH; }
 
-// Tile height used for an L x L lattice.
+// Tile height used for an L x L lattice.  SWGPU_TILE_H (32, 64 or 128)
+// overrides the default for tuning runs.
 int pick_tile_height(int L)
 {
+    if (const char *env = std::getenv("SWGPU_TILE_H")) {
+        const int th = std::atoi(env);
+        if (th == 32 || th == 64 || th == 128) return th;
+    }
     if (L <= 32) return 32;
     if (L <= 64) return 64;
     return 128;
