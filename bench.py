@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the Swendsen-Wang hot path on GB300: prints one JSON line.
+
+Workload: plain SW on the 2D periodic Ising lattice, L = 16384 (268M sites),
+J = 1, T = 2.269185 (critical), hot start; one step = 50 sweeps, the
+configured run length of that lattice.  Metric: site updates per ns over the
+whole job (all ranks), with the lattice resident on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs under torchrun, one independent lattice per GPU (replicas: the
+single-lattice path has no exchange step), timed between barriers, max over
+ranks.  ``--impl reference`` times the CPU oracle (the only reference that
+exists: the paper publishes no code) on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SW site updates/ns at T_c (L=16384)"
+UNIT = "site-updates/ns"
+WIDE_MULS_PER_PHILOX = 20          # 10 rounds x 2 (32x32->64) products
+PROFILE_FILE = os.path.join(ROOT, "profiles", "k_tile_L16384_Tc.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(w, extra=None):
+    cfg = {"workload": f"plain SW, 2D Ising periodic L={w.L}, J=1, T={w.T}, hot start, "
+                       f"{w.sweeps} sweeps per step",
+           "L": w.L, "T": w.T, "J": 1.0, "sweeps_per_step": w.sweeps,
+           "l2": "inputs larger than L2 (256 MiB spins, 512 MiB site codes per lattice)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- roofline
+def alu_peak_tmul(sm_count: int, sm_max_mhz: float) -> float:
+    """Integer multiply ceiling in T (32x32->64 products)/s: the FMA pipe
+    issues 16 lanes of IMAD per SM sub-partition per clock (64 per SM) and a
+    full 64-bit product takes two of them."""
+    return sm_count * 64 / 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def philox_calls_per_start(L: int) -> int:
+    """Philox blocks the tile kernel draws to start one sweep: per 128-wide
+    tile row, 64 BOND blocks (one per two sites; 128 on rows that begin on an
+    odd site, which odd L gives every other row) and 2 SPIN blocks for the
+    clusters that end inside the tile."""
+    tiles_x = (L + 127) // 128
+    odd_rows = L // 2 if L % 2 else 0
+    bond = tiles_x * (64 * (L - odd_rows) + 128 * odd_rows)
+    return bond + 2 * L * tiles_x
+
+
+def profile_traffic(kernel_src_sha: str):
+    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
+    or None when that summary was taken on a different kernel source."""
+    try:
+        txt = open(PROFILE_FILE).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(r"dram bytes per launch:\s*([0-9]+)", txt)
+    if not m_sha or not m_tr or m_sha.group(1) != kernel_src_sha:
+        return None
+    return int(m_tr.group(1))
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("sw_device.cuh", "sw_engine.cu"):
+        h.update(open(os.path.join(ROOT, "paper_0808_2109_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------ cpu baseline
+def cpu_baseline_oracle(w):
+    """The oracle as it stands, single-threaded, on one sweep of the lattice."""
+    import oracle
+    oracle.build()
+    chain = oracle.sw_chain(w.L, 1.0, w.T, w.seed)
+    t0 = time.perf_counter()
+    chain.run(1)
+    dt = time.perf_counter() - t0
+    return {"value": w.L * w.L / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 sweep of the L={w.L} lattice from the hot start ({dt:.1f} s)"}
+
+
+# --------------------------------------------------------------- our arm
+def run_gb300(args):
+    import numpy as np
+    import torch
+    from paper_0808_2109_gb300 import _build, swgpu, workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    w = workloads.LARGE
+    K, W = args.steps, args.warmup
+    N = w.L * w.L
+    stream = torch.cuda.Stream()
+    lat = swgpu.Lattice(w.L, T=w.T, seed=w.seed + rank)
+    lat.set_stream(stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(W):
+        lat.sweep(w.sweeps)
+    lat.sync()
+    lat.observables()
+
+    # ---- timed region: K steps, lattice resident in HBM
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        lat.sweep(w.sweeps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    obs = lat.observables()
+    assert len(obs) == K * w.sweeps
+    value = world * N * w.sweeps * K / (ms * 1e6)
+
+    # ---- per-kernel device times: the same steps, kernels bracketed by events
+    prof_steps = max(1, min(K, 3))
+    lat.profile(True)
+    for _ in range(prof_steps):
+        lat.sweep(w.sweeps)
+    st = lat.profile_read()
+    lat.profile(False)
+    lat.observables()
+    tile_avg_ms = st["tile_ms"] / st["tile_launches"]
+    starts = prof_steps * w.sweeps
+    muls = starts * philox_calls_per_start(w.L) * WIDE_MULS_PER_PHILOX
+    achieved = muls / (st["tile_ms"] * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = alu_peak_tmul(props.multi_processor_count, sm_max)
+    traffic = profile_traffic(kernel_source_sha())
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
+                "unit": "T int32 products/s (32x32->64, Philox4x32-10)",
+                "frac": round(achieved / peak, 4),
+                "traffic": (round(traffic * st["tile_launches"] / max(st["tile_launches"], 1))
+                            if traffic is not None else None),
+                "kernel": "k_tile<128> (fused finish/start of a sweep)",
+                "tile_kernel_avg_ms": round(tile_avg_ms, 4),
+                "merge_group_avg_ms": round(st["merge_ms"] / max(st["merge_groups"], 1), 4),
+                "peak_source": f"derived: {props.multi_processor_count} SMs x 64 IMAD lanes/clk / 2 "
+                               f"per 64-bit product x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"}
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e_steps = max(1, min(K, 5))
+    h_in = torch.empty(N, dtype=torch.uint8, pin_memory=True).numpy()
+    h_out = torch.empty(N, dtype=torch.uint8, pin_memory=True).numpy()
+    h_in[:] = lat.spins()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_spins(h_in)                  # host -> device: this step's input lattice
+        lat.sweep(w.sweeps)
+        o = lat.observables()                # device -> host: per-sweep observables
+        swgpu.sw_get_spins(lat.h, w.L, h_out)  # device -> host: the resulting lattice
+        h_in, h_out = h_out, h_in
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * N * w.sweeps * e2e_steps / (e2e_s * 1e9), "unit": UNIT,
+           "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + w.sweeps * 48,
+           "steps": e2e_steps}
+    del o
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline_oracle(w)
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": round(ms / K, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": workload_config(w, {"parallelism": f"replicas x{world}",
+                                          "seeds": f"{w.seed}..{w.seed + world - 1}"}),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": K * (4 * w.sweeps + 1),
+            "clocks": clk, "impl": "gb300",
+        }
+    lat.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle, single-threaded, one sweep of an L=4096 lattice of the
+    same configuration per step (an L=16384 sweep takes ~30 s on one core)."""
+    from paper_0808_2109_gb300 import workloads
+    import oracle
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    oracle.build()
+    w = workloads.LARGE
+    Ls = 4096
+    chain = oracle.sw_chain(Ls, 1.0, w.T, w.seed)
+    for _ in range(args.warmup):
+        chain.run(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        chain.run(1)
+    dt = time.perf_counter() - t0
+    value = Ls * Ls * args.steps / (dt * 1e9)
+    sample = f"one sweep of an L={Ls} lattice at T={w.T} per step, single-threaded oracle"
+    return {
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": workload_config(w, {"sample_L": Ls}), "impl": "reference",
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_gb300(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

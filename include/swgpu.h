@@ -149,6 +149,25 @@ int sw_get_state(sw_ctx *ctx, sw_state *out);
 /* Wait for all work queued on the context's stream. */
 int sw_sync(sw_ctx *ctx);
 
+/* Device time of the kernels of the sweeps run since the last read, from
+ * CUDA events recorded around them.  (Measurement support: the paper's
+ * per-step timings, Sec. II.C, have no other counterpart here.) */
+typedef struct {
+    int64_t tile_launches; /* launches of the tile kernel                   */
+    double tile_ms;        /* their summed device time                      */
+    int64_t merge_groups;  /* launch groups (a group = the three merge kernels) */
+    double merge_ms;       /* summed device time of the merge groups         */
+    int64_t tile_sites;    /* L*L                                            */
+    int32_t tile_height;   /* rows per tile (tiles are 128 sites wide)       */
+} sw_kernel_stats;
+
+/* enable != 0: later sweeps are launched one kernel at a time (not as CUDA
+ * graphs) with events around every kernel; 0 restores graph launches. */
+int sw_profile(sw_ctx *ctx, int32_t enable);
+
+/* Synchronise, return the accumulated kernel times and reset them. */
+int sw_profile_read(sw_ctx *ctx, sw_kernel_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

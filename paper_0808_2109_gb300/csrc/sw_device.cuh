@@ -384,13 +384,19 @@ __device__ __forceinline__ int gfind(int32_t *par, int x)
     return x;
 }
 
-__device__ __forceinline__ void gunite(int32_t *par, int a, int b)
+// Union of the node forest ordered by key: the root with the larger key is
+// hung under the root with the smaller one.  Keys are the global indices of
+// the pieces' local roots, distinct between pieces and equal only inside one
+// piece (whose non-representative nodes are never roots), so keys fall
+// strictly along every chain of root links (no cycle can form) and each
+// set's root carries the set's minimum key: the global cluster root.
+__device__ __forceinline__ void gunite_by_key(int32_t *par, const int32_t *key, int a, int b)
 {
     for (;;) {
         a = gfind(par, a);
         b = gfind(par, b);
         if (a == b) return;
-        if (a > b) {
+        if (key[a] > key[b]) {
             const int t = a;
             a = b;
             b = t;
@@ -811,11 +817,11 @@ __global__ void k_merge_union(const SweepArgs a)
         na = g * S + SL::BOTTOM + x;
         nb = t.g_down * S + SL::TOP + x;
     }
-    gunite(a.npar, na, nb);
+    gunite_by_key(a.npar, a.nkey, na, nb);
 }
 
-// Compress every node to its root and gather the minimum key at the root:
-// the global cluster root is its minimum site index.
+// Compress every node to its root (whose key is the cluster's minimum site
+// index) and count the clusters that touch a tile border.
 template <int TH>
 __global__ void k_merge_compress(const SweepArgs a)
 {
@@ -829,18 +835,20 @@ __global__ void k_merge_compress(const SweepArgs a)
     const int key = a.nkey[n];
     bool is_root = false;
     if ((uint32_t)key != KEY_NONE) {
-        // read-only find: the forest is fixed now, and each thread writes
-        // only its own entry, so every entry ends pointing at its root
+        // No union happens any more, so every node on the walk from n has the
+        // same root r: writing r over each of them (full path compression)
+        // can only ever store the final value, and later walks get short.
         int r = (int)n, p = gload(a.npar + r);
         while (p != r) {
             r = p;
             p = gload(a.npar + r);
         }
-        a.npar[n] = r;
-        if (r != n)
-            atomicMin(a.nkey + r, key);
-        else
-            is_root = true;
+        for (int x = (int)n; x != r;) {
+            const int nx = gload(a.npar + x);
+            *(volatile int32_t *)(a.npar + x) = r;
+            x = nx;
+        }
+        is_root = r == n;
     }
     // one root node per cluster that touches a tile border
     const uint32_t roots = __ballot_sync(__activemask(), is_root);
@@ -881,6 +889,21 @@ __global__ void k_hot_start(uint8_t *spin, int64_t N, uint32_t key0, uint32_t ke
     const U4 r = philox4x32_10((uint32_t)(i >> 7), 0u, 0u, STREAM_INIT, key0, key1);
     const int bit = (int)(i & 127);
     spin[i] = (uint8_t)((u4_word(r, bit >> 5) >> (bit & 31)) & 1u);
+}
+
+// Sets *bad if any of the n bytes is not 0 or 1.
+__global__ void k_check_spins(const uint8_t *p, int64_t n, int32_t *bad)
+{
+    int found = 0;
+    const int64_t n16 = n / 16;
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 v = q[i];
+        found |= ((v.x | v.y | v.z | v.w) & 0xFEFEFEFEu) != 0u;
+    }
+    for (int64_t i = n16 * 16 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        found |= p[i] > 1;
+    if (__syncthreads_or(found) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
 // Bond bits of the last sweep (tile-major words) -> row-major bond bytes.

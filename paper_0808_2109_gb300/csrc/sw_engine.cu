@@ -146,6 +146,14 @@ struct sw_ctx {
 
     Replica rep{};
     std::map<int, cudaGraphExec_t> graphs;
+
+    // opt-in per-kernel timing (launches without graphs)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;      // events owned by the context
+    std::vector<cudaEvent_t> ev_marks;     // per launch group: tile start, tile end, merge end
+    size_t ev_used = 0;
+    int64_t prof_groups = 0;
+    double prof_tile_ms = 0.0, prof_merge_ms = 0.0;
 };
 
 namespace {
@@ -156,6 +164,8 @@ void ctx_free(sw_ctx *c)
     cudaSetDevice(c->dev);
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
     void *ptrs[] = {c->spin, c->label, c->code, c->bondbits, c->cross, c->npar, c->nkey,
                     c->nfinal, c->thr_dev, c->rep_dev, c->tile_rep, c->jbase, c->bond_bytes, c->obs};
     for (void *p : ptrs)
@@ -307,6 +317,73 @@ int graph_for(sw_ctx *c, int m, cudaGraphExec_t *out)
     return SW_OK;
 }
 
+cudaError_t next_event(sw_ctx *c, cudaEvent_t *ev)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        c->ev_pool.push_back(e);
+    }
+    *ev = c->ev_pool[c->ev_used++];
+    return cudaSuccess;
+}
+
+// Profiling mode: the same launch groups, enqueued one by one, the tile
+// kernel and the three merge kernels of every group bracketed by events.
+int enqueue_profiled(sw_ctx *c, int32_t n)
+{
+    int32_t zero = 0;
+    SW_CUDA(cudaMemcpyAsync(c->jbase, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    SweepArgs a = args_of(c);
+    for (int j = 0; j <= n; ++j) {
+        cudaEvent_t e0, e1, e2;
+        SW_CUDA(next_event(c, &e0));
+        SW_CUDA(next_event(c, &e1));
+        SW_CUDA(next_event(c, &e2));
+        a.j = j;
+        SW_CUDA(cudaEventRecord(e0, c->stream));
+        switch (c->TH) {
+        case 32: k_tile<32><<<a.n_tiles, TileCfg<32>::NT, tile_smem_bytes<32>(), c->stream>>>(a); break;
+        case 64: k_tile<64><<<a.n_tiles, TileCfg<64>::NT, tile_smem_bytes<64>(), c->stream>>>(a); break;
+        default: k_tile<128><<<a.n_tiles, TileCfg<128>::NT, tile_smem_bytes<128>(), c->stream>>>(a); break;
+        }
+        SW_CUDA(cudaGetLastError());
+        SW_CUDA(cudaEventRecord(e1, c->stream));
+        if (j < n) {
+            // the merge kernels of group j (enqueue_launch minus its tile kernel)
+            const int TH = c->TH;
+            const int64_t nu = (int64_t)a.n_tiles * (TH + TW);
+            const int64_t nn = (int64_t)a.n_tiles * c->S;
+            const unsigned bu = (unsigned)((nu + MERGE_THREADS - 1) / MERGE_THREADS);
+            const unsigned bn = (unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS);
+            switch (TH) {
+            case 32:
+                k_merge_union<32><<<bu, MERGE_THREADS, 0, c->stream>>>(a);
+                k_merge_compress<32><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
+                k_merge_final<32><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
+                break;
+            case 64:
+                k_merge_union<64><<<bu, MERGE_THREADS, 0, c->stream>>>(a);
+                k_merge_compress<64><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
+                k_merge_final<64><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
+                break;
+            default:
+                k_merge_union<128><<<bu, MERGE_THREADS, 0, c->stream>>>(a);
+                k_merge_compress<128><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
+                k_merge_final<128><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
+                break;
+            }
+            SW_CUDA(cudaGetLastError());
+        }
+        SW_CUDA(cudaEventRecord(e2, c->stream));
+        c->ev_marks.push_back(e0);
+        c->ev_marks.push_back(e1);
+        c->ev_marks.push_back(e2);
+    }
+    return SW_OK;
+}
+
 int run_sweeps(sw_ctx *c, int32_t n)
 {
     if (n < 0) return SW_ERR_ARG;
@@ -321,6 +398,14 @@ int run_sweeps(sw_ctx *c, int32_t n)
     R.obs = c->obs + c->obs_tail;
     SW_CUDA(cudaMemcpyAsync(c->rep_dev, &R, sizeof(Replica), cudaMemcpyHostToDevice, c->stream));
     SW_CUDA(cudaMemsetAsync(R.obs, 0, (size_t)n * sizeof(DevObs), c->stream));
+    if (c->profiling) {
+        rc = enqueue_profiled(c, n);
+        if (rc != SW_OK) return rc;
+        c->obs_tail += n;
+        c->sweep += (uint64_t)n;
+        c->swept = true;
+        return SW_OK;
+    }
     // n + 1 tile launches (j = 0..n), in graph chunks of at most MAX_CHUNK
     int64_t done = 0;
     const int64_t total = (int64_t)n + 1;
@@ -474,11 +559,54 @@ int sw_set_spins(sw_ctx *ctx, const uint8_t *host_in)
 {
     if (!ctx || !host_in) return SW_ERR_ARG;
     const size_t N = (size_t)ctx->L * ctx->L;
-    for (size_t i = 0; i < N; ++i)
-        if (host_in[i] > 1) return SW_ERR_ARG;
     SW_CUDA(cudaSetDevice(ctx->dev));
-    SW_CUDA(cudaMemcpyAsync(ctx->spin, host_in, N, cudaMemcpyHostToDevice, ctx->stream));
+    // Stage in the site-code buffer (free between calls; at least N bytes),
+    // check every byte on the device, and only then replace the spins.
+    uint8_t *stage = reinterpret_cast<uint8_t *>(ctx->code);
+    int32_t *bad = ctx->jbase;   // scratch word, rewritten by every sweep call
+    SW_CUDA(cudaMemcpyAsync(stage, host_in, N, cudaMemcpyHostToDevice, ctx->stream));
+    SW_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), ctx->stream));
+    k_check_spins<<<(unsigned)std::min<size_t>((N + 4095) / 4096, 4096), 256, 0, ctx->stream>>>(stage, (int64_t)N, bad);
+    SW_CUDA(cudaGetLastError());
+    int32_t hbad = 0;
+    SW_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (hbad) return SW_ERR_ARG;
+    SW_CUDA(cudaMemcpyAsync(ctx->spin, stage, N, cudaMemcpyDeviceToDevice, ctx->stream));
+    SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SW_OK;
+}
+
+int sw_profile(sw_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return SW_ERR_ARG;
+    ctx->profiling = enable != 0;
+    return SW_OK;
+}
+
+int sw_profile_read(sw_ctx *ctx, sw_kernel_stats *out)
+{
+    if (!ctx || !out) return SW_ERR_ARG;
+    SW_CUDA(cudaSetDevice(ctx->dev));
+    SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i + 2 < ctx->ev_marks.size(); i += 3) {
+        float t = 0.f, m = 0.f;
+        SW_CUDA(cudaEventElapsedTime(&t, ctx->ev_marks[i], ctx->ev_marks[i + 1]));
+        SW_CUDA(cudaEventElapsedTime(&m, ctx->ev_marks[i + 1], ctx->ev_marks[i + 2]));
+        ctx->prof_tile_ms += t;
+        ctx->prof_merge_ms += m;
+        ctx->prof_groups += 1;
+    }
+    ctx->ev_marks.clear();
+    ctx->ev_used = 0;
+    out->tile_launches = ctx->prof_groups;
+    out->tile_ms = ctx->prof_tile_ms;
+    out->merge_groups = ctx->prof_groups;
+    out->merge_ms = ctx->prof_merge_ms;
+    out->tile_sites = (int64_t)ctx->L * ctx->L;
+    out->tile_height = ctx->TH;
+    ctx->prof_groups = 0;
+    ctx->prof_tile_ms = ctx->prof_merge_ms = 0.0;
     return SW_OK;
 }
 

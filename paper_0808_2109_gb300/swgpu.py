@@ -44,6 +44,17 @@ class SwState(ctypes.Structure):
     ]
 
 
+class SwKernelStats(ctypes.Structure):
+    _fields_ = [
+        ("tile_launches", ctypes.c_int64),
+        ("tile_ms", ctypes.c_double),
+        ("merge_groups", ctypes.c_int64),
+        ("merge_ms", ctypes.c_double),
+        ("tile_sites", ctypes.c_int64),
+        ("tile_height", ctypes.c_int32),
+    ]
+
+
 class SwError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -73,6 +84,8 @@ SIGNATURES = {
     "sw_get_bonds": ([_P, _P], ctypes.c_int),
     "sw_get_state": ([_P, _P], ctypes.c_int),
     "sw_sync": ([_P], ctypes.c_int),
+    "sw_profile": ([_P, _i32], ctypes.c_int),
+    "sw_profile_read": ([_P, _P], ctypes.c_int),
 }
 
 
@@ -200,6 +213,16 @@ def sw_sync(h) -> None:
     _check(lib().sw_sync(h), "sw_sync")
 
 
+def sw_profile(h, enable: bool) -> None:
+    _check(lib().sw_profile(h, 1 if enable else 0), "sw_profile")
+
+
+def sw_profile_read(h) -> dict:
+    st = SwKernelStats()
+    _check(lib().sw_profile_read(h, ctypes.byref(st)), "sw_profile_read")
+    return {f: getattr(st, f) for f, _ in SwKernelStats._fields_}
+
+
 # -------------------------------------------------------------- convenience
 
 class Lattice:
@@ -261,3 +284,9 @@ class Lattice:
 
     def sync(self):
         sw_sync(self.h)
+
+    def profile(self, enable: bool = True):
+        sw_profile(self.h, enable)
+
+    def profile_read(self) -> dict:
+        return sw_profile_read(self.h)
