@@ -33,6 +33,7 @@ METRIC = "SW site updates/ns at T_c (L=16384)"
 UNIT = "site-updates/ns"
 WIDE_MULS_PER_PHILOX = 20          # 10 rounds x 2 (32x32->64) products
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_tile_L16384_Tc.md")
+MERGE_JUMPS = 3                    # pointer-jumping launches per sweep in the merge
 
 
 def parse_args():
@@ -291,7 +292,7 @@ def run_gb300(args):
             "config": workload_config(w, {"parallelism": f"replicas x{world}",
                                           "seeds": f"{w.seed}..{w.seed + world - 1}"}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": K * (4 * w.sweeps + 1),
+            "gpu_launches": K * ((4 + MERGE_JUMPS) * w.sweeps + 1),
             "clocks": clk, "impl": "gb300",
         }
     lat.close()

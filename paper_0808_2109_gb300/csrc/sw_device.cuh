@@ -22,6 +22,7 @@
 // the SM boundary; spins stay in shared memory from one sweep to the next.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 
 namespace swg {
@@ -71,6 +72,10 @@ struct Replica {
     int32_t *label;         // L*L labels of the last sweep (written at j = nsweeps)
     uint8_t *bond;          // unused by the kernels (host bookkeeping)
     DevObs *obs;            // nsweeps entries
+    // PCC scratch (Sec. III): spanning candidates and their coverage
+    int32_t *cand;          // [2][L] candidate roots (x, then y)
+    int32_t *ncand;         // [2] candidate counts
+    uint32_t *cov;          // [L][tiles_x][4] column coverage, then [L][tiles_y][4] row coverage
 };
 
 // Buffers shared by all tiles of a launch (indexed by the global tile g).
@@ -86,6 +91,9 @@ struct SweepArgs {
     int32_t *npar;              // n_tiles * S node parents
     int32_t *nkey;              // n_tiles * S node keys (global root candidates)
     uint32_t *nfinal;           // n_tiles * S resolved (root | spin << 30)
+    // PCC only (null otherwise), indexed by node:
+    uint32_t *pmask;            // n_tiles * S * 8: a piece's column mask (4 words), row mask (4 words)
+    int32_t *cid;               // n_tiles * S * 2: candidate id + 2 of a root node (x, y), 0 = none
 };
 
 // ------------------------------------------------------------------ Philox
@@ -442,7 +450,16 @@ struct TileSmem {
     uint32_t spb[TH][8];            // SPIN-stream blocks covering each row
     uint32_t finfo[Slots<TH>::S];   // resolved finals of the tile's own nodes
     long long red[TileCfg<TH>::NW][4];
+    uint32_t pm[Slots<TH>::S][8];   // PCC: per border piece, columns and rows it occupies
 };
+
+// Dynamic shared memory of a tile launch: the piece masks only when a PCC
+// lattice takes part.
+template <int TH>
+constexpr size_t tile_smem(bool pcc)
+{
+    return pcc ? sizeof(TileSmem<TH>) : offsetof(TileSmem<TH>, pm);
+}
 
 // ----------------------------------------------------------------- k_tile
 template <int TH>
@@ -590,6 +607,9 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
         }
         __syncthreads();
     }
+    const bool pcc = (R.flags & RF_PCC) != 0;
+    if (pcc)
+        for (int q = tid; q < S * 8; q += NT) (&sm.pm[0][0])[q] = 0u;
     if (t.lt == 0 && tid == 0) {
         R.obs[j].threshold = thr;
         R.obs[j].spans_x = 0;
@@ -772,6 +792,8 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
         const int c = xb >> 5;
         const uint32_t heads = run_heads(sm.ih[y][c]);
         const int base = y * PW + 32 * c;
+        int slot = -1;            // PCC: border piece of the sites gathered in cols
+        uint32_t cols = 0u;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int x = xb + e;
@@ -779,8 +801,30 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
             const int v = sm.par[head_of(heads, base, x & 31)];
             const int info = (v < 0 || (uint32_t)v >= INFO_INTERIOR) ? v : sm.par[v];
             wv[e >> 1] |= ((uint32_t)info & 0xFFFFu) << (16 * (e & 1));
+            if (pcc && info < 0) {
+                // the columns and rows each border piece occupies (only a
+                // piece touching the border can belong to a spanning cluster)
+                const int sl = info & 0x3FF;
+                if (sl != slot) {
+                    if (slot >= 0) {
+                        atomicOr(&sm.pm[slot][c], cols);
+                        atomicOr(&sm.pm[slot][4 + (y >> 5)], 1u << (y & 31));
+                    }
+                    slot = sl;
+                    cols = 0u;
+                }
+                cols |= 1u << (x & 31);
+            }
+        }
+        if (slot >= 0) {
+            atomicOr(&sm.pm[slot][c], cols);
+            atomicOr(&sm.pm[slot][4 + (y >> 5)], 1u << (y & 31));
         }
         code4[idx] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    if (pcc) {
+        __syncthreads();
+        for (int q = tid; q < S * 8; q += NT) a.pmask[(size_t)g * S * 8 + q] = (&sm.pm[0][0])[q];
     }
     long long v4[4] = {nb, ncl_interior, 0, 0};
     DevObs *o = R.obs + j;
@@ -818,6 +862,22 @@ __global__ void k_merge_union(const SweepArgs a)
         nb = t.g_down * S + SL::TOP + x;
     }
     gunite_by_key(a.npar, a.nkey, na, nb);
+}
+
+// One round of pointer jumping over the node forest (every parent replaced
+// by its grandparent): a few rounds between the unions and the compression
+// cut the depth of the chains that unions across many tiles leave behind.
+template <int TH>
+__global__ void k_merge_jump(const SweepArgs a)
+{
+    constexpr int S = Slots<TH>::S;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (int64_t)a.n_tiles * S) return;
+    const Replica &R = a.reps[a.tile_rep[n / S]];
+    if (!(a.j + *a.jbase < R.nsweeps)) return;
+    const int p = gload(a.npar + n);
+    const int gp = gload(a.npar + p);
+    if (gp != p) *(volatile int32_t *)(a.npar + n) = gp;
 }
 
 // Compress every node to its root (whose key is the cluster's minimum site
@@ -878,6 +938,145 @@ __global__ void k_merge_final(const SweepArgs a)
     const int bit = root & 127;
     const uint32_t spin = (u4_word(r, bit >> 5) >> (bit & 31)) & 1u;
     a.nfinal[n] = root | (spin ? FINAL_SPIN : 0u);
+}
+
+// ------------------------------------------------------------------- PCC
+// Extension rule under periodic boundaries (Sec. III): a cluster spans x
+// iff its projection on the x axis, the range P_x(C), is all of [0, L-1],
+// i.e. iff it occupies every column (likewise y and rows).  Each tile
+// recorded, per border piece, the columns and rows it occupies; here the
+// pieces of one global cluster are united (the paper's update of P_x on a
+// merge) as bit sets per tile column (tile row).
+//
+// Step 1: candidates.  A cluster occupying every column holds a site of
+// column 0, on the left edge of a tile of tile column 0; one occupying every
+// row holds a site of row 0, on the top edge of a tile of tile row 0.  Those
+// edge nodes' roots get compact candidate ids (cid = id + 2).
+template <int TH>
+__global__ void k_pcc_candidates(const SweepArgs a)
+{
+    using SL = Slots<TH>;
+    constexpr int S = SL::S;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)a.n_tiles * (TH + TW)) return;
+    const int g = (int)(idx / (TH + TW));
+    const int e = (int)(idx % (TH + TW));
+    const Replica &R = a.reps[a.tile_rep[g]];
+    if (!(R.flags & RF_PCC) || !(a.j + *a.jbase < R.nsweeps)) return;
+    const Tile t = tile_of(R, g, TH);
+    int axis, node;
+    if (e < TH) {
+        if (t.tx != 0 || e >= t.th) return;
+        axis = 0;
+        node = g * S + SL::LEFT + e;
+    } else {
+        const int x = e - TH;
+        if (t.ty != 0 || x >= t.tw) return;
+        axis = 1;
+        node = g * S + SL::TOP + x;
+    }
+    const int r = gload(a.npar + node);
+    int32_t *c = a.cid + (size_t)r * 2 + axis;
+    if (atomicCAS(c, 0, 1) == 0) {
+        const int id = atomicAdd(R.ncand + axis, 1);   // < L: at most one per edge site
+        R.cand[axis * R.L + id] = r;
+        *(volatile int32_t *)c = id + 2;
+    }
+}
+
+// Step 2: every border piece ORs the columns (rows) it occupies into its
+// candidate cluster's coverage of the piece's tile column (tile row).
+template <int TH>
+__global__ void k_pcc_cover(const SweepArgs a)
+{
+    constexpr int S = Slots<TH>::S;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (int64_t)a.n_tiles * S) return;
+    const int g = (int)(n / S);
+    const Replica &R = a.reps[a.tile_rep[g]];
+    if (!(R.flags & RF_PCC) || !(a.j + *a.jbase < R.nsweeps)) return;
+    const uint4 *pm4 = reinterpret_cast<const uint4 *>(a.pmask + (size_t)n * 8);
+    const uint4 c4 = pm4[0], r4 = pm4[1];
+    if (!(c4.x | c4.y | c4.z | c4.w | r4.x | r4.y | r4.z | r4.w)) return;
+    const int r = gload(a.npar + n);
+    const Tile t = tile_of(R, g, TH);
+    const int cx = a.cid[(size_t)r * 2 + 0], cy = a.cid[(size_t)r * 2 + 1];
+    if (cx >= 2) {
+        uint32_t *cov = R.cov + ((size_t)(cx - 2) * R.tiles_x + t.tx) * 4;
+        const uint32_t w[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (w[q]) atomicOr(cov + q, w[q]);
+    }
+    if (cy >= 2) {
+        uint32_t *cov = R.cov + (size_t)R.L * R.tiles_x * 4 + ((size_t)(cy - 2) * R.tiles_y + t.ty) * 4;
+        const uint32_t w[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (w[q]) atomicOr(cov + q, w[q]);
+    }
+}
+
+// Step 3 (one block per lattice): a candidate spans x iff its coverage of
+// every tile column is that column's full mask (P_x(C) = [0, L-1]); y alike.
+// Record the flags, apply the PCC feedback to the threshold for the next
+// sweep -- down by delta_k if the clusters percolate, up otherwise, delta_k =
+// 2^(32 - min(8 + floor(k/1000), 20)), clamped to [0, 2^32] -- and clear the
+// scratch.
+template <int TH>
+__global__ void k_pcc_decide(const SweepArgs a, int n_reps)
+{
+    const int rr = blockIdx.x;
+    if (rr >= n_reps) return;
+    const Replica &R = a.reps[rr];
+    const int j = a.j + *a.jbase;
+    if (!(R.flags & RF_PCC) || !(j < R.nsweeps)) return;
+    const int nx = R.ncand[0], ny = R.ncand[1];
+    const uint32_t *covx = R.cov;
+    const uint32_t *covy = R.cov + (size_t)R.L * R.tiles_x * 4;
+    int sx = 0, sy = 0;
+    for (int id = threadIdx.x; id < nx; id += blockDim.x) {
+        bool full = true;
+        for (int tx = 0; tx < R.tiles_x && full; ++tx) {
+            const int tw = min(TW, R.L - TW * tx);
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t m = valid_mask(q, tw);
+                full &= (covx[((size_t)id * R.tiles_x + tx) * 4 + q] & m) == m;
+            }
+        }
+        sx |= full;
+    }
+    for (int id = threadIdx.x; id < ny; id += blockDim.x) {
+        bool full = true;
+        for (int ty = 0; ty < R.tiles_y && full; ++ty) {
+            const int th = min(TH, R.L - TH * ty);
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t m = valid_mask(q, th);
+                full &= (covy[((size_t)id * R.tiles_y + ty) * 4 + q] & m) == m;
+            }
+        }
+        sy |= full;
+    }
+    sx = __syncthreads_or(sx);
+    sy = __syncthreads_or(sy);
+    for (int64_t q = threadIdx.x; q < (int64_t)nx * R.tiles_x * 4; q += blockDim.x) R.cov[q] = 0u;
+    for (int64_t q = threadIdx.x; q < (int64_t)ny * R.tiles_y * 4; q += blockDim.x)
+        R.cov[(size_t)R.L * R.tiles_x * 4 + q] = 0u;
+    for (int id = threadIdx.x; id < nx; id += blockDim.x) a.cid[(size_t)R.cand[id] * 2 + 0] = 0;
+    for (int id = threadIdx.x; id < ny; id += blockDim.x) a.cid[(size_t)R.cand[R.L + id] * 2 + 1] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R.obs[j].spans_x = sx;
+        R.obs[j].spans_y = sy;
+        const uint64_t k = R.sweep0 + (uint64_t)j;
+        const uint64_t e = 8 + k / 1000;
+        const uint64_t delta = (uint64_t)1 << (32 - (e < 20 ? e : 20));
+        const uint64_t top = (uint64_t)1 << 32;
+        const uint64_t t = *R.thr_dev;
+        *R.thr_dev = (sx || sy) ? (t > delta ? t - delta : 0) : (t + delta < top ? t + delta : top);
+        R.ncand[0] = 0;
+        R.ncand[1] = 0;
+    }
 }
 
 // ------------------------------------------------------------ small kernels

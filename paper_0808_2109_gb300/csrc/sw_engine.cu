@@ -20,6 +20,7 @@ namespace {
 
 constexpr int MAX_CHUNK = 512;   // launches per captured graph
 constexpr int MERGE_THREADS = 256;
+constexpr int MERGE_JUMPS = 3;     // pointer-jumping rounds between unions and compression
 
 #define SW_CUDA(call)                                   \
     do {                                                \
@@ -37,46 +38,72 @@ int sw_cuda_fail(cudaError_t e)
 }
 
 template <int TH>
-size_t tile_smem_bytes()
-{
-    return sizeof(TileSmem<TH>);
-}
-
-template <int TH>
 cudaError_t tile_prepare()
 {
     static bool done = false;
     static cudaError_t err = cudaSuccess;
     if (!done) {
         err = cudaFuncSetAttribute(k_tile<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)tile_smem_bytes<TH>());
+                                   (int)tile_smem<TH>(true));
         done = true;
     }
     return err;
 }
 
-// One launch group: the tile kernel of launch j and, while sweep j is
-// running, the three merge kernels.
 template <int TH>
-cudaError_t enqueue_launch(const SweepArgs &a, cudaStream_t st)
+void launch_tile(const SweepArgs &a, bool pcc, cudaStream_t st)
+{
+    k_tile<TH><<<a.n_tiles, TileCfg<TH>::NT, tile_smem<TH>(pcc), st>>>(a);
+}
+
+// The merge of launch group j: unions across tile edges, pointer jumping,
+// compression; for PCC lattices the span test and the feedback; then every
+// node's resolved root and new spin.
+template <int TH>
+void launch_merge(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
 {
     constexpr int S = Slots<TH>::S;
-    k_tile<TH><<<a.n_tiles, TileCfg<TH>::NT, tile_smem_bytes<TH>(), st>>>(a);
     const int64_t nu = (int64_t)a.n_tiles * (TH + TW);
     const int64_t nn = (int64_t)a.n_tiles * S;
-    k_merge_union<TH><<<(unsigned)((nu + MERGE_THREADS - 1) / MERGE_THREADS), MERGE_THREADS, 0, st>>>(a);
-    k_merge_compress<TH><<<(unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS), MERGE_THREADS, 0, st>>>(a);
-    k_merge_final<TH><<<(unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS), MERGE_THREADS, 0, st>>>(a);
+    const unsigned bu = (unsigned)((nu + MERGE_THREADS - 1) / MERGE_THREADS);
+    const unsigned bn = (unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS);
+    k_merge_union<TH><<<bu, MERGE_THREADS, 0, st>>>(a);
+    for (int r = 0; r < MERGE_JUMPS; ++r) k_merge_jump<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
+    k_merge_compress<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
+    if (pcc) {
+        k_pcc_candidates<TH><<<bu, MERGE_THREADS, 0, st>>>(a);
+        k_pcc_cover<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
+        k_pcc_decide<TH><<<n_reps, 256, 0, st>>>(a, n_reps);
+    }
+    k_merge_final<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
+}
+
+cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, cudaStream_t st)
+{
+    switch (TH) {
+    case 32: launch_tile<32>(a, pcc, st); break;
+    case 64: launch_tile<64>(a, pcc, st); break;
+    default: launch_tile<128>(a, pcc, st); break;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, cudaStream_t st)
+cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
 {
     switch (TH) {
-    case 32: return enqueue_launch<32>(a, st);
-    case 64: return enqueue_launch<64>(a, st);
-    default: return enqueue_launch<128>(a, st);
+    case 32: launch_merge<32>(a, pcc, n_reps, st); break;
+    case 64: launch_merge<64>(a, pcc, n_reps, st); break;
+    default: launch_merge<128>(a, pcc, n_reps, st); break;
     }
+    return cudaGetLastError();
+}
+
+// One launch group: the tile kernel of launch j, then the merge of sweep j.
+cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
+{
+    cudaError_t e = enqueue_tile(TH, a, pcc, st);
+    if (e != cudaSuccess) return e;
+    return enqueue_merge(TH, a, pcc, n_reps, st);
 }
 
 cudaError_t prepare_th(int TH)
@@ -140,6 +167,10 @@ struct sw_ctx {
     int32_t *tile_rep = nullptr;
     int32_t *jbase = nullptr;
     uint8_t *bond_bytes = nullptr;
+    // PCC scratch
+    uint32_t *pmask = nullptr;
+    int32_t *cid = nullptr, *cand = nullptr, *ncand = nullptr;
+    uint32_t *cov = nullptr;
 
     DevObs *obs = nullptr;
     int64_t obs_cap = 0, obs_head = 0, obs_tail = 0;
@@ -167,7 +198,8 @@ void ctx_free(sw_ctx *c)
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
     void *ptrs[] = {c->spin, c->label, c->code, c->bondbits, c->cross, c->npar, c->nkey,
-                    c->nfinal, c->thr_dev, c->rep_dev, c->tile_rep, c->jbase, c->bond_bytes, c->obs};
+                    c->nfinal, c->thr_dev, c->rep_dev, c->tile_rep, c->jbase, c->bond_bytes, c->obs,
+                    c->pmask, c->cid, c->cand, c->ncand, c->cov};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -189,6 +221,8 @@ SweepArgs args_of(const sw_ctx *c)
     a.npar = c->npar;
     a.nkey = c->nkey;
     a.nfinal = c->nfinal;
+    a.pmask = c->pmask;
+    a.cid = c->cid;
     return a;
 }
 
@@ -235,6 +269,17 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc)
     if ((e = dalloc(&c->tile_rep, nt)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&c->jbase, 1)) != cudaSuccess) return fail(e);
     if ((e = cudaMemsetAsync(c->tile_rep, 0, nt * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
+    if (pcc) {
+        const size_t ncov = (size_t)L * (c->tiles_x + c->tiles_y) * 4;
+        if ((e = dalloc(&c->pmask, nt * c->S * 8)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->cid, nt * c->S * 2)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->cand, (size_t)2 * L)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->ncand, 2)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->cov, ncov)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(c->cid, 0, nt * c->S * 2 * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(c->ncand, 0, 2 * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(c->cov, 0, ncov * sizeof(uint32_t), c->stream)) != cudaSuccess) return fail(e);
+    }
     if ((e = cudaMemcpyAsync(c->thr_dev, &c->thr, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
         return fail(e);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -256,6 +301,9 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc)
     R.label = c->label;
     R.bond = nullptr;
     R.obs = nullptr;
+    R.cand = c->cand;
+    R.ncand = c->ncand;
+    R.cov = c->cov;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
     *out = c;
     return SW_OK;
@@ -301,7 +349,7 @@ int graph_for(sw_ctx *c, int m, cudaGraphExec_t *out)
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < m && e == cudaSuccess; ++j) {
         a.j = j;
-        e = enqueue_launch_th(c->TH, a, c->cap_stream);
+        e = enqueue_launch_th(c->TH, a, c->pcc, 1, c->cap_stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -343,39 +391,9 @@ int enqueue_profiled(sw_ctx *c, int32_t n)
         SW_CUDA(next_event(c, &e2));
         a.j = j;
         SW_CUDA(cudaEventRecord(e0, c->stream));
-        switch (c->TH) {
-        case 32: k_tile<32><<<a.n_tiles, TileCfg<32>::NT, tile_smem_bytes<32>(), c->stream>>>(a); break;
-        case 64: k_tile<64><<<a.n_tiles, TileCfg<64>::NT, tile_smem_bytes<64>(), c->stream>>>(a); break;
-        default: k_tile<128><<<a.n_tiles, TileCfg<128>::NT, tile_smem_bytes<128>(), c->stream>>>(a); break;
-        }
-        SW_CUDA(cudaGetLastError());
+        SW_CUDA(enqueue_tile(c->TH, a, c->pcc, c->stream));
         SW_CUDA(cudaEventRecord(e1, c->stream));
-        if (j < n) {
-            // the merge kernels of group j (enqueue_launch minus its tile kernel)
-            const int TH = c->TH;
-            const int64_t nu = (int64_t)a.n_tiles * (TH + TW);
-            const int64_t nn = (int64_t)a.n_tiles * c->S;
-            const unsigned bu = (unsigned)((nu + MERGE_THREADS - 1) / MERGE_THREADS);
-            const unsigned bn = (unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS);
-            switch (TH) {
-            case 32:
-                k_merge_union<32><<<bu, MERGE_THREADS, 0, c->stream>>>(a);
-                k_merge_compress<32><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
-                k_merge_final<32><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
-                break;
-            case 64:
-                k_merge_union<64><<<bu, MERGE_THREADS, 0, c->stream>>>(a);
-                k_merge_compress<64><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
-                k_merge_final<64><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
-                break;
-            default:
-                k_merge_union<128><<<bu, MERGE_THREADS, 0, c->stream>>>(a);
-                k_merge_compress<128><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
-                k_merge_final<128><<<bn, MERGE_THREADS, 0, c->stream>>>(a);
-                break;
-            }
-            SW_CUDA(cudaGetLastError());
-        }
+        if (j < n) SW_CUDA(enqueue_merge(c->TH, a, c->pcc, 1, c->stream));
         SW_CUDA(cudaEventRecord(e2, c->stream));
         c->ev_marks.push_back(e0);
         c->ev_marks.push_back(e1);
@@ -493,10 +511,8 @@ int sw_create_p(sw_ctx **out, int32_t L, double p, uint64_t seed, uint32_t flags
 int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags)
 {
     (void)flags;
-    (void)L;
-    (void)seed;
     if (out) *out = nullptr;
-    return SW_ERR_STATE;  // built in the next step of the engine
+    return ctx_create(out, L, (uint64_t)1 << 31, seed, true);   // p = 1/2
 }
 
 int sw_destroy(sw_ctx *ctx)
