@@ -51,8 +51,13 @@ extern "C" {
 #define SW_ERR_TIMEOUT (-4)   /* a bounded device-side wait ran out            */
 #define SW_ERR_STATE (-5)     /* the call does not fit the object's state      */
 
-/* Creation flags. */
+/* Creation flags.  A tile-height flag fixes the rows per 128-site-wide tile
+ * (results do not depend on it; it trades shared memory against the number
+ * of border nodes); without one the library picks from L. */
 #define SW_FLAG_NONE 0u
+#define SW_FLAG_TILE_32 (1u << 8)
+#define SW_FLAG_TILE_64 (1u << 9)
+#define SW_FLAG_TILE_128 (1u << 10)
 
 typedef struct sw_ctx sw_ctx; /* opaque; owned by the library */
 
@@ -79,6 +84,11 @@ typedef struct {
 
 /* Name of a status code (static string). */
 const char *sw_strerror(int code);
+
+/* The CUDA runtime's description of the last CUDA failure the library saw
+ * on the calling thread ("" if none); diagnostic text for SW_ERR_CUDA and
+ * SW_ERR_NOMEM. */
+const char *sw_last_error_detail(void);
 
 /* Bond threshold of Sec. I step 1: t = floor((1 - exp(-2J/T)) * 2^32).
  * J >= 0 and T > 0 (T may be +inf); else SW_ERR_ARG. */
@@ -167,6 +177,80 @@ int sw_profile(sw_ctx *ctx, int32_t enable);
 
 /* Synchronise, return the accumulated kernel times and reset them. */
 int sw_profile_read(sw_ctx *ctx, sw_kernel_stats *out);
+
+/* ------------------------------------------------- batched and served runs
+ * Many independent lattices on one GPU at once (the paper's decompositions
+ * spread ONE lattice over processors, Sec. II; here independent lattices
+ * share the device).  A server owns a worker thread that admits submitted
+ * jobs while their device memory fits its budget, runs every admitted
+ * lattice in the same kernel launches (one tile table over all of them,
+ * captured as CUDA graphs), lets new jobs join at sweep boundaries and
+ * copies finished jobs out.  A job's results equal those of the same
+ * lattice run alone with sw_create/pcc_create and sw_sweep. */
+typedef struct sw_server sw_server;
+
+#define SW_JOB_SW 0   /* plain SW at (J, T)                  */
+#define SW_JOB_SWP 1  /* plain SW at bond probability p      */
+#define SW_JOB_PCC 2  /* PCC lattice (threshold starts at 2^31) */
+
+typedef struct {
+    int32_t L;          /* 2 <= L <= 4096                                      */
+    int32_t kind;       /* SW_JOB_*                                            */
+    double J, T, p;     /* J, T for SW_JOB_SW; p for SW_JOB_SWP                */
+    uint64_t seed;
+    int32_t nsweeps;    /* >= 1                                                */
+    int32_t tile_h;     /* 0 = autotuned, else 32, 64 or 128                   */
+    sw_obs *obs_out;    /* optional: nsweeps entries, written before completion */
+    uint8_t *spins_out; /* optional: L*L final spins                            */
+    int32_t *labels_out;/* optional: L*L labels of the last sweep               */
+} sw_job;
+/* The caller owns obs_out/spins_out/labels_out; they must stay valid until
+ * sw_batch_poll reports the job finished. */
+
+typedef struct {
+    int32_t status;         /* SW_OK, or the error that ended the job             */
+    int32_t L, nsweeps, tile_h;
+    uint64_t threshold;     /* threshold after the last sweep (PCC: fed back)     */
+    int64_t sum_bond_sum;   /* sums over the sweeps of the sw_obs fields          */
+    int64_t sum_abs_mag;
+    int64_t sum_nclusters;
+    double queued_s;        /* submit -> admitted                                 */
+    double run_s;           /* admitted -> finished                               */
+} sw_result;
+
+typedef struct {
+    int64_t submitted, admitted, finished, pending, active;
+    int64_t site_updates;   /* L*L*nsweeps summed over finished jobs              */
+    size_t bytes_in_use, bytes_budget;
+    int64_t launches;       /* launch groups run by the worker                    */
+} sw_server_stats;
+
+/* Create a server on the current device with a budget of device bytes for
+ * lattice state (0 = 80% of the free memory).  Errors: SW_ERR_NOMEM,
+ * SW_ERR_CUDA. */
+int sw_server_create(sw_server **out, size_t device_bytes, uint32_t flags);
+
+/* Stop the worker (jobs not finished are dropped) and free everything. */
+int sw_server_destroy(sw_server *srv);
+
+/* Queue n jobs; ids_out[n] receives their ids.  A job that can never run
+ * (bad arguments, or larger than the whole budget) makes the call return
+ * SW_ERR_ARG / SW_ERR_NOMEM with nothing queued. */
+int sw_batch_submit(sw_server *srv, const sw_job *jobs, int32_t n, uint64_t *ids_out);
+
+/* SW_PENDING while job `id` waits or runs; SW_OK once finished, with *out
+ * filled (the job is then forgotten); SW_ERR_ARG for an unknown id. */
+int sw_batch_poll(sw_server *srv, uint64_t id, sw_result *out);
+
+/* Block until every submitted job has finished (or timeout_s > 0 passes:
+ * SW_ERR_TIMEOUT). */
+int sw_batch_wait_all(sw_server *srv, double timeout_s);
+
+int sw_server_get_stats(sw_server *srv, sw_server_stats *out);
+
+/* Autotuner: the fastest tile height for an L x L lattice at temperature T
+ * on this GPU, timed on a short run and cached per (L, T bucket). */
+int sw_autotune(int32_t L, double T, int32_t *tile_h_out);
 
 #ifdef __cplusplus
 }

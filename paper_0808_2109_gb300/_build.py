@@ -11,7 +11,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD, "libswgpu.so")
 
-SOURCES = ["sw_engine.cu"]
+SOURCES = ["sw_engine.cu", "sw_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -23,19 +23,31 @@ def _inputs():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every CUDA source into one shared library (returns its path)."""
+    """Compile every CUDA source (in parallel) and link one shared library."""
+    from concurrent.futures import ThreadPoolExecutor
+
     os.makedirs(BUILD, exist_ok=True)
     if not force and os.path.exists(LIB_PATH):
         if os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(f) for f in _inputs()):
             return LIB_PATH
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", INCLUDE, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+    tag = f".tmp{os.getpid()}"
+    common = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        common.append("-Xptxas=-v")
+
+    def compile_one(src):
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + tag + ".o")
+        subprocess.run(common + ["-c", "-o", obj, os.path.join(CSRC, src)], check=True)
+        return obj
+
+    with ThreadPoolExecutor(len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + tag
+    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp] + objs, check=True)
     os.replace(tmp, LIB_PATH)
+    for o in objs:
+        os.remove(o)
     return LIB_PATH
 
 

@@ -72,29 +72,37 @@ struct Replica {
     int32_t *label;         // L*L labels of the last sweep (written at j = nsweeps)
     uint8_t *bond;          // unused by the kernels (host bookkeeping)
     DevObs *obs;            // nsweeps entries
-    // PCC scratch (Sec. III): spanning candidates and their coverage
+    int32_t jstart;         // launch index of this lattice's first launch
+    // per-lattice scratch, indexed by the lattice's own tiles (lt) and nodes (lt * S + slot)
+    uint16_t *code;         // tiles * TH * TW site codes
+    uint32_t *bondbits;     // tiles * TH * 8 words (last sweep of a call only)
+    uint32_t *cross;        // tiles * CROSS_WORDS
+    int32_t *npar;          // tiles * S node parents
+    int32_t *nkey;          // tiles * S node keys (global root candidates)
+    uint32_t *nfinal;       // tiles * S resolved (root | spin << 30)
+    // PCC scratch (Sec. III): spanning candidates and their coverage (null otherwise)
+    uint32_t *pmask;        // tiles * S * 8: a piece's column mask (4 words), row mask (4 words)
+    int32_t *cid;           // tiles * S * 2: candidate id + 2 of a root node (x, y), 0 = none
     int32_t *cand;          // [2][L] candidate roots (x, then y)
     int32_t *ncand;         // [2] candidate counts
     uint32_t *cov;          // [L][tiles_x][4] column coverage, then [L][tiles_y][4] row coverage
 };
 
-// Buffers shared by all tiles of a launch (indexed by the global tile g).
+// A launch: every tile of every lattice in the tile table (entries of -1
+// are idle CTAs, so a batch can keep a fixed grid while lattices come and go).
 struct SweepArgs {
     const Replica *reps;
-    const int32_t *tile_rep;    // replica of each global tile
+    const int32_t *tile_rep;    // lattice of each global tile, or -1
     int32_t n_tiles;
     int32_t j;                  // launch index within a graph chunk
     const int32_t *jbase;       // chunk offset: launch index = j + *jbase
-    uint16_t *code;             // n_tiles * TH * TW site codes
-    uint32_t *bondbits;         // n_tiles * TH * 8 words (last sweep only)
-    uint32_t *cross;            // n_tiles * CROSS_WORDS
-    int32_t *npar;              // n_tiles * S node parents
-    int32_t *nkey;              // n_tiles * S node keys (global root candidates)
-    uint32_t *nfinal;           // n_tiles * S resolved (root | spin << 30)
-    // PCC only (null otherwise), indexed by node:
-    uint32_t *pmask;            // n_tiles * S * 8: a piece's column mask (4 words), row mask (4 words)
-    int32_t *cid;               // n_tiles * S * 2: candidate id + 2 of a root node (x, y), 0 = none
 };
+
+// Launch index of a lattice: finishes its sweep j-1 and starts its sweep j.
+__device__ __forceinline__ int lattice_launch(const SweepArgs &a, const Replica &R)
+{
+    return a.j + *a.jbase - R.jstart;
+}
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -163,7 +171,7 @@ __device__ __forceinline__ uint32_t valid_mask(int c, int tw)
 
 // ------------------------------------------------------------ tile geometry
 struct Tile {
-    int g, lt, tx, ty, x0, y0, tw, th, g_right, g_down;
+    int g, lt, tx, ty, x0, y0, tw, th, g_right, g_down;   // lt, g_right, g_down: the lattice's own tiles
 };
 
 __device__ __forceinline__ Tile tile_of(const Replica &R, int g, int TH)
@@ -177,8 +185,8 @@ __device__ __forceinline__ Tile tile_of(const Replica &R, int g, int TH)
     t.y0 = t.ty * TH;
     t.tw = min(TW, R.L - t.x0);
     t.th = min(TH, R.L - t.y0);
-    t.g_right = R.tile_base + t.ty * R.tiles_x + (t.tx + 1) % R.tiles_x;
-    t.g_down = R.tile_base + ((t.ty + 1) % R.tiles_y) * R.tiles_x + t.tx;
+    t.g_right = t.ty * R.tiles_x + (t.tx + 1) % R.tiles_x;        // local tile indices
+    t.g_down = ((t.ty + 1) % R.tiles_y) * R.tiles_x + t.tx;
     return t;
 }
 
@@ -478,8 +486,11 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
 
     const int g = blockIdx.x;
     if (g >= a.n_tiles) return;
-    const Replica &R = a.reps[a.tile_rep[g]];
-    const int j = a.j + *a.jbase;   // finishes sweep j-1, starts sweep j
+    const int ri = a.tile_rep[g];
+    if (ri < 0) return;
+    const Replica &R = a.reps[ri];
+    const int j = lattice_launch(a, R);   // finishes sweep j-1, starts sweep j
+    if (j < 0) return;
     const bool fin = j >= 1 && j <= R.nsweeps;
     const bool start = j < R.nsweeps;
     if (!fin && !start) return;
@@ -488,7 +499,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
     // site indices fit in 32 bits (N <= 2^30)
     const uint32_t uL = (uint32_t)L;
     const uint32_t gbase = (uint32_t)t.y0 * uL + (uint32_t)t.x0;   // global index of local site 0
-    uint16_t *code = a.code + (size_t)g * TH * TW;
+    uint16_t *code = R.code + (size_t)t.lt * TH * TW;
 
     if (fin) {
         // ---- finish sweep k-1: resolve every site's cluster and flip it
@@ -502,7 +513,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
             const int idx = tid + q * NT;
             cv[q] = ((idx * 8) / TW < t.th) ? code4[idx] : make_uint4(0u, 0u, 0u, 0u);
         }
-        for (int s = tid; s < S; s += NT) sm.finfo[s] = a.nfinal[(size_t)g * S + s];
+        for (int s = tid; s < S; s += NT) sm.finfo[s] = R.nfinal[(size_t)t.lt * S + s];
         for (int y = tid; y < t.th; y += NT) sm.sp[y][TWW] = 0u;
         __syncthreads();
 #pragma unroll
@@ -552,14 +563,14 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
         for (int w = warp; w < TWW + 1; w += NW) {
             const int x = 32 * w + lane;
             int spin = 0;
-            if (x < t.tw) spin = (a.nfinal[(size_t)t.g_down * S + SL::TOP + x] & FINAL_SPIN) ? 1 : 0;
+            if (x < t.tw) spin = (R.nfinal[(size_t)t.g_down * S + SL::TOP + x] & FINAL_SPIN) ? 1 : 0;
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
             if (lane == 0) sm.sp[t.th][w] = word;
         }
         __syncthreads();
         // right halo column: new spins of the left column of the tile to the right
         for (int y = tid; y < t.th; y += NT) {
-            if (a.nfinal[(size_t)t.g_right * S + SL::LEFT + y] & FINAL_SPIN)
+            if (R.nfinal[(size_t)t.g_right * S + SL::LEFT + y] & FINAL_SPIN)
                 sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
         }
         __syncthreads();
@@ -698,14 +709,14 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
             const int y = 32 * q + lane;
             const int bit = (y < t.th) ? (sm.bh[y][(t.tw - 1) >> 5] >> ((t.tw - 1) & 31)) & 1 : 0;
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
-            if (lane == 0) a.cross[(size_t)g * CROSS_WORDS + q] = word;
+            if (lane == 0) R.cross[(size_t)t.lt * CROSS_WORDS + q] = word;
         } else if (lane < TWW) {
-            a.cross[(size_t)g * CROSS_WORDS + TWW + lane] = sm.bv[t.th - 1][lane];
+            R.cross[(size_t)t.lt * CROSS_WORDS + TWW + lane] = sm.bv[t.th - 1][lane];
         }
     }
     if (j == R.nsweeps - 1) {
         // the last sweep of the call keeps its bonds for sw_get_bonds
-        uint32_t *bb = a.bondbits + (size_t)g * TH * 2 * TWW;
+        uint32_t *bb = R.bondbits + (size_t)t.lt * TH * 2 * TWW;
         for (int w = tid; w < t.th * TWW; w += NT) {
             const int y = w >> 2, c = w & 3;
             bb[y * 2 * TWW + c] = sm.bh[y][c];
@@ -738,14 +749,14 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
     for (int q = 0; q < SPT; ++q) {
         const int s = tid + q * NT;
         if (s >= S) break;
-        const size_t node = (size_t)g * S + s;
+        const size_t node = (size_t)t.lt * S + s;
         if (rs[q] >= 0) {
             const int rep = sm.par[rs[q]] & 0x3FF;
-            a.npar[node] = (int32_t)((size_t)g * S + rep);
-            a.nkey[node] = (int32_t)(gbase + (uint32_t)(rs[q] / PW) * uL + (uint32_t)(rs[q] % PW));
+            R.npar[node] = (int32_t)((size_t)t.lt * S + rep);
+            R.nkey[node] = (int32_t)(gbase + (uint32_t)(rs[q] / PW) * uL + (uint32_t)(rs[q] % PW));
         } else {
-            a.npar[node] = (int32_t)node;
-            a.nkey[node] = (int32_t)KEY_NONE;
+            R.npar[node] = (int32_t)node;
+            R.nkey[node] = (int32_t)KEY_NONE;
         }
     }
     // Every run head learns its root; every interior root gets its record
@@ -824,7 +835,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
     }
     if (pcc) {
         __syncthreads();
-        for (int q = tid; q < S * 8; q += NT) a.pmask[(size_t)g * S * 8 + q] = (&sm.pm[0][0])[q];
+        for (int q = tid; q < S * 8; q += NT) R.pmask[(size_t)t.lt * S * 8 + q] = (&sm.pm[0][0])[q];
     }
     long long v4[4] = {nb, ncl_interior, 0, 0};
     DevObs *o = R.obs + j;
@@ -844,24 +855,27 @@ __global__ void k_merge_union(const SweepArgs a)
     if (idx >= (int64_t)a.n_tiles * (TH + TW)) return;
     const int g = (int)(idx / (TH + TW));
     const int e = (int)(idx % (TH + TW));
-    const Replica &R = a.reps[a.tile_rep[g]];
-    if (!(a.j + *a.jbase < R.nsweeps)) return;
+    const int ri = a.tile_rep[g];
+    if (ri < 0) return;
+    const Replica &R = a.reps[ri];
+    const int j = lattice_launch(a, R);
+    if (j < 0 || j >= R.nsweeps) return;
     const Tile t = tile_of(R, g, TH);
     int na, nb;
     if (e < TH) {
         const int y = e;
         if (y >= t.th) return;
-        if (!((a.cross[(size_t)g * CROSS_WORDS + (y >> 5)] >> (y & 31)) & 1u)) return;
-        na = g * S + SL::RIGHT + y;
+        if (!((R.cross[(size_t)t.lt * CROSS_WORDS + (y >> 5)] >> (y & 31)) & 1u)) return;
+        na = t.lt * S + SL::RIGHT + y;
         nb = t.g_right * S + SL::LEFT + y;
     } else {
         const int x = e - TH;
         if (x >= t.tw) return;
-        if (!((a.cross[(size_t)g * CROSS_WORDS + TWW + (x >> 5)] >> (x & 31)) & 1u)) return;
-        na = g * S + SL::BOTTOM + x;
+        if (!((R.cross[(size_t)t.lt * CROSS_WORDS + TWW + (x >> 5)] >> (x & 31)) & 1u)) return;
+        na = t.lt * S + SL::BOTTOM + x;
         nb = t.g_down * S + SL::TOP + x;
     }
-    gunite_by_key(a.npar, a.nkey, na, nb);
+    gunite_by_key(R.npar, R.nkey, na, nb);
 }
 
 // One round of pointer jumping over the node forest (every parent replaced
@@ -873,11 +887,15 @@ __global__ void k_merge_jump(const SweepArgs a)
     constexpr int S = Slots<TH>::S;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (int64_t)a.n_tiles * S) return;
-    const Replica &R = a.reps[a.tile_rep[n / S]];
-    if (!(a.j + *a.jbase < R.nsweeps)) return;
-    const int p = gload(a.npar + n);
-    const int gp = gload(a.npar + p);
-    if (gp != p) *(volatile int32_t *)(a.npar + n) = gp;
+    const int ri = a.tile_rep[n / S];
+    if (ri < 0) return;
+    const Replica &R = a.reps[ri];
+    const int j = lattice_launch(a, R);
+    if (j < 0 || j >= R.nsweeps) return;
+    const int64_t nl = n - (int64_t)R.tile_base * S;   // the lattice's own node
+    const int p = gload(R.npar + nl);
+    const int gp = gload(R.npar + p);
+    if (gp != p) *(volatile int32_t *)(R.npar + nl) = gp;
 }
 
 // Compress every node to its root (whose key is the cluster's minimum site
@@ -889,26 +907,29 @@ __global__ void k_merge_compress(const SweepArgs a)
     static_assert(S % 32 == 0, "a warp's nodes must belong to one tile");
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (int64_t)a.n_tiles * S) return;
-    const int j = a.j + *a.jbase;
-    const Replica &R = a.reps[a.tile_rep[n / S]];
-    if (!(j < R.nsweeps)) return;   // uniform across the warp (one tile)
-    const int key = a.nkey[n];
+    const int ri = a.tile_rep[n / S];
+    if (ri < 0) return;                 // uniform across the warp (one tile)
+    const Replica &R = a.reps[ri];
+    const int j = lattice_launch(a, R);
+    if (j < 0 || j >= R.nsweeps) return;
+    const int nl = (int)(n - (int64_t)R.tile_base * S);   // the lattice's own node
+    const int key = R.nkey[nl];
     bool is_root = false;
     if ((uint32_t)key != KEY_NONE) {
         // No union happens any more, so every node on the walk from n has the
         // same root r: writing r over each of them (full path compression)
         // can only ever store the final value, and later walks get short.
-        int r = (int)n, p = gload(a.npar + r);
+        int r = nl, p = gload(R.npar + r);
         while (p != r) {
             r = p;
-            p = gload(a.npar + r);
+            p = gload(R.npar + r);
         }
-        for (int x = (int)n; x != r;) {
-            const int nx = gload(a.npar + x);
-            *(volatile int32_t *)(a.npar + x) = r;
+        for (int x = nl; x != r;) {
+            const int nx = gload(R.npar + x);
+            *(volatile int32_t *)(R.npar + x) = r;
             x = nx;
         }
-        is_root = r == n;
+        is_root = r == nl;
     }
     // one root node per cluster that touches a tile border
     const uint32_t roots = __ballot_sync(__activemask(), is_root);
@@ -924,20 +945,23 @@ __global__ void k_merge_final(const SweepArgs a)
     constexpr int S = Slots<TH>::S;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (int64_t)a.n_tiles * S) return;
-    const int j = a.j + *a.jbase;
-    const Replica &R = a.reps[a.tile_rep[n / S]];
-    if (!(j < R.nsweeps)) return;
-    const uint32_t key0 = (uint32_t)a.nkey[n];
+    const int ri = a.tile_rep[n / S];
+    if (ri < 0) return;
+    const Replica &R = a.reps[ri];
+    const int j = lattice_launch(a, R);
+    if (j < 0 || j >= R.nsweeps) return;
+    const int64_t nl = n - (int64_t)R.tile_base * S;   // the lattice's own node
+    const uint32_t key0 = (uint32_t)R.nkey[nl];
     if (key0 == KEY_NONE) {
-        a.nfinal[n] = 0u;
+        R.nfinal[nl] = 0u;
         return;
     }
-    const uint32_t root = (uint32_t)a.nkey[a.npar[n]];
+    const uint32_t root = (uint32_t)R.nkey[R.npar[nl]];
     const uint64_t k = R.sweep0 + (uint64_t)j;
     const U4 r = stream_block(R, root >> 7, k, STREAM_SPIN);
     const int bit = root & 127;
     const uint32_t spin = (u4_word(r, bit >> 5) >> (bit & 31)) & 1u;
-    a.nfinal[n] = root | (spin ? FINAL_SPIN : 0u);
+    R.nfinal[nl] = root | (spin ? FINAL_SPIN : 0u);
 }
 
 // ------------------------------------------------------------------- PCC
@@ -961,22 +985,25 @@ __global__ void k_pcc_candidates(const SweepArgs a)
     if (idx >= (int64_t)a.n_tiles * (TH + TW)) return;
     const int g = (int)(idx / (TH + TW));
     const int e = (int)(idx % (TH + TW));
-    const Replica &R = a.reps[a.tile_rep[g]];
-    if (!(R.flags & RF_PCC) || !(a.j + *a.jbase < R.nsweeps)) return;
+    const int ri = a.tile_rep[g];
+    if (ri < 0) return;
+    const Replica &R = a.reps[ri];
+    const int j = lattice_launch(a, R);
+    if (!(R.flags & RF_PCC) || j < 0 || j >= R.nsweeps) return;
     const Tile t = tile_of(R, g, TH);
     int axis, node;
     if (e < TH) {
         if (t.tx != 0 || e >= t.th) return;
         axis = 0;
-        node = g * S + SL::LEFT + e;
+        node = t.lt * S + SL::LEFT + e;
     } else {
         const int x = e - TH;
         if (t.ty != 0 || x >= t.tw) return;
         axis = 1;
-        node = g * S + SL::TOP + x;
+        node = t.lt * S + SL::TOP + x;
     }
-    const int r = gload(a.npar + node);
-    int32_t *c = a.cid + (size_t)r * 2 + axis;
+    const int r = gload(R.npar + node);
+    int32_t *c = R.cid + (size_t)r * 2 + axis;
     if (atomicCAS(c, 0, 1) == 0) {
         const int id = atomicAdd(R.ncand + axis, 1);   // < L: at most one per edge site
         R.cand[axis * R.L + id] = r;
@@ -993,14 +1020,18 @@ __global__ void k_pcc_cover(const SweepArgs a)
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (int64_t)a.n_tiles * S) return;
     const int g = (int)(n / S);
-    const Replica &R = a.reps[a.tile_rep[g]];
-    if (!(R.flags & RF_PCC) || !(a.j + *a.jbase < R.nsweeps)) return;
-    const uint4 *pm4 = reinterpret_cast<const uint4 *>(a.pmask + (size_t)n * 8);
+    const int ri = a.tile_rep[g];
+    if (ri < 0) return;
+    const Replica &R = a.reps[ri];
+    const int j = lattice_launch(a, R);
+    if (!(R.flags & RF_PCC) || j < 0 || j >= R.nsweeps) return;
+    const int64_t nl = n - (int64_t)R.tile_base * S;   // the lattice's own node
+    const uint4 *pm4 = reinterpret_cast<const uint4 *>(R.pmask + (size_t)nl * 8);
     const uint4 c4 = pm4[0], r4 = pm4[1];
     if (!(c4.x | c4.y | c4.z | c4.w | r4.x | r4.y | r4.z | r4.w)) return;
-    const int r = gload(a.npar + n);
+    const int r = gload(R.npar + nl);
     const Tile t = tile_of(R, g, TH);
-    const int cx = a.cid[(size_t)r * 2 + 0], cy = a.cid[(size_t)r * 2 + 1];
+    const int cx = R.cid[(size_t)r * 2 + 0], cy = R.cid[(size_t)r * 2 + 1];
     if (cx >= 2) {
         uint32_t *cov = R.cov + ((size_t)(cx - 2) * R.tiles_x + t.tx) * 4;
         const uint32_t w[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -1029,8 +1060,9 @@ __global__ void k_pcc_decide(const SweepArgs a, int n_reps)
     const int rr = blockIdx.x;
     if (rr >= n_reps) return;
     const Replica &R = a.reps[rr];
-    const int j = a.j + *a.jbase;
-    if (!(R.flags & RF_PCC) || !(j < R.nsweeps)) return;
+    if (R.L <= 0) return;                  // unused slot of a batch
+    const int j = lattice_launch(a, R);
+    if (!(R.flags & RF_PCC) || j < 0 || j >= R.nsweeps) return;
     const int nx = R.ncand[0], ny = R.ncand[1];
     const uint32_t *covx = R.cov;
     const uint32_t *covy = R.cov + (size_t)R.L * R.tiles_x * 4;
@@ -1062,8 +1094,8 @@ __global__ void k_pcc_decide(const SweepArgs a, int n_reps)
     for (int64_t q = threadIdx.x; q < (int64_t)nx * R.tiles_x * 4; q += blockDim.x) R.cov[q] = 0u;
     for (int64_t q = threadIdx.x; q < (int64_t)ny * R.tiles_y * 4; q += blockDim.x)
         R.cov[(size_t)R.L * R.tiles_x * 4 + q] = 0u;
-    for (int id = threadIdx.x; id < nx; id += blockDim.x) a.cid[(size_t)R.cand[id] * 2 + 0] = 0;
-    for (int id = threadIdx.x; id < ny; id += blockDim.x) a.cid[(size_t)R.cand[R.L + id] * 2 + 1] = 0;
+    for (int id = threadIdx.x; id < nx; id += blockDim.x) R.cid[(size_t)R.cand[id] * 2 + 0] = 0;
+    for (int id = threadIdx.x; id < ny; id += blockDim.x) R.cid[(size_t)R.cand[R.L + id] * 2 + 1] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         R.obs[j].spans_x = sx;
@@ -1081,7 +1113,7 @@ __global__ void k_pcc_decide(const SweepArgs a, int n_reps)
 
 // ------------------------------------------------------------ small kernels
 // Hot start: s_i = bit (i mod 128) of Philox(i/128, 0, INIT).
-__global__ void k_hot_start(uint8_t *spin, int64_t N, uint32_t key0, uint32_t key1)
+static __global__ void k_hot_start(uint8_t *spin, int64_t N, uint32_t key0, uint32_t key1)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -1091,7 +1123,7 @@ __global__ void k_hot_start(uint8_t *spin, int64_t N, uint32_t key0, uint32_t ke
 }
 
 // Sets *bad if any of the n bytes is not 0 or 1.
-__global__ void k_check_spins(const uint8_t *p, int64_t n, int32_t *bad)
+static __global__ void k_check_spins(const uint8_t *p, int64_t n, int32_t *bad)
 {
     int found = 0;
     const int64_t n16 = n / 16;

@@ -3,6 +3,8 @@
 // graphs.  Every step of a sweep runs in the kernels of sw_device.cuh.
 #include "swgpu.h"
 #include "sw_device.cuh"
+#include "sw_internal.h"
+#include "sw_launch.cuh"
 
 #include <cuda_runtime.h>
 
@@ -16,26 +18,8 @@
 
 using namespace swg;
 
-namespace {
-
-constexpr int MAX_CHUNK = 512;   // launches per captured graph
-constexpr int MERGE_THREADS = 256;
-constexpr int MERGE_JUMPS = 3;     // pointer-jumping rounds between unions and compression
-
-#define SW_CUDA(call)                                   \
-    do {                                                \
-        cudaError_t e_ = (call);                        \
-        if (e_ != cudaSuccess) return sw_cuda_fail(e_); \
-    } while (0)
-
-int sw_cuda_fail(cudaError_t e)
-{
-    if (e == cudaErrorMemoryAllocation) {
-        cudaGetLastError();
-        return SW_ERR_NOMEM;
-    }
-    return SW_ERR_CUDA;
-}
+// ---- the kernel launches (declared in sw_launch.cuh)
+namespace swg {
 
 template <int TH>
 cudaError_t tile_prepare()
@@ -115,16 +99,46 @@ cudaError_t prepare_th(int TH)
     }
 }
 
-int slots_of(int TH) { return 2 * TW + 2 * TH; }
-
-// Tile height used for an L x L lattice.  SWGPU_TILE_H (32, 64 or 128)
-// overrides the default for tuning runs.
-int pick_tile_height(int L)
+cudaError_t enqueue_hot_start(uint8_t *spin, int64_t N, uint64_t seed, cudaStream_t st)
 {
-    if (const char *env = std::getenv("SWGPU_TILE_H")) {
-        const int th = std::atoi(env);
-        if (th == 32 || th == 64 || th == 128) return th;
+    k_hot_start<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(spin, N, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return cudaGetLastError();
+}
+
+}  // namespace swg
+
+namespace {
+
+constexpr int MAX_CHUNK = 512;   // launches per captured graph
+
+#define SW_CUDA(call)                                             \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return sw_cuda_fail(e_, __LINE__); \
+    } while (0)
+
+thread_local cudaError_t last_cuda_error = cudaSuccess;
+thread_local int last_cuda_line = 0;
+thread_local char last_cuda_text[160];
+
+int sw_cuda_fail(cudaError_t e, int line = 0)
+{
+    last_cuda_error = e;
+    last_cuda_line = line;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return SW_ERR_NOMEM;
     }
+    return SW_ERR_CUDA;
+}
+
+// Tile height used for an L x L lattice: a SW_FLAG_TILE_* flag, else the
+// smallest height that covers short lattices, else 128.
+int pick_tile_height(int L, uint32_t flags)
+{
+    if (flags & SW_FLAG_TILE_32) return 32;
+    if (flags & SW_FLAG_TILE_64) return 64;
+    if (flags & SW_FLAG_TILE_128) return 128;
     if (L <= 32) return 32;
     if (L <= 64) return 64;
     return 128;
@@ -139,6 +153,12 @@ cudaError_t dalloc(T **p, size_t count)
 }
 
 }  // namespace
+
+std::mutex &sw_capture_mutex()
+{
+    static std::mutex m;
+    return m;
+}
 
 struct sw_ctx {
     int dev = 0;
@@ -192,6 +212,7 @@ namespace {
 void ctx_free(sw_ctx *c)
 {
     if (!c) return;
+    std::lock_guard<std::mutex> lk(sw_capture_mutex());
     cudaSetDevice(c->dev);
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
@@ -215,34 +236,29 @@ SweepArgs args_of(const sw_ctx *c)
     a.n_tiles = c->n_tiles;
     a.j = 0;
     a.jbase = c->jbase;
-    a.code = c->code;
-    a.bondbits = c->bondbits;
-    a.cross = c->cross;
-    a.npar = c->npar;
-    a.nkey = c->nkey;
-    a.nfinal = c->nfinal;
-    a.pmask = c->pmask;
-    a.cid = c->cid;
     return a;
 }
 
-int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc)
+int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, uint32_t flags)
 {
     if (!out) return SW_ERR_ARG;
     *out = nullptr;
     if (L < 2 || L > 32768) return SW_ERR_ARG;
+    cudaGetLastError();   // a stale error of an unrelated earlier call is not ours
     sw_ctx *c = new (std::nothrow) sw_ctx();
     if (!c) return SW_ERR_NOMEM;
     int rc = SW_OK;
+    std::unique_lock<std::mutex> lk(sw_capture_mutex());
     auto fail = [&](cudaError_t e) {
-        rc = sw_cuda_fail(e);
+        rc = sw_cuda_fail(e, __LINE__);
+        lk.unlock();
         ctx_free(c);
         return rc;
     };
     cudaError_t e = cudaGetDevice(&c->dev);
     if (e != cudaSuccess) return fail(e);
     c->L = L;
-    c->TH = pick_tile_height(L);
+    c->TH = pick_tile_height(L, flags);
     c->S = slots_of(c->TH);
     c->tiles_x = (L + TW - 1) / TW;
     c->tiles_y = (L + c->TH - 1) / c->TH;
@@ -301,10 +317,20 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc)
     R.label = c->label;
     R.bond = nullptr;
     R.obs = nullptr;
+    R.jstart = 0;
+    R.code = c->code;
+    R.bondbits = c->bondbits;
+    R.cross = c->cross;
+    R.npar = c->npar;
+    R.nkey = c->nkey;
+    R.nfinal = c->nfinal;
+    R.pmask = c->pmask;
+    R.cid = c->cid;
     R.cand = c->cand;
     R.ncand = c->ncand;
     R.cov = c->cov;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
+    lk.unlock();
     *out = c;
     return SW_OK;
 }
@@ -317,6 +343,7 @@ int ensure_obs(sw_ctx *c, int64_t n)
     int64_t cap = c->obs_cap ? c->obs_cap : 64;
     while (cap < pending + n) cap *= 2;
     DevObs *nb = nullptr;
+    std::lock_guard<std::mutex> lk(sw_capture_mutex());
     SW_CUDA(dalloc(&nb, (size_t)cap));
     if (pending > 0) {
         cudaError_t e = cudaMemcpyAsync(nb, c->obs + c->obs_head, pending * sizeof(DevObs),
@@ -344,6 +371,7 @@ int graph_for(sw_ctx *c, int m, cudaGraphExec_t *out)
         return SW_OK;
     }
     cudaGraph_t g = nullptr;
+    std::lock_guard<std::mutex> lk(sw_capture_mutex());
     SW_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     SweepArgs a = args_of(c);
     cudaError_t e = cudaSuccess;
@@ -407,6 +435,7 @@ int run_sweeps(sw_ctx *c, int32_t n)
     if (n < 0) return SW_ERR_ARG;
     if (n == 0) return SW_OK;
     SW_CUDA(cudaSetDevice(c->dev));
+    cudaGetLastError();   // a stale error of an unrelated earlier call is not ours
     int rc = ensure_obs(c, n);
     if (rc != SW_OK) return rc;
     Replica &R = c->rep;
@@ -433,8 +462,18 @@ int run_sweeps(sw_ctx *c, int32_t n)
         SW_CUDA(cudaMemcpyAsync(c->jbase, &jb, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
         cudaGraphExec_t ex = nullptr;
         rc = graph_for(c, m, &ex);
-        if (rc != SW_OK) return rc;
-        SW_CUDA(cudaGraphLaunch(ex, c->stream));
+        if (rc == SW_OK) {
+            SW_CUDA(cudaGraphLaunch(ex, c->stream));
+        } else {
+            // capture refused (e.g. invalidated by another thread): the same
+            // launch groups, enqueued directly
+            cudaGetLastError();
+            SweepArgs a = args_of(c);
+            for (int j = 0; j < m; ++j) {
+                a.j = j;
+                SW_CUDA(enqueue_launch_th(c->TH, a, c->pcc, 1, c->stream));
+            }
+        }
         done += m;
     }
     c->obs_tail += n;
@@ -462,6 +501,14 @@ const char *sw_strerror(int code)
     }
 }
 
+const char *sw_last_error_detail(void)
+{
+    if (last_cuda_error == cudaSuccess) return "";
+    std::snprintf(last_cuda_text, sizeof(last_cuda_text), "%s (sw_engine.cu:%d)",
+                  cudaGetErrorString(last_cuda_error), last_cuda_line);
+    return last_cuda_text;
+}
+
 int sw_threshold(double J, double T, uint64_t *out)
 {
     if (!out || !(J >= 0.0) || !(T > 0.0)) return SW_ERR_ARG;
@@ -476,7 +523,7 @@ int sw_threshold(double J, double T, uint64_t *out)
     return SW_OK;
 }
 
-static int threshold_of_p(double p, uint64_t *out)
+int sw_threshold_p_internal(double p, uint64_t *out)
 {
     if (!(p >= 0.0) || !(p <= 1.0)) return SW_ERR_ARG;
     if (p == 0.0)
@@ -490,29 +537,26 @@ static int threshold_of_p(double p, uint64_t *out)
 
 int sw_create(sw_ctx **out, int32_t L, double J, double T, uint64_t seed, uint32_t flags)
 {
-    (void)flags;
     if (out) *out = nullptr;
     uint64_t thr = 0;
     int rc = sw_threshold(J, T, &thr);
     if (rc != SW_OK) return rc;
-    return ctx_create(out, L, thr, seed, false);
+    return ctx_create(out, L, thr, seed, false, flags);
 }
 
 int sw_create_p(sw_ctx **out, int32_t L, double p, uint64_t seed, uint32_t flags)
 {
-    (void)flags;
     if (out) *out = nullptr;
     uint64_t thr = 0;
-    int rc = threshold_of_p(p, &thr);
+    int rc = sw_threshold_p_internal(p, &thr);
     if (rc != SW_OK) return rc;
-    return ctx_create(out, L, thr, seed, false);
+    return ctx_create(out, L, thr, seed, false, flags);
 }
 
 int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags)
 {
-    (void)flags;
     if (out) *out = nullptr;
-    return ctx_create(out, L, (uint64_t)1 << 31, seed, true);   // p = 1/2
+    return ctx_create(out, L, (uint64_t)1 << 31, seed, true, flags);   // p = 1/2
 }
 
 int sw_destroy(sw_ctx *ctx)
@@ -643,7 +687,10 @@ int sw_get_bonds(sw_ctx *ctx, uint8_t *host_out)
     if (!ctx->swept) return SW_ERR_STATE;
     SW_CUDA(cudaSetDevice(ctx->dev));
     const size_t N = (size_t)ctx->L * ctx->L;
-    if (!ctx->bond_bytes) SW_CUDA(dalloc(&ctx->bond_bytes, N));
+    if (!ctx->bond_bytes) {
+        std::lock_guard<std::mutex> lk(sw_capture_mutex());
+        SW_CUDA(dalloc(&ctx->bond_bytes, N));
+    }
     const unsigned blocks = (unsigned)((N + 255) / 256);
     switch (ctx->TH) {
     case 32: k_bond_bytes<32><<<blocks, 256, 0, ctx->stream>>>(ctx->bondbits, ctx->L, ctx->tiles_x, ctx->bond_bytes); break;

@@ -1,0 +1,30 @@
+// sw_launch.cuh -- how the host enqueues the kernels of sw_device.cuh: one
+// launch group = the tile kernel of launch j, then the merge of sweep j.
+// Shared by the single-lattice engine and the batch server.
+#pragma once
+
+#include "sw_device.cuh"
+
+#include <cuda_runtime.h>
+
+namespace swg {
+
+constexpr int MERGE_THREADS = 256;
+constexpr int MERGE_JUMPS = 3;     // pointer-jumping rounds between unions and compression
+
+// Defined once, in sw_engine.cu: every kernel template is instantiated in
+// that translation unit only, so each kernel has a single module copy (and
+// the shared-memory attribute set by prepare_th applies to the copy that
+// runs).
+__attribute__((visibility("hidden"))) cudaError_t prepare_th(int TH);
+__attribute__((visibility("hidden"))) cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int n_reps,
+                                                                cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, bool pcc, int n_reps,
+                                                                    cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t enqueue_hot_start(uint8_t *spin, int64_t N, uint64_t seed,
+                                                                    cudaStream_t st);
+
+inline int slots_of(int TH) { return 2 * TW + 2 * TH; }
+
+}  // namespace swg

@@ -55,10 +55,65 @@ class SwKernelStats(ctypes.Structure):
     ]
 
 
+SW_JOB_SW, SW_JOB_SWP, SW_JOB_PCC = 0, 1, 2
+SW_FLAG_TILE = {32: 1 << 8, 64: 1 << 9, 128: 1 << 10}
+
+
+class SwJob(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int32),
+        ("kind", ctypes.c_int32),
+        ("J", ctypes.c_double),
+        ("T", ctypes.c_double),
+        ("p", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("nsweeps", ctypes.c_int32),
+        ("tile_h", ctypes.c_int32),
+        ("obs_out", ctypes.c_void_p),
+        ("spins_out", ctypes.c_void_p),
+        ("labels_out", ctypes.c_void_p),
+    ]
+
+
+class SwResult(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("L", ctypes.c_int32),
+        ("nsweeps", ctypes.c_int32),
+        ("tile_h", ctypes.c_int32),
+        ("threshold", ctypes.c_uint64),
+        ("sum_bond_sum", ctypes.c_int64),
+        ("sum_abs_mag", ctypes.c_int64),
+        ("sum_nclusters", ctypes.c_int64),
+        ("queued_s", ctypes.c_double),
+        ("run_s", ctypes.c_double),
+    ]
+
+
+class SwServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("admitted", ctypes.c_int64),
+        ("finished", ctypes.c_int64),
+        ("pending", ctypes.c_int64),
+        ("active", ctypes.c_int64),
+        ("site_updates", ctypes.c_int64),
+        ("bytes_in_use", ctypes.c_size_t),
+        ("bytes_budget", ctypes.c_size_t),
+        ("launches", ctypes.c_int64),
+    ]
+
+
 class SwError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {strerror(code)} ({code})")
+        detail = ""
+        if code in (SW_ERR_CUDA, SW_ERR_NOMEM):
+            try:
+                detail = lib().sw_last_error_detail().decode()
+            except Exception:
+                detail = ""
+        super().__init__(f"{where}: {strerror(code)} ({code})" + (f": {detail}" if detail else ""))
 
 
 _lock = threading.Lock()
@@ -69,6 +124,7 @@ _P = ctypes.c_void_p
 _i32, _u32, _i64, _u64, _dbl = ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
 SIGNATURES = {
     "sw_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "sw_last_error_detail": ([], ctypes.c_char_p),
     "sw_threshold": ([_dbl, _dbl, _P], ctypes.c_int),
     "sw_create": ([_P, _i32, _dbl, _dbl, _u64, _u32], ctypes.c_int),
     "sw_create_p": ([_P, _i32, _dbl, _u64, _u32], ctypes.c_int),
@@ -86,6 +142,13 @@ SIGNATURES = {
     "sw_sync": ([_P], ctypes.c_int),
     "sw_profile": ([_P, _i32], ctypes.c_int),
     "sw_profile_read": ([_P, _P], ctypes.c_int),
+    "sw_server_create": ([_P, ctypes.c_size_t, _u32], ctypes.c_int),
+    "sw_server_destroy": ([_P], ctypes.c_int),
+    "sw_batch_submit": ([_P, _P, _i32, _P], ctypes.c_int),
+    "sw_batch_poll": ([_P, _u64, _P], ctypes.c_int),
+    "sw_batch_wait_all": ([_P, _dbl], ctypes.c_int),
+    "sw_server_get_stats": ([_P, _P], ctypes.c_int),
+    "sw_autotune": ([_i32, _dbl, _P], ctypes.c_int),
 }
 
 
@@ -223,6 +286,49 @@ def sw_profile_read(h) -> dict:
     return {f: getattr(st, f) for f, _ in SwKernelStats._fields_}
 
 
+def sw_server_create(device_bytes: int = 0, flags: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().sw_server_create(ctypes.byref(h), device_bytes, flags), "sw_server_create")
+    return h
+
+
+def sw_server_destroy(h) -> None:
+    _check(lib().sw_server_destroy(h), "sw_server_destroy")
+
+
+def sw_batch_submit(h, jobs) -> list[int]:
+    arr = (SwJob * len(jobs))(*jobs)
+    ids = (ctypes.c_uint64 * max(len(jobs), 1))()
+    _check(lib().sw_batch_submit(h, arr, len(jobs), ids), "sw_batch_submit")
+    return [int(ids[i]) for i in range(len(jobs))]
+
+
+def sw_batch_poll(h, job_id: int):
+    """None while the job waits or runs, else its SwResult."""
+    res = SwResult()
+    rc = lib().sw_batch_poll(h, job_id, ctypes.byref(res))
+    if rc == SW_PENDING:
+        return None
+    _check(rc, "sw_batch_poll")
+    return res
+
+
+def sw_batch_wait_all(h, timeout_s: float = 0.0) -> None:
+    _check(lib().sw_batch_wait_all(h, timeout_s), "sw_batch_wait_all")
+
+
+def sw_server_get_stats(h) -> dict:
+    st = SwServerStats()
+    _check(lib().sw_server_get_stats(h, ctypes.byref(st)), "sw_server_get_stats")
+    return {f: getattr(st, f) for f, _ in SwServerStats._fields_}
+
+
+def sw_autotune(L: int, T: float) -> int:
+    out = ctypes.c_int32()
+    _check(lib().sw_autotune(L, T, ctypes.byref(out)), "sw_autotune")
+    return int(out.value)
+
+
 # -------------------------------------------------------------- convenience
 
 class Lattice:
@@ -290,3 +396,70 @@ class Lattice:
 
     def profile_read(self) -> dict:
         return sw_profile_read(self.h)
+
+
+class Server:
+    """A batch/serve server; jobs keep their output arrays alive until polled."""
+
+    def __init__(self, device_bytes: int = 0):
+        self.h = sw_server_create(device_bytes)
+        self._outputs = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            sw_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, specs, want_obs=True, want_spins=False, want_labels=False) -> list[int]:
+        """specs: dicts with L, sweeps, seed and T (plain), p, or pcc=True;
+        optional tile_h."""
+        jobs, outs = [], []
+        for sp in specs:
+            L, n = int(sp["L"]), int(sp["sweeps"])
+            o = {"obs": np.zeros(n, dtype=OBS_DTYPE) if want_obs else None,
+                 "spins": np.zeros(L * L, dtype=np.uint8) if want_spins else None,
+                 "labels": np.zeros(L * L, dtype=np.int32) if want_labels else None}
+            j = SwJob()
+            j.L, j.nsweeps, j.seed = L, n, int(sp["seed"])
+            j.J = float(sp.get("J", 1.0))
+            if sp.get("pcc"):
+                j.kind = SW_JOB_PCC
+            elif sp.get("p") is not None:
+                j.kind, j.p = SW_JOB_SWP, float(sp["p"])
+            else:
+                j.kind, j.T = SW_JOB_SW, float(sp["T"])
+            j.tile_h = int(sp.get("tile_h", 0))
+            j.obs_out = o["obs"].ctypes.data if want_obs else None
+            j.spins_out = o["spins"].ctypes.data if want_spins else None
+            j.labels_out = o["labels"].ctypes.data if want_labels else None
+            jobs.append(j)
+            outs.append(o)
+        ids = sw_batch_submit(self.h, jobs)
+        for i, o in zip(ids, outs):
+            self._outputs[i] = o
+        return ids
+
+    def poll(self, job_id: int):
+        """None while pending, else (SwResult, outputs dict)."""
+        res = sw_batch_poll(self.h, job_id)
+        if res is None:
+            return None
+        return res, self._outputs.pop(job_id)
+
+    def wait_all(self, timeout_s: float = 0.0):
+        sw_batch_wait_all(self.h, timeout_s)
+
+    def stats(self) -> dict:
+        return sw_server_get_stats(self.h)
