@@ -53,6 +53,34 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_jobs(jobs, rank: int, world: int):
+    """Independent jobs split over ranks with no exchange: largest first, each
+    to the least-loaded rank (cost = sites x sweeps); every rank computes the
+    same assignment and keeps its own share."""
+    load = [0] * world
+    mine = []
+    order = sorted(range(len(jobs)), key=lambda i: (-jobs[i].L * jobs[i].L * jobs[i].sweeps, i))
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += jobs[i].L * jobs[i].L * jobs[i].sweeps
+        if r == rank:
+            mine.append(jobs[i])
+    return mine
+
+
 def workload_config(w, extra=None):
     cfg = {"workload": f"plain SW, 2D Ising periodic L={w.L}, J=1, T={w.T}, hot start, "
                        f"{w.sweeps} sweeps per step",
@@ -218,11 +246,7 @@ def run_gb300(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1))
     obs = lat.observables()
     assert len(obs) == K * w.sweeps
     value = world * N * w.sweeps * K / (ms * 1e6)
@@ -269,11 +293,7 @@ def run_gb300(args):
         o = lat.observables()                # device -> host: per-sweep observables
         swgpu.sw_get_spins(lat.h, w.L, h_out)  # device -> host: the resulting lattice
         h_in, h_out = h_out, h_in
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": world * N * w.sweeps * e2e_steps / (e2e_s * 1e9), "unit": UNIT,
            "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + w.sweeps * 48,
            "steps": e2e_steps}
