@@ -248,6 +248,35 @@ int sw_batch_wait_all(sw_server *srv, double timeout_s);
 
 int sw_server_get_stats(sw_server *srv, sw_server_stats *out);
 
+/* ------------------------------------------------- sweep without allocation
+ * The paper has no counterpart to this call: it exists for callers that must
+ * not allocate device memory -- code running inside someone else's CUDA graph
+ * capture, inside an allocator or framework that owns all device memory, or
+ * in a latency-bound loop where cudaMalloc's implicit synchronisation is not
+ * acceptable.  It runs ONE Swendsen-Wang sweep k of an L x L lattice on
+ * caller-owned DEVICE buffers, and all its scratch memory sits in one
+ * fixed-size array inside the library (about 3 MiB per GPU, reserved on
+ * every GPU that loads the library until the process exits), so it calls no
+ * cudaMalloc or cudaFree.
+ *   spin_in   L*L spins (0/1) before the sweep
+ *   spin_out  L*L spins after the sweep (may equal spin_in)
+ *   labels_out L*L labels of the sweep (cluster roots, minimum site index)
+ *   obs_out   one sw_obs of the sweep (the call zeroes it first)
+ *   threshold the bond threshold t in [0, 2^32] (see sw_threshold)
+ *   seed, sweep  the Philox key and the sweep index k of the sweep
+ *   stream    a cudaStream_t (NULL: the legacy default stream); the call is
+ *             asynchronous on it
+ * Results equal sw_sweep on a lattice with the same spins, seed, threshold
+ * and sweep index.  L above SW_STATIC_MAX_L (or below 2), a threshold above
+ * 2^32 or a NULL buffer: SW_ERR_ARG.  The one array is shared by every call:
+ * calls that overlap on the GPU (other streams, other threads) race; run them
+ * one after another.  The first call on a device sets the array up (looks up
+ * its device address, raises a kernel's shared-memory limit): make it before
+ * any stream capture starts. */
+#define SW_STATIC_MAX_L 1024
+int sw_sweep_static(const uint8_t *spin_in, uint8_t *spin_out, int32_t *labels_out, sw_obs *obs_out,
+                    int32_t L, uint64_t threshold, uint64_t seed, uint64_t sweep, void *stream);
+
 /* Autotuner: the fastest tile height for an L x L lattice at temperature T
  * on this GPU, timed on a short run and cached per (L, T bucket). */
 int sw_autotune(int32_t L, double T, int32_t *tile_h_out);

@@ -149,6 +149,7 @@ SIGNATURES = {
     "sw_batch_wait_all": ([_P, _dbl], ctypes.c_int),
     "sw_server_get_stats": ([_P, _P], ctypes.c_int),
     "sw_autotune": ([_i32, _dbl, _P], ctypes.c_int),
+    "sw_sweep_static": ([_P, _P, _P, _P, _i32, _u64, _u64, _u64, _P], ctypes.c_int),
 }
 
 
@@ -321,6 +322,17 @@ def sw_server_get_stats(h) -> dict:
     st = SwServerStats()
     _check(lib().sw_server_get_stats(h, ctypes.byref(st)), "sw_server_get_stats")
     return {f: getattr(st, f) for f, _ in SwServerStats._fields_}
+
+
+def sw_sweep_static(spin_in: int, spin_out: int, labels_out: int, obs_out: int, L: int,
+                    threshold: int, seed: int, sweep: int, stream=None) -> None:
+    """One sweep on caller-owned device buffers (raw device addresses, e.g.
+    ``tensor.data_ptr()``) with no device allocation; see include/swgpu.h."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().sw_sweep_static(ctypes.c_void_p(spin_in), ctypes.c_void_p(spin_out),
+                                 ctypes.c_void_p(labels_out), ctypes.c_void_p(obs_out), L,
+                                 threshold, seed, sweep, ctypes.c_void_p(raw) if raw else None),
+           "sw_sweep_static")
 
 
 def sw_autotune(L: int, T: float) -> int:
