@@ -43,6 +43,11 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-solo comparison")
+    ap.add_argument("--workload", default="plain", choices=["plain", "serve"])
+    ap.add_argument("--lattice", type=int, default=0, help="profiling only: another L")
+    ap.add_argument("--sweeps", type=int, default=0, help="profiling only: sweeps per step")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     return ap.parse_args()
 
 
@@ -217,6 +222,8 @@ def run_gb300(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
     w = workloads.LARGE
+    if args.lattice or args.sweeps:
+        w = workloads.Plain(args.lattice or w.L, w.T, args.sweeps or w.sweeps, w.seed)
     K, W = args.steps, args.warmup
     N = w.L * w.L
     stream = torch.cuda.Stream()
@@ -299,6 +306,10 @@ def run_gb300(args):
            "steps": e2e_steps}
     del o
 
+    batched = None
+    if not args.no_batch and not (args.lattice or args.sweeps):
+        batched = run_batch_vs_solo(swgpu, workloads, rank, world, barrier)
+
     out = None
     if rank == 0:
         cpu = None
@@ -311,7 +322,7 @@ def run_gb300(args):
             "dtype": "u32", "data": "synthetic",
             "config": workload_config(w, {"parallelism": f"replicas x{world}",
                                           "seeds": f"{w.seed}..{w.seed + world - 1}"}),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
             "gpu_launches": K * ((4 + MERGE_JUMPS) * w.sweeps + 1),
             "clocks": clk, "impl": "gb300",
         }
@@ -319,6 +330,99 @@ def run_gb300(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
+
+
+# ------------------------------------------------------ batched vs solo
+def run_batch_vs_solo(swgpu, workloads, rank, world, barrier):
+    """The uneven 512-replica mix (500 sweeps each) through the batch server,
+    then the same replicas one at a time through sw_create/sw_sweep, on the
+    same GPU; replicas shard over ranks with no exchange."""
+    jobs = shard_jobs(workloads.batch_manifest(), rank, world)
+    specs = [{"L": j.L, "T": j.T, "sweeps": j.sweeps, "seed": j.seed} for j in jobs]
+    updates = sum(j.L * j.L * j.sweeps for j in jobs)
+    srv = swgpu.Server()
+    for L in sorted({j.L for j in jobs}):            # autotune outside the timed region
+        for T in (2.0, 2.3, 2.6):
+            swgpu.sw_autotune(L, T)
+    barrier()
+    t0 = time.perf_counter()
+    ids = srv.submit(specs, want_obs=True)
+    srv.wait_all(0.0)
+    t_batch = max_over_ranks(time.perf_counter() - t0)
+    res = [srv.poll(i) for i in ids]
+    assert all(r is not None and r[0].status == 0 for r in res)
+    stats = srv.stats()
+    srv.close()
+    barrier()
+    t0 = time.perf_counter()
+    for sp in specs:
+        lat = swgpu.Lattice(sp["L"], T=sp["T"], seed=sp["seed"])
+        lat.sweep(sp["sweeps"])
+        lat.observables()
+        lat.close()
+    t_solo = max_over_ranks(time.perf_counter() - t0)
+    total = updates * world   # equal shares by construction, up to one job
+    return {"replicas": 512, "sweeps": 500, "site_updates": int(total),
+            "value": round(total / (t_batch * 1e9), 3), "unit": UNIT,
+            "solo_value": round(total / (t_solo * 1e9), 3),
+            "speedup_vs_solo": round(t_solo / t_batch, 3),
+            "batch_s": round(t_batch, 3), "solo_s": round(t_solo, 3),
+            "launch_groups": int(stats["launches"]),
+            "timing": "wall clock from submit to last completion (host), max over ranks"}
+
+
+# ------------------------------------------------------------------- serve
+def run_serve(args):
+    """The Poisson trace replayed in real time: a client submits each job at
+    its arrival time; latency = submit -> finished (server clocks)."""
+    import torch
+    from paper_0808_2109_gb300 import _build, swgpu, workloads
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    _build.build()
+    trace = workloads.serve_trace(duration_s=args.serve_seconds)
+    for L in (32, 64, 128, 256, 512, 1024, 2048, 4096):
+        for T in (2.0, 2.3, 2.6):
+            swgpu.sw_autotune(L, T)
+    srv = swgpu.Server()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ids = []
+    t0 = time.perf_counter()
+    for job in trace:
+        delay = job.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        sp = {"L": job.L, "sweeps": job.sweeps, "seed": job.seed}
+        if job.pcc:
+            sp["pcc"] = True
+        else:
+            sp["T"] = job.T
+        ids += srv.submit([sp], want_obs=False)
+    srv.wait_all(0.0)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    lat, upd = [], 0
+    for i, job in zip(ids, trace):
+        r, _ = srv.poll(i)
+        assert r.status == 0
+        lat.append(r.queued_s + r.run_s)
+        upd += job.L * job.L * job.sweeps
+    srv.close()
+    import numpy as np
+    lat = np.array(lat)
+    return {"metric": "served SW/PCC site updates/ns (Poisson 200 jobs/s)", "value": round(upd / (wall * 1e9), 3),
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "jobs": len(trace),
+            "offered_site_updates_per_ns": round(upd / (args.serve_seconds * 1e9), 3),
+            "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4),
+                          "p99": round(float(np.percentile(lat, 99)), 4),
+                          "max": round(float(lat.max()), 4)},
+            "wall_s": round(wall, 2), "arrival_window_s": args.serve_seconds, "clocks": clk,
+            "config": {"workload": "Poisson 200 jobs/s, L log-uniform [32,4096], sweeps U[10,1000], "
+                                   "80% SW T~U[1.8,3.2], 20% PCC", "data": "synthetic"}}
 
 
 # ---------------------------------------------------------- reference arm
@@ -357,7 +461,12 @@ def run_reference(args):
 
 def main():
     args = parse_args()
-    out = run_reference(args) if args.impl == "reference" else run_gb300(args)
+    if args.impl == "reference":
+        out = run_reference(args)
+    elif args.workload == "serve":
+        out = run_serve(args)
+    else:
+        out = run_gb300(args)
     if out is not None:
         print(json.dumps(out), flush=True)
 
