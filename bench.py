@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--lattice", type=int, default=0, help="profiling only: another L")
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: sweeps per step")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--tile-h", type=int, default=0, choices=[0, 32, 64, 96, 128],
+                    help="rows per tile (0: the autotuner's choice for this L and T)")
     return ap.parse_args()
 
 
@@ -227,7 +229,8 @@ def run_gb300(args):
     K, W = args.steps, args.warmup
     N = w.L * w.L
     stream = torch.cuda.Stream()
-    lat = swgpu.Lattice(w.L, T=w.T, seed=w.seed + rank)
+    tile_h = args.tile_h or swgpu.sw_autotune(w.L, w.T)
+    lat = swgpu.Lattice(w.L, T=w.T, seed=w.seed + rank, tile_h=tile_h)
     lat.set_stream(stream)
 
     def barrier():
@@ -280,7 +283,7 @@ def run_gb300(args):
                 "frac": round(achieved / peak, 4),
                 "traffic": (round(traffic * st["tile_launches"] / max(st["tile_launches"], 1))
                             if traffic is not None else None),
-                "kernel": "k_tile<128> (fused finish/start of a sweep)",
+                "kernel": f"k_tile<{tile_h}> (fused finish/start of a sweep)",
                 "tile_kernel_avg_ms": round(tile_avg_ms, 4),
                 "merge_group_avg_ms": round(st["merge_ms"] / max(st["merge_groups"], 1), 4),
                 "peak_source": f"derived: {props.multi_processor_count} SMs x 64 IMAD lanes/clk / 2 "
@@ -321,7 +324,8 @@ def run_gb300(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
             "config": workload_config(w, {"parallelism": f"replicas x{world}",
-                                          "seeds": f"{w.seed}..{w.seed + world - 1}"}),
+                                          "seeds": f"{w.seed}..{w.seed + world - 1}",
+                                          "tile_h": tile_h}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
             "gpu_launches": K * ((4 + MERGE_JUMPS) * w.sweeps + 1),
             "clocks": clk, "impl": "gb300",

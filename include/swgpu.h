@@ -58,6 +58,7 @@ extern "C" {
 #define SW_FLAG_TILE_32 (1u << 8)
 #define SW_FLAG_TILE_64 (1u << 9)
 #define SW_FLAG_TILE_128 (1u << 10)
+#define SW_FLAG_TILE_96 (1u << 11)
 
 typedef struct sw_ctx sw_ctx; /* opaque; owned by the library */
 
@@ -199,7 +200,7 @@ typedef struct {
     double J, T, p;     /* J, T for SW_JOB_SW; p for SW_JOB_SWP                */
     uint64_t seed;
     int32_t nsweeps;    /* >= 1                                                */
-    int32_t tile_h;     /* 0 = autotuned, else 32, 64 or 128                   */
+    int32_t tile_h;     /* 0 = autotuned, else 32, 64, 96 or 128               */
     sw_obs *obs_out;    /* optional: nsweeps entries, written before completion */
     uint8_t *spins_out; /* optional: L*L final spins                            */
     int32_t *labels_out;/* optional: L*L labels of the last sweep               */

@@ -67,6 +67,7 @@ cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, cudaStream_t st)
     switch (TH) {
     case 32: launch_tile<32>(a, pcc, st); break;
     case 64: launch_tile<64>(a, pcc, st); break;
+    case 96: launch_tile<96>(a, pcc, st); break;
     default: launch_tile<128>(a, pcc, st); break;
     }
     return cudaGetLastError();
@@ -77,6 +78,7 @@ cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int n_reps, cuda
     switch (TH) {
     case 32: launch_merge<32>(a, pcc, n_reps, st); break;
     case 64: launch_merge<64>(a, pcc, n_reps, st); break;
+    case 96: launch_merge<96>(a, pcc, n_reps, st); break;
     default: launch_merge<128>(a, pcc, n_reps, st); break;
     }
     return cudaGetLastError();
@@ -95,6 +97,7 @@ cudaError_t prepare_th(int TH)
     switch (TH) {
     case 32: return tile_prepare<32>();
     case 64: return tile_prepare<64>();
+    case 96: return tile_prepare<96>();
     default: return tile_prepare<128>();
     }
 }
@@ -133,15 +136,18 @@ int sw_cuda_fail(cudaError_t e, int line = 0)
 }
 
 // Tile height used for an L x L lattice: a SW_FLAG_TILE_* flag, else the
-// smallest height that covers short lattices, else 128.
+// smallest height that covers short lattices, else 96 (three CTAs fit on an
+// SM, against two for 128).
 int pick_tile_height(int L, uint32_t flags)
 {
     if (flags & SW_FLAG_TILE_32) return 32;
     if (flags & SW_FLAG_TILE_64) return 64;
+    if (flags & SW_FLAG_TILE_96) return 96;
     if (flags & SW_FLAG_TILE_128) return 128;
     if (L <= 32) return 32;
     if (L <= 64) return 64;
-    return 128;
+    if (L <= 128) return 128;
+    return 96;
 }
 
 template <typename T>
@@ -695,6 +701,7 @@ int sw_get_bonds(sw_ctx *ctx, uint8_t *host_out)
     switch (ctx->TH) {
     case 32: k_bond_bytes<32><<<blocks, 256, 0, ctx->stream>>>(ctx->bondbits, ctx->L, ctx->tiles_x, ctx->bond_bytes); break;
     case 64: k_bond_bytes<64><<<blocks, 256, 0, ctx->stream>>>(ctx->bondbits, ctx->L, ctx->tiles_x, ctx->bond_bytes); break;
+    case 96: k_bond_bytes<96><<<blocks, 256, 0, ctx->stream>>>(ctx->bondbits, ctx->L, ctx->tiles_x, ctx->bond_bytes); break;
     default: k_bond_bytes<128><<<blocks, 256, 0, ctx->stream>>>(ctx->bondbits, ctx->L, ctx->tiles_x, ctx->bond_bytes); break;
     }
     SW_CUDA(cudaGetLastError());

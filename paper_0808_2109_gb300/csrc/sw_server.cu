@@ -37,11 +37,11 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int GROUPS_PER_STEP = 16;   // launch groups between admissions
-constexpr int N_LANES = 3;            // tile heights 32, 64, 128
+constexpr int N_LANES = 4;            // tile heights 32, 64, 96, 128
 constexpr int32_t SERVER_MAX_L = 4096;
 
-int lane_of_th(int th) { return th == 32 ? 0 : th == 64 ? 1 : 2; }
-int th_of_lane(int l) { return l == 0 ? 32 : l == 1 ? 64 : 128; }
+int lane_of_th(int th) { return th == 32 ? 0 : th == 64 ? 1 : th == 96 ? 2 : 3; }
+int th_of_lane(int l) { return l == 0 ? 32 : l == 1 ? 64 : l == 2 ? 96 : 128; }
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -550,7 +550,7 @@ int sw_batch_submit(sw_server *s, const sw_job *jobs, int32_t n, uint64_t *ids_o
         made.push_back(j);
         j->spec = q;
         if (q.L < 2 || q.L > SERVER_MAX_L || q.nsweeps < 1 ||
-            (q.tile_h != 0 && q.tile_h != 32 && q.tile_h != 64 && q.tile_h != 128)) {
+            (q.tile_h != 0 && q.tile_h != 32 && q.tile_h != 64 && q.tile_h != 96 && q.tile_h != 128)) {
             rc = SW_ERR_ARG;
             break;
         }
@@ -648,13 +648,13 @@ int sw_autotune(int32_t L, double T, int32_t *tile_h_out)
         return SW_OK;
     }
     const double Trep = regime == 0 ? 2.0 : (regime == 1 ? 2.269185 : 3.0);
-    const int heights[3] = {32, 64, 128};
-    const uint32_t flags[3] = {SW_FLAG_TILE_32, SW_FLAG_TILE_64, SW_FLAG_TILE_128};
+    const int heights[4] = {32, 64, 96, 128};
+    const uint32_t flags[4] = {SW_FLAG_TILE_32, SW_FLAG_TILE_64, SW_FLAG_TILE_96, SW_FLAG_TILE_128};
     const double target = 4e7;   // site updates timed per candidate
     const int n = (int)std::min(200.0, std::max(4.0, target / ((double)Lb * Lb)));
     int best = Lb <= 32 ? 32 : (Lb <= 64 ? 64 : 128);
     double best_t = 1e300;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 4; ++c) {
         if (heights[c] > std::max(32, Lb)) continue;
         sw_ctx *ctx = nullptr;
         if (sw_create(&ctx, Lb, 1.0, Trep, 12345, flags[c]) != SW_OK) continue;

@@ -56,7 +56,7 @@ class SwKernelStats(ctypes.Structure):
 
 
 SW_JOB_SW, SW_JOB_SWP, SW_JOB_PCC = 0, 1, 2
-SW_FLAG_TILE = {32: 1 << 8, 64: 1 << 9, 128: 1 << 10}
+SW_FLAG_TILE = {32: 1 << 8, 64: 1 << 9, 96: 1 << 11, 128: 1 << 10}
 
 
 class SwJob(ctypes.Structure):
@@ -347,16 +347,17 @@ class Lattice:
     """One L x L lattice on the GPU (plain SW at J, T or p; or PCC)."""
 
     def __init__(self, L: int, *, J: float = 1.0, T: float | None = None, p: float | None = None,
-                 seed: int = 1, pcc: bool = False):
+                 seed: int = 1, pcc: bool = False, tile_h: int = 0):
         self.L = int(L)
+        flags = SW_FLAG_TILE.get(int(tile_h), 0)
         if pcc:
-            self.h = pcc_create(self.L, seed)
+            self.h = pcc_create(self.L, seed, flags)
         elif p is not None:
-            self.h = sw_create_p(self.L, p, seed)
+            self.h = sw_create_p(self.L, p, seed, flags)
         else:
             if T is None:
                 raise ValueError("give T, p or pcc=True")
-            self.h = sw_create(self.L, J, T, seed)
+            self.h = sw_create(self.L, J, T, seed, flags)
         self.pcc = bool(pcc)
 
     def close(self):

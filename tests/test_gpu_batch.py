@@ -141,7 +141,7 @@ def test_tile_height_does_not_change_results(sw, orc):
     sp = {"L": 300, "T": 2.269185, "sweeps": 12, "seed": 4}
     outs = []
     with sw.Server() as srv:
-        for th in (32, 64, 128):
+        for th in (32, 64, 96, 128):
             (i,) = srv.submit([dict(sp, tile_h=th)], want_spins=True, want_labels=True)
             srv.wait_all(60.0)
             res, out = srv.poll(i)
@@ -151,7 +151,7 @@ def test_tile_height_does_not_change_results(sw, orc):
         assert_obs_equal(o["obs"], outs[0]["obs"])
         np.testing.assert_array_equal(o["spins"], outs[0]["spins"])
         np.testing.assert_array_equal(o["labels"], outs[0]["labels"])
-    assert sw.sw_autotune(300, 2.269185) in (32, 64, 128)
+    assert sw.sw_autotune(300, 2.269185) in (32, 64, 96, 128)
     assert sw.sw_autotune(20, 3.0) == 32
 
 

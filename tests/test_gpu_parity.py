@@ -25,8 +25,9 @@ def sw():
     return swgpu
 
 
-def _compare(sw, orc, L, T=None, p=None, seed=1, calls=(5,)):
+def _compare(sw, orc, L, T=None, p=None, seed=1, calls=(5,), tile_h=0):
     kw = dict(T=T) if T is not None else dict(p=p)
+    kw["tile_h"] = tile_h
     ref = orc.sw_chain(L, 1.0, T, seed) if T is not None else orc.sw_chain_p(L, p, seed)
     with sw.Lattice(L, seed=seed, **kw) as lat:
         np.testing.assert_array_equal(lat.spins(), ref.spin, err_msg="hot start")
@@ -47,6 +48,14 @@ def _compare(sw, orc, L, T=None, p=None, seed=1, calls=(5,)):
 def test_small_lattices_bit_exact(sw, orc, L):
     for T in (2.0, 2.269185, 3.0):
         _compare(sw, orc, L, T=T, seed=L, calls=(4,))
+
+
+@pytest.mark.parametrize("tile_h", [32, 64, 96, 128])
+@pytest.mark.parametrize("L", [5, 95, 97, 130, 200, 385])
+def test_every_tile_height(sw, orc, L, tile_h):
+    """Results do not depend on the tile height (ragged last tile rows,
+    partial sub-tile rows, a lattice narrower than one tile)."""
+    _compare(sw, orc, L, T=2.269185, seed=L + tile_h, calls=(3, 2), tile_h=tile_h)
 
 
 @pytest.mark.parametrize("L", [17, 128, 300])
