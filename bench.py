@@ -327,7 +327,7 @@ def run_gb300(args):
                                           "seeds": f"{w.seed}..{w.seed + world - 1}",
                                           "tile_h": tile_h}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
-            "gpu_launches": K * ((4 + MERGE_JUMPS) * w.sweeps + 1),
+            "gpu_launches": K * ((3 + MERGE_JUMPS) * w.sweeps + 1),
             "clocks": clk, "impl": "gb300",
         }
     lat.close()

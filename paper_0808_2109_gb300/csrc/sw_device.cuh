@@ -35,7 +35,9 @@ constexpr int CROSS_WORDS = 8;    // per tile: 4 words right-edge bits, 4 words 
 // 30-bit global roots: the GPU path supports N = L*L <= 2^30.
 constexpr uint32_t ROOT_MASK = 0x3FFFFFFFu;
 constexpr uint32_t FINAL_SPIN = 0x40000000u;
-constexpr uint32_t KEY_NONE = 0x3FFFFFFFu;
+constexpr uint32_t KEY_NONE = 0x3FFFFFFFu;   // an edge slot past the tile's sites
+constexpr uint32_t KEY_REP = 0x40000000u;    // the node represents its piece
+constexpr uint32_t KEY_MASK = 0x3FFFFFFFu;
 
 // 2-byte tile-local cluster code of a site, written when a sweep starts and
 // read when it finishes.
@@ -167,6 +169,17 @@ __device__ __forceinline__ uint32_t valid_mask(int c, int tw)
 {
     const int n = tw - 32 * c;
     return n >= 32 ? 0xFFFFFFFFu : (n <= 0 ? 0u : ((1u << n) - 1u));
+}
+
+// Resolved final (root | spin << 30) of an edge slot.  A representative
+// holds its own; any other slot holds FINAL_ALIAS | a representative of the
+// same cluster.  Only nfinal is read: the tile kernel that reads a
+// neighbour's finals rewrites that neighbour's npar and nkey concurrently.
+constexpr uint32_t FINAL_ALIAS = 0x80000000u;
+__device__ __forceinline__ uint32_t node_final(const Replica &R, size_t node)
+{
+    const uint32_t f = R.nfinal[node];
+    return (f & FINAL_ALIAS) ? R.nfinal[f & ~FINAL_ALIAS] : f;
 }
 
 // ------------------------------------------------------------ tile geometry
@@ -563,14 +576,14 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
         for (int w = warp; w < TWW + 1; w += NW) {
             const int x = 32 * w + lane;
             int spin = 0;
-            if (x < t.tw) spin = (R.nfinal[(size_t)t.g_down * S + SL::TOP + x] & FINAL_SPIN) ? 1 : 0;
+            if (x < t.tw) spin = (node_final(R, (size_t)t.g_down * S + SL::TOP + x) & FINAL_SPIN) ? 1 : 0;
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
             if (lane == 0) sm.sp[t.th][w] = word;
         }
         __syncthreads();
         // right halo column: new spins of the left column of the tile to the right
         for (int y = tid; y < t.th; y += NT) {
-            if (R.nfinal[(size_t)t.g_right * S + SL::LEFT + y] & FINAL_SPIN)
+            if (node_final(R, (size_t)t.g_right * S + SL::LEFT + y) & FINAL_SPIN)
                 sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
         }
         __syncthreads();
@@ -753,7 +766,8 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
         if (rs[q] >= 0) {
             const int rep = sm.par[rs[q]] & 0x3FF;
             R.npar[node] = (int32_t)((size_t)t.lt * S + rep);
-            R.nkey[node] = (int32_t)(gbase + (uint32_t)(rs[q] / PW) * uL + (uint32_t)(rs[q] % PW));
+            R.nkey[node] = (int32_t)((gbase + (uint32_t)(rs[q] / PW) * uL + (uint32_t)(rs[q] % PW)) |
+                                     (rep == s ? KEY_REP : 0u));
         } else {
             R.npar[node] = (int32_t)node;
             R.nkey[node] = (int32_t)KEY_NONE;
@@ -844,124 +858,166 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
 }
 
 // ------------------------------------------------------------- merge phase
-// Master step 2 of Sec. II.A: only links between neighbouring domains are
-// activated on the "new lattice" of border sites.
+// Launch shape of the merge kernels: one block per tile (blockIdx.x = the
+// tile's index in the tile table) of S/4 threads; thread i takes the slots
+// i + q*S/4 (q < 4) and the crossing links i + q*S/4 (q < 2).  The tile's
+// lattice, launch and range checks are read once per thread instead of once
+// per node, and the loads of a thread's nodes are issued together.
 template <int TH>
-__global__ void k_merge_union(const SweepArgs a)
+struct MergeCfg {
+    static constexpr int S = Slots<TH>::S;
+    static constexpr int MT = S / 4;                    // threads per block
+    static constexpr int NPT = 4;                       // slots per thread
+    static constexpr int EPT = (TH + TW + MT - 1) / MT; // crossing links per thread
+    static_assert(S % 4 == 0 && EPT == 2, "merge launch shape");
+};
+
+// The lattice of tile g and its launch index, or null when the tile is idle
+// or the lattice has no sweep in this launch (uniform across the block).
+__device__ __forceinline__ const Replica *merge_lattice(const SweepArgs &a, int g, int &j)
+{
+    const int ri = a.tile_rep[g];
+    if (ri < 0) return nullptr;
+    const Replica *R = a.reps + ri;
+    j = lattice_launch(a, *R);
+    return (j < 0 || j >= R->nsweeps) ? nullptr : R;
+}
+
+// Master step 2 of Sec. II.A: only links between neighbouring domains are
+// activated on the "new lattice" of border sites.  Link e < TH joins row e
+// of the tile's right column to the left column of the tile to its right;
+// link TH + x joins column x of its bottom row to the top row below it.
+template <int TH>
+__global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_union(const SweepArgs a)
 {
     using SL = Slots<TH>;
+    using MC = MergeCfg<TH>;
     constexpr int S = SL::S;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)a.n_tiles * (TH + TW)) return;
-    const int g = (int)(idx / (TH + TW));
-    const int e = (int)(idx % (TH + TW));
-    const int ri = a.tile_rep[g];
-    if (ri < 0) return;
-    const Replica &R = a.reps[ri];
-    const int j = lattice_launch(a, R);
-    if (j < 0 || j >= R.nsweeps) return;
-    const Tile t = tile_of(R, g, TH);
-    int na, nb;
-    if (e < TH) {
-        const int y = e;
-        if (y >= t.th) return;
-        if (!((R.cross[(size_t)t.lt * CROSS_WORDS + (y >> 5)] >> (y & 31)) & 1u)) return;
-        na = t.lt * S + SL::RIGHT + y;
-        nb = t.g_right * S + SL::LEFT + y;
-    } else {
-        const int x = e - TH;
-        if (x >= t.tw) return;
-        if (!((R.cross[(size_t)t.lt * CROSS_WORDS + TWW + (x >> 5)] >> (x & 31)) & 1u)) return;
-        na = t.lt * S + SL::BOTTOM + x;
-        nb = t.g_down * S + SL::TOP + x;
-    }
-    gunite_by_key(R.npar, R.nkey, na, nb);
-}
-
-// One round of pointer jumping over the node forest (every parent replaced
-// by its grandparent): a few rounds between the unions and the compression
-// cut the depth of the chains that unions across many tiles leave behind.
-template <int TH>
-__global__ void k_merge_jump(const SweepArgs a)
-{
-    constexpr int S = Slots<TH>::S;
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (int64_t)a.n_tiles * S) return;
-    const int ri = a.tile_rep[n / S];
-    if (ri < 0) return;
-    const Replica &R = a.reps[ri];
-    const int j = lattice_launch(a, R);
-    if (j < 0 || j >= R.nsweeps) return;
-    const int64_t nl = n - (int64_t)R.tile_base * S;   // the lattice's own node
-    const int p = gload(R.npar + nl);
-    const int gp = gload(R.npar + p);
-    if (gp != p) *(volatile int32_t *)(R.npar + nl) = gp;
-}
-
-// Compress every node to its root (whose key is the cluster's minimum site
-// index) and count the clusters that touch a tile border.
-template <int TH>
-__global__ void k_merge_compress(const SweepArgs a)
-{
-    constexpr int S = Slots<TH>::S;
-    static_assert(S % 32 == 0, "a warp's nodes must belong to one tile");
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (int64_t)a.n_tiles * S) return;
-    const int ri = a.tile_rep[n / S];
-    if (ri < 0) return;                 // uniform across the warp (one tile)
-    const Replica &R = a.reps[ri];
-    const int j = lattice_launch(a, R);
-    if (j < 0 || j >= R.nsweeps) return;
-    const int nl = (int)(n - (int64_t)R.tile_base * S);   // the lattice's own node
-    const int key = R.nkey[nl];
-    bool is_root = false;
-    if ((uint32_t)key != KEY_NONE) {
-        // No union happens any more, so every node on the walk from n has the
-        // same root r: writing r over each of them (full path compression)
-        // can only ever store the final value, and later walks get short.
-        int r = nl, p = gload(R.npar + r);
-        while (p != r) {
-            r = p;
-            p = gload(R.npar + r);
+    int j;
+    const Replica *Rp = merge_lattice(a, blockIdx.x, j);
+    if (!Rp) return;
+    const Replica &R = *Rp;
+    const Tile t = tile_of(R, blockIdx.x, TH);
+    const uint32_t *cross = R.cross + (size_t)t.lt * CROSS_WORDS;
+    int na[MC::EPT], nb[MC::EPT];
+#pragma unroll
+    for (int q = 0; q < MC::EPT; ++q) {
+        const int e = threadIdx.x + q * MC::MT;
+        na[q] = -1;
+        if (e < TH) {
+            if (e < t.th && ((cross[e >> 5] >> (e & 31)) & 1u)) {
+                na[q] = t.lt * S + SL::RIGHT + e;
+                nb[q] = t.g_right * S + SL::LEFT + e;
+            }
+        } else if (e < TH + TW) {
+            const int x = e - TH;
+            if (x < t.tw && ((cross[TWW + (x >> 5)] >> (x & 31)) & 1u)) {
+                na[q] = t.lt * S + SL::BOTTOM + x;
+                nb[q] = t.g_down * S + SL::TOP + x;
+            }
         }
-        for (int x = nl; x != r;) {
-            const int nx = gload(R.npar + x);
-            *(volatile int32_t *)(R.npar + x) = r;
-            x = nx;
-        }
-        is_root = r == nl;
     }
-    // one root node per cluster that touches a tile border
-    const uint32_t roots = __ballot_sync(__activemask(), is_root);
-    if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && roots)
-        atomicAdd(&R.obs[j].nclusters, (unsigned long long)__popc(roots));
+#pragma unroll
+    for (int q = 0; q < MC::EPT; ++q)
+        if (na[q] >= 0) gunite_by_key(R.npar, R.nkey, na[q], nb[q]);
 }
 
-// Each node takes its cluster's root and the cluster's new spin:
-// bit (root mod 128) of Philox(root/128, k, SPIN) (Sec. I step 3).
+// One round of pointer jumping over the representatives (every parent
+// replaced by its grandparent): a few rounds between the unions and the
+// compression cut the depth of the chains that unions across many tiles
+// leave behind.  Other slots only alias their piece's representative.
 template <int TH>
-__global__ void k_merge_final(const SweepArgs a)
+__global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs a)
 {
-    constexpr int S = Slots<TH>::S;
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (int64_t)a.n_tiles * S) return;
-    const int ri = a.tile_rep[n / S];
-    if (ri < 0) return;
-    const Replica &R = a.reps[ri];
-    const int j = lattice_launch(a, R);
-    if (j < 0 || j >= R.nsweeps) return;
-    const int64_t nl = n - (int64_t)R.tile_base * S;   // the lattice's own node
-    const uint32_t key0 = (uint32_t)R.nkey[nl];
-    if (key0 == KEY_NONE) {
-        R.nfinal[nl] = 0u;
-        return;
+    using MC = MergeCfg<TH>;
+    int j;
+    const Replica *Rp = merge_lattice(a, blockIdx.x, j);
+    if (!Rp) return;
+    const Replica &R = *Rp;
+    const int base = (blockIdx.x - R.tile_base) * MC::S;   // the lattice's own nodes
+    uint32_t key[MC::NPT];
+    int p[MC::NPT], gp[MC::NPT];
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) key[q] = (uint32_t)R.nkey[base + threadIdx.x + q * MC::MT];
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) p[q] = (key[q] & KEY_REP) ? gload(R.npar + base + threadIdx.x + q * MC::MT) : -1;
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) gp[q] = p[q] >= 0 ? gload(R.npar + p[q]) : -1;
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q)
+        if (gp[q] != p[q]) *(volatile int32_t *)(R.npar + base + threadIdx.x + q * MC::MT) = gp[q];
+}
+
+// Resolve every node once the unions are done: each representative walks to
+// its root r (key: the cluster's minimum site index), writes r over every
+// node of the walk (full path compression: no union happens any more, so
+// every node on it has root r) and stores the cluster's root and new spin,
+// bit (root mod 128) of Philox(root/128, k, SPIN) (Sec. I step 3).  Any
+// other slot stores FINAL_ALIAS | its representative.  Counts the clusters
+// that touch a tile border (one root node each).
+template <int TH>
+__global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepArgs a)
+{
+    using MC = MergeCfg<TH>;
+    int j;
+    const Replica *Rp = merge_lattice(a, blockIdx.x, j);
+    if (!Rp) return;
+    const Replica &R = *Rp;
+    const int base = (blockIdx.x - R.tile_base) * MC::S;
+    uint32_t key[MC::NPT];
+    int r[MC::NPT], p[MC::NPT];
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) key[q] = (uint32_t)R.nkey[base + threadIdx.x + q * MC::MT];
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) {
+        r[q] = base + threadIdx.x + q * MC::MT;
+        p[q] = gload(R.npar + r[q]);
     }
-    const uint32_t root = (uint32_t)R.nkey[R.npar[nl]];
+    // the walks of the thread's representatives advance in lock step
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int q = 0; q < MC::NPT; ++q) {
+            if ((key[q] & KEY_REP) && p[q] != r[q]) {
+                r[q] = p[q];
+                more = true;
+            }
+        }
+        if (!more) break;
+#pragma unroll
+        for (int q = 0; q < MC::NPT; ++q)
+            if (key[q] & KEY_REP) p[q] = gload(R.npar + r[q]);
+    }
+    uint32_t rkey[MC::NPT];
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) rkey[q] = (key[q] & KEY_REP) ? (uint32_t)R.nkey[r[q]] & KEY_MASK : 0u;
     const uint64_t k = R.sweep0 + (uint64_t)j;
-    const U4 r = stream_block(R, root >> 7, k, STREAM_SPIN);
-    const int bit = root & 127;
-    const uint32_t spin = (u4_word(r, bit >> 5) >> (bit & 31)) & 1u;
-    R.nfinal[nl] = root | (spin ? FINAL_SPIN : 0u);
+    int nroots = 0;
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) {
+        const int n = base + threadIdx.x + q * MC::MT;
+        if (key[q] & KEY_REP) {
+            for (int x = n; x != r[q];) {
+                const int nx = gload(R.npar + x);
+                *(volatile int32_t *)(R.npar + x) = r[q];
+                x = nx;
+            }
+            nroots += r[q] == n;
+            const U4 u = stream_block(R, rkey[q] >> 7, k, STREAM_SPIN);
+            const int bit = rkey[q] & 127;
+            const uint32_t spin = (u4_word(u, bit >> 5) >> (bit & 31)) & 1u;
+            R.nfinal[n] = rkey[q] | (spin ? FINAL_SPIN : 0u);
+        } else {
+            // the alias points at a representative: its parent since the tile
+            // kernel, moved up the same cluster by path halving at most
+            R.nfinal[n] = key[q] == KEY_NONE ? 0u : FINAL_ALIAS | (uint32_t)p[q];
+        }
+    }
+    // every thread of the block gets here; the last warp may be partial
+    const int wb = threadIdx.x & ~31;
+    const unsigned wm = MC::MT - wb >= 32 ? 0xFFFFFFFFu : (1u << (MC::MT - wb)) - 1u;
+    nroots = __reduce_add_sync(wm, nroots);
+    if ((threadIdx.x & 31) == 0 && nroots) atomicAdd(&R.obs[j].nclusters, (unsigned long long)nroots);
 }
 
 // ------------------------------------------------------------------- PCC
@@ -1002,7 +1058,8 @@ __global__ void k_pcc_candidates(const SweepArgs a)
         axis = 1;
         node = t.lt * S + SL::TOP + x;
     }
-    const int r = gload(R.npar + node);
+    int r = gload(R.npar + node);
+    if (!((uint32_t)R.nkey[node] & KEY_REP)) r = gload(R.npar + r);   // via the representative
     int32_t *c = R.cid + (size_t)r * 2 + axis;
     if (atomicCAS(c, 0, 1) == 0) {
         const int id = atomicAdd(R.ncand + axis, 1);   // < L: at most one per edge site

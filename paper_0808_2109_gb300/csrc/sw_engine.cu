@@ -47,19 +47,20 @@ template <int TH>
 void launch_merge(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
 {
     constexpr int S = Slots<TH>::S;
+    constexpr int MT = MergeCfg<TH>::MT;
     const int64_t nu = (int64_t)a.n_tiles * (TH + TW);
     const int64_t nn = (int64_t)a.n_tiles * S;
     const unsigned bu = (unsigned)((nu + MERGE_THREADS - 1) / MERGE_THREADS);
     const unsigned bn = (unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS);
-    k_merge_union<TH><<<bu, MERGE_THREADS, 0, st>>>(a);
-    for (int r = 0; r < MERGE_JUMPS; ++r) k_merge_jump<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
-    k_merge_compress<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
-    if (pcc) {
+    const unsigned tiles = (unsigned)a.n_tiles;
+    k_merge_union<TH><<<tiles, MT, 0, st>>>(a);
+    for (int r = 0; r < MERGE_JUMPS; ++r) k_merge_jump<TH><<<tiles, MT, 0, st>>>(a);
+    k_merge_resolve<TH><<<tiles, MT, 0, st>>>(a);
+    if (pcc) {   // reads the compressed forest; the spins do not depend on it
         k_pcc_candidates<TH><<<bu, MERGE_THREADS, 0, st>>>(a);
         k_pcc_cover<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
         k_pcc_decide<TH><<<n_reps, 256, 0, st>>>(a, n_reps);
     }
-    k_merge_final<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
 }
 
 cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, cudaStream_t st)
