@@ -274,6 +274,9 @@ struct TileCfg {
     static constexpr int NT = 4 * TH;           // threads per CTA
     static constexpr int NW = NT / 32;          // warps = sub-tiles
     static constexpr int SUBY = TH / 32;        // sub-tile rows
+    // CTAs per SM the register allocation must leave room for (96-row tiles:
+    // three, which the shared memory also allows)
+    static constexpr int MINB = TH == 96 ? 3 : 1;
 };
 
 // Root of x without writing (a forest no thread is changing any more).
@@ -484,7 +487,7 @@ constexpr size_t tile_smem(bool pcc)
 
 // ----------------------------------------------------------------- k_tile
 template <int TH>
-__global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
+__global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(const SweepArgs a)
 {
     using SL = Slots<TH>;
     constexpr int S = SL::S;
@@ -645,41 +648,9 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
     const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
     const bool any_bond = thr != 0;               // t = 0: P = 0, nothing bonds
     const uint32_t tm1 = (uint32_t)(thr - 1);     // t in [1, 2^32] -> t - 1 fits 32 bits
-    for (int y = warp; y < t.th; y += NW) {
-        const uint32_t G0 = gbase + (uint32_t)y * uL;
-        uint32_t rh[TWW], rv[TWW];
-        if (!any_bond) {
-#pragma unroll
-            for (int q = 0; q < TWW; ++q) rh[q] = rv[q] = 0u;
-        } else if ((G0 & 1u) == 0) {
-            // aligned row: lane l draws the blocks of sites (2l, 2l+1) and
-            // (64+2l, 65+2l); lane x of each 32-site word then fetches its
-            // two bits by shuffle
-            const uint32_t b0 = (G0 >> 1) + lane;
-            const U4 r0 = philox4x32_10(b0, klo, khi, STREAM_BOND, R.key0, R.key1);
-            const U4 r1 = philox4x32_10(b0 + 32, klo, khi, STREAM_BOND, R.key0, R.key1);
-            const uint32_t nib0 = (below(r0.x, tm1) ? 1u : 0u) | (below(r0.y, tm1) ? 2u : 0u) |
-                                  (below(r0.z, tm1) ? 4u : 0u) | (below(r0.w, tm1) ? 8u : 0u);
-            const uint32_t nib1 = (below(r1.x, tm1) ? 1u : 0u) | (below(r1.y, tm1) ? 2u : 0u) |
-                                  (below(r1.z, tm1) ? 4u : 0u) | (below(r1.w, tm1) ? 8u : 0u);
-#pragma unroll
-            for (int q = 0; q < TWW; ++q) {
-                const uint32_t n = __shfl_sync(0xFFFFFFFFu, q < 2 ? nib0 : nib1, 16 * (q & 1) + (lane >> 1)) >>
-                                   (2 * (lane & 1));
-                rh[q] = __ballot_sync(0xFFFFFFFFu, n & 1u);
-                rv[q] = __ballot_sync(0xFFFFFFFFu, n & 2u);
-            }
-        } else {
-            // odd row start (odd L): every site draws its own block
-#pragma unroll
-            for (int q = 0; q < TWW; ++q) {
-                const uint32_t gi = G0 + 32 * q + lane;
-                const U4 r = philox4x32_10(gi >> 1, klo, khi, STREAM_BOND, R.key0, R.key1);
-                const bool odd = gi & 1u;
-                rh[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.z : r.x, tm1));
-                rv[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.w : r.y, tm1));
-            }
-        }
+    // the bonds of row y from its two horizontal-and-vertical draw words per
+    // 32-site word (rh, rv): keep the links whose spins agree, store them
+    auto store_row = [&](int y, const uint32_t (&rh)[TWW], const uint32_t (&rv)[TWW]) {
         if (lane < TWW) {
             const int c = lane;
             const uint32_t rhc = c == 0 ? rh[0] : c == 1 ? rh[1] : c == 2 ? rh[2] : rh[3];
@@ -696,6 +667,67 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT) k_tile(const SweepArgs a)
             // row's down link cross the tile edge
             sm.ih[y][c] = h & valid_mask(c, t.tw - 1);
             sm.iv[y][c] = (y < t.th - 1) ? v : 0u;
+        }
+    };
+    // aligned row: lane l drew the blocks of sites (2l, 2l+1) (r0) and
+    // (64+2l, 65+2l) (r1); lane x of each 32-site word fetches its two bits
+    // by shuffle
+    auto draws_aligned = [&](const U4 &r0, const U4 &r1, uint32_t (&rh)[TWW], uint32_t (&rv)[TWW]) {
+        const uint32_t nib0 = (below(r0.x, tm1) ? 1u : 0u) | (below(r0.y, tm1) ? 2u : 0u) |
+                              (below(r0.z, tm1) ? 4u : 0u) | (below(r0.w, tm1) ? 8u : 0u);
+        const uint32_t nib1 = (below(r1.x, tm1) ? 1u : 0u) | (below(r1.y, tm1) ? 2u : 0u) |
+                              (below(r1.z, tm1) ? 4u : 0u) | (below(r1.w, tm1) ? 8u : 0u);
+#pragma unroll
+        for (int q = 0; q < TWW; ++q) {
+            const uint32_t n = __shfl_sync(0xFFFFFFFFu, q < 2 ? nib0 : nib1, 16 * (q & 1) + (lane >> 1)) >>
+                               (2 * (lane & 1));
+            rh[q] = __ballot_sync(0xFFFFFFFFu, n & 1u);
+            rv[q] = __ballot_sync(0xFFFFFFFFu, n & 2u);
+        }
+    };
+    if (any_bond && (uL & 1u) == 0) {
+        // even L: every row starts on an even site; two rows per pass, four
+        // independent Philox blocks in flight per lane
+        for (int y = warp; y < t.th; y += 2 * NW) {
+            const int y2 = y + NW;
+            const uint32_t b0 = ((gbase + (uint32_t)y * uL) >> 1) + lane;
+            const uint32_t b2 = ((gbase + (uint32_t)y2 * uL) >> 1) + lane;
+            const U4 r0 = philox4x32_10(b0, klo, khi, STREAM_BOND, R.key0, R.key1);
+            const U4 r1 = philox4x32_10(b0 + 32, klo, khi, STREAM_BOND, R.key0, R.key1);
+            const U4 r2 = philox4x32_10(b2, klo, khi, STREAM_BOND, R.key0, R.key1);
+            const U4 r3 = philox4x32_10(b2 + 32, klo, khi, STREAM_BOND, R.key0, R.key1);
+            uint32_t rh[TWW], rv[TWW];
+            draws_aligned(r0, r1, rh, rv);
+            store_row(y, rh, rv);
+            if (y2 < t.th) {
+                draws_aligned(r2, r3, rh, rv);
+                store_row(y2, rh, rv);
+            }
+        }
+    } else {
+        for (int y = warp; y < t.th; y += NW) {
+            const uint32_t G0 = gbase + (uint32_t)y * uL;
+            uint32_t rh[TWW], rv[TWW];
+            if (!any_bond) {
+#pragma unroll
+                for (int q = 0; q < TWW; ++q) rh[q] = rv[q] = 0u;
+            } else if ((G0 & 1u) == 0) {
+                const uint32_t b0 = (G0 >> 1) + lane;
+                const U4 r0 = philox4x32_10(b0, klo, khi, STREAM_BOND, R.key0, R.key1);
+                const U4 r1 = philox4x32_10(b0 + 32, klo, khi, STREAM_BOND, R.key0, R.key1);
+                draws_aligned(r0, r1, rh, rv);
+            } else {
+                // odd row start (odd L): every site draws its own block
+#pragma unroll
+                for (int q = 0; q < TWW; ++q) {
+                    const uint32_t gi = G0 + 32 * q + lane;
+                    const U4 r = philox4x32_10(gi >> 1, klo, khi, STREAM_BOND, R.key0, R.key1);
+                    const bool odd = gi & 1u;
+                    rh[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.z : r.x, tm1));
+                    rv[q] = __ballot_sync(0xFFFFFFFFu, below(odd ? r.w : r.y, tm1));
+                }
+            }
+            store_row(y, rh, rv);
         }
     }
     // SPIN-stream blocks covering each row, for the clusters that end inside
@@ -1177,6 +1209,21 @@ static __global__ void k_hot_start(uint8_t *spin, int64_t N, uint32_t key0, uint
     const U4 r = philox4x32_10((uint32_t)(i >> 7), 0u, 0u, STREAM_INIT, key0, key1);
     const int bit = (int)(i & 127);
     spin[i] = (uint8_t)((u4_word(r, bit >> 5) >> (bit & 31)) & 1u);
+}
+
+// A served lattice's initial device state in one launch: the hot start, zero
+// observables (n_obs 8-byte words) and the threshold word.
+static __global__ void k_job_init(uint8_t *spin, int64_t N, uint32_t key0, uint32_t key1,
+                                  unsigned long long *obs, int64_t n_obs, uint64_t *thr_dev, uint64_t thr)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        const U4 r = philox4x32_10((uint32_t)(i >> 7), 0u, 0u, STREAM_INIT, key0, key1);
+        const int bit = (int)(i & 127);
+        spin[i] = (uint8_t)((u4_word(r, bit >> 5) >> (bit & 31)) & 1u);
+    }
+    if (i < n_obs) obs[i] = 0ull;
+    if (i == 0) *thr_dev = thr;
 }
 
 // Sets *bad if any of the n bytes is not 0 or 1.

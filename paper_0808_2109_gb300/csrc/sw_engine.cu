@@ -8,6 +8,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -106,6 +107,17 @@ cudaError_t prepare_th(int TH)
 cudaError_t enqueue_hot_start(uint8_t *spin, int64_t N, uint64_t seed, cudaStream_t st)
 {
     k_hot_start<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(spin, N, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_job_init(uint8_t *spin, int64_t N, uint64_t seed, void *obs, int64_t obs_bytes, uint64_t *thr_dev,
+                             uint64_t thr, cudaStream_t st)
+{
+    const int64_t n_obs = obs_bytes / 8;
+    const int64_t n = std::max(N, n_obs);
+    k_job_init<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(spin, N, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                                            static_cast<unsigned long long *>(obs), n_obs, thr_dev,
+                                                            thr);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,9 @@ __attribute__((visibility("hidden"))) cudaError_t enqueue_launch_th(int TH, cons
                                                                     cudaStream_t st);
 __attribute__((visibility("hidden"))) cudaError_t enqueue_hot_start(uint8_t *spin, int64_t N, uint64_t seed,
                                                                     cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t enqueue_job_init(uint8_t *spin, int64_t N, uint64_t seed, void *obs,
+                                                                   int64_t obs_bytes, uint64_t *thr_dev, uint64_t thr,
+                                                                   cudaStream_t st);
 
 inline int slots_of(int TH) { return 2 * TW + 2 * TH; }
 

@@ -53,7 +53,8 @@ struct Job {
     int TH = 128, tiles_x = 0, tiles_y = 0, n_tiles = 0, S = 0;
     size_t bytes = 0;
     Clock::time_point t_submit, t_admit;
-    // device state
+    // device state: every buffer is carved from one block
+    void *block = nullptr;
     uint8_t *spin = nullptr;
     int32_t *label = nullptr;
     uint16_t *code = nullptr;
@@ -66,19 +67,49 @@ struct Job {
     int32_t jstart = 0;
 };
 
-size_t job_bytes(int L, int TH, int nsweeps, bool pcc)
+// Byte offsets of a job's buffers inside its one device block, each on a
+// 256-byte boundary; PCC scratch last, in one range that starts zeroed.
+struct JobLayout {
+    size_t spin, label, code, bondbits, cross, npar, nkey, nfinal, thr, obs;
+    size_t pmask, cid, cand, ncand, cov, pcc_end, total;
+};
+
+JobLayout job_layout(int L, int TH, int nsweeps, bool pcc)
 {
     const size_t N = (size_t)L * L;
     const size_t tx = (L + TW - 1) / TW, ty = (L + TH - 1) / TH, nt = tx * ty;
     const size_t S = (size_t)slots_of(TH);
-    size_t b = round256(N) + round256(4 * N) + round256(nt * TH * TW * 2) + round256(nt * TH * 2 * TWW * 4) +
-               round256(nt * CROSS_WORDS * 4) + 3 * round256(nt * S * 4) + round256((size_t)nsweeps * sizeof(DevObs)) +
-               256;
-    if (pcc)
-        b += round256(nt * S * 8 * 4) + round256(nt * S * 2 * 4) + round256(2 * (size_t)L * 4) + 256 +
-             round256((size_t)L * (tx + ty) * 4 * 4);
-    return b;
+    JobLayout o{};
+    size_t at = 0;
+    auto take = [&at](size_t bytes) {
+        const size_t here = at;
+        at += round256(std::max<size_t>(bytes, 1));
+        return here;
+    };
+    o.spin = take(N);
+    o.label = take(4 * N);
+    o.code = take(nt * TH * TW * 2);
+    o.bondbits = take(nt * TH * 2 * TWW * 4);
+    o.cross = take(nt * CROSS_WORDS * 4);
+    o.npar = take(nt * S * 4);
+    o.nkey = take(nt * S * 4);
+    o.nfinal = take(nt * S * 4);
+    o.thr = take(8);
+    o.obs = take((size_t)nsweeps * sizeof(DevObs));
+    o.pmask = o.cid = o.cand = o.ncand = o.cov = o.pcc_end = at;
+    if (pcc) {
+        o.pmask = take(nt * S * 8 * 4);
+        o.cid = take(nt * S * 2 * 4);
+        o.cand = take(2 * (size_t)L * 4);
+        o.ncand = take(2 * 4);
+        o.cov = take((size_t)L * (tx + ty) * 4 * 4);
+        o.pcc_end = at;
+    }
+    o.total = at;
+    return o;
 }
+
+size_t job_bytes(int L, int TH, int nsweeps, bool pcc) { return job_layout(L, TH, nsweeps, pcc).total; }
 
 struct Lane {
     int TH = 128;
@@ -90,6 +121,8 @@ struct Lane {
     std::vector<Replica> reps_host;
     std::vector<int32_t> tile_rep_host;
     std::vector<Job *> slot_job;
+    std::vector<int> free_slots;   // unused slots (a stack)
+    int tail = 0;                  // every tile from here on is free
     cudaGraphExec_t graph = nullptr;
     bool graph_pcc = false;
     bool dirty = true;       // tables changed since the last upload
@@ -115,59 +148,51 @@ struct sw_server {
     std::thread worker;
     sw_server_stats stats{};
     int worker_error = SW_OK;
+    DevObs *stage = nullptr;   // pinned staging for retired jobs' observables
+    size_t stage_cap = 0;
 };
 
 namespace {
 
 void free_job_device(Job *j, cudaStream_t st)
 {
-    void *ptrs[] = {j->spin, j->label, j->code, j->bondbits, j->cross, j->npar, j->nkey, j->nfinal,
-                    j->pmask, j->cid, j->cand, j->ncand, j->cov, j->thr_dev, j->obs};
-    for (void *p : ptrs)
-        if (p) cudaFreeAsync(p, st);
+    if (j->block) cudaFreeAsync(j->block, st);
+    j->block = nullptr;
 }
 
-template <typename T>
-cudaError_t aalloc(T **p, size_t count, cudaStream_t st)
-{
-    return cudaMallocAsync((void **)p, std::max<size_t>(count, 1) * sizeof(T), st);
-}
-
-// Device state of a newly admitted job: buffers, hot start, PCC scratch.
+// Device state of a newly admitted job: one stream-ordered block for all its
+// buffers, zeroed PCC scratch, and one kernel for the hot start, the
+// observables and the threshold.
 cudaError_t job_alloc(Job *j, cudaStream_t st)
 {
     const size_t N = (size_t)j->spec.L * j->spec.L;
-    const size_t nt = (size_t)j->n_tiles, S = (size_t)j->S;
-    cudaError_t e;
-#define A(ptr, n)                                            \
-    if ((e = aalloc(&j->ptr, (n), st)) != cudaSuccess) return e;
-    A(spin, N);
-    A(label, N);
-    A(code, nt * j->TH * TW);
-    A(bondbits, nt * j->TH * 2 * TWW);
-    A(cross, nt * CROSS_WORDS);
-    A(npar, nt * S);
-    A(nkey, nt * S);
-    A(nfinal, nt * S);
-    A(thr_dev, 1);
-    A(obs, (size_t)j->spec.nsweeps);
-    if (j->pcc) {
-        A(pmask, nt * S * 8);
-        A(cid, nt * S * 2);
-        A(cand, 2 * (size_t)j->spec.L);
-        A(ncand, 2);
-        A(cov, (size_t)j->spec.L * (j->tiles_x + j->tiles_y) * 4);
-        if ((e = cudaMemsetAsync(j->cid, 0, nt * S * 2 * sizeof(int32_t), st)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(j->ncand, 0, 2 * sizeof(int32_t), st)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(j->cov, 0, (size_t)j->spec.L * (j->tiles_x + j->tiles_y) * 4 * sizeof(uint32_t), st)) !=
-            cudaSuccess)
-            return e;
-    }
-#undef A
-    if ((e = cudaMemsetAsync(j->obs, 0, (size_t)j->spec.nsweeps * sizeof(DevObs), st)) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(j->thr_dev, &j->thr, sizeof(uint64_t), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    const JobLayout o = job_layout(j->spec.L, j->TH, j->spec.nsweeps, j->pcc);
+    cudaError_t e = cudaMallocAsync(&j->block, o.total, st);
+    if (e != cudaSuccess) {
+        j->block = nullptr;
         return e;
-    return enqueue_hot_start(j->spin, (int64_t)N, j->spec.seed, st);
+    }
+    unsigned char *b = static_cast<unsigned char *>(j->block);
+    j->spin = b + o.spin;
+    j->label = reinterpret_cast<int32_t *>(b + o.label);
+    j->code = reinterpret_cast<uint16_t *>(b + o.code);
+    j->bondbits = reinterpret_cast<uint32_t *>(b + o.bondbits);
+    j->cross = reinterpret_cast<uint32_t *>(b + o.cross);
+    j->npar = reinterpret_cast<int32_t *>(b + o.npar);
+    j->nkey = reinterpret_cast<int32_t *>(b + o.nkey);
+    j->nfinal = reinterpret_cast<uint32_t *>(b + o.nfinal);
+    j->thr_dev = reinterpret_cast<uint64_t *>(b + o.thr);
+    j->obs = reinterpret_cast<DevObs *>(b + o.obs);
+    if (j->pcc) {
+        j->pmask = reinterpret_cast<uint32_t *>(b + o.pmask);
+        j->cid = reinterpret_cast<int32_t *>(b + o.cid);
+        j->cand = reinterpret_cast<int32_t *>(b + o.cand);
+        j->ncand = reinterpret_cast<int32_t *>(b + o.ncand);
+        j->cov = reinterpret_cast<uint32_t *>(b + o.cov);
+        if ((e = cudaMemsetAsync(b + o.pmask, 0, o.pcc_end - o.pmask, st)) != cudaSuccess) return e;
+    }
+    return enqueue_job_init(j->spin, (int64_t)N, j->spec.seed, j->obs, (int64_t)j->spec.nsweeps * sizeof(DevObs),
+                            j->thr_dev, j->thr, st);
 }
 
 Replica replica_of(const Job *j)
@@ -230,35 +255,53 @@ cudaError_t lane_reserve(Lane &ln, int tiles, int reps)
         Replica empty{};
         ln.reps_host.resize(cap, empty);
         ln.slot_job.resize(cap, nullptr);
+        for (int i = cap - 1; i >= ln.cap_reps; --i) ln.free_slots.push_back(i);
         ln.cap_reps = cap;
         ln.dirty = ln.recapture = true;
     }
     return cudaSuccess;
 }
 
-// First run of `n` free tiles in the lane's table (growing it if needed).
+// `n` free tiles in a row in the lane's table: after the last used tile when
+// they fit there, else the first run of free tiles, else new capacity.
 int lane_place_tiles(Lane &ln, int n)
 {
-    int run = 0;
-    for (int i = 0; i < ln.cap_tiles; ++i) {
-        run = ln.tile_rep_host[i] < 0 ? run + 1 : 0;
-        if (run == n) return i - n + 1;
+    int start = -1;
+    if (ln.tail + n <= ln.cap_tiles) {
+        start = ln.tail;
+    } else {
+        int run = 0;
+        for (int i = 0; i < ln.tail && start < 0; ++i) {
+            run = ln.tile_rep_host[i] < 0 ? run + 1 : 0;
+            if (run == n) start = i - n + 1;
+        }
+        if (start < 0) {
+            start = ln.tail;
+            if (lane_reserve(ln, start + n, ln.cap_reps) != cudaSuccess) return -1;
+        }
     }
-    // trailing free tiles plus new capacity
-    int tail = 0;
-    for (int i = ln.cap_tiles - 1; i >= 0 && ln.tile_rep_host[i] < 0; --i) ++tail;
-    const int start = ln.cap_tiles - tail;
-    if (lane_reserve(ln, start + n, ln.cap_reps) != cudaSuccess) return -1;
+    ln.tail = std::max(ln.tail, start + n);
     return start;
 }
 
 int lane_free_slot(Lane &ln)
 {
-    for (int i = 0; i < ln.cap_reps; ++i)
-        if (!ln.slot_job[i]) return i;
-    const int s = ln.cap_reps;
-    if (lane_reserve(ln, ln.cap_tiles, s + 1) != cudaSuccess) return -1;
+    if (ln.free_slots.empty() && lane_reserve(ln, ln.cap_tiles, ln.cap_reps + 1) != cudaSuccess) return -1;
+    const int s = ln.free_slots.back();
+    ln.free_slots.pop_back();
     return s;
+}
+
+// Gives a retired lattice's tiles and slot back.
+void lane_release(Lane &ln, Job *j)
+{
+    for (int i = 0; i < j->n_tiles; ++i) ln.tile_rep_host[j->tile_base + i] = -1;
+    while (ln.tail > 0 && ln.tile_rep_host[ln.tail - 1] < 0) --ln.tail;
+    ln.slot_job[j->slot] = nullptr;
+    ln.reps_host[j->slot] = Replica{};
+    ln.free_slots.push_back(j->slot);
+    ln.active -= 1;
+    ln.dirty = true;
 }
 
 SweepArgs lane_args(Lane &ln)
@@ -304,44 +347,95 @@ double secs(Clock::time_point a, Clock::time_point b)
     return std::chrono::duration<double>(b - a).count();
 }
 
-// Copy a finished job's outputs to the caller and summarise it.
-int retire(sw_server *s, Job *j, sw_result *res)
+// Copy finished jobs' outputs to their callers, summarise them and free
+// them: every job's observables go through one pinned staging buffer, with
+// one wait per lane instead of one per job.
+void retire_all(sw_server *s, const std::vector<Job *> &done)
 {
-    Lane &ln = s->lanes[j->lane];
-    cudaStream_t st = ln.stream;
-    std::vector<DevObs> obs((size_t)j->spec.nsweeps);
-    cudaError_t e = cudaMemcpyAsync(obs.data(), j->obs, obs.size() * sizeof(DevObs), cudaMemcpyDeviceToHost, st);
-    const size_t N = (size_t)j->spec.L * j->spec.L;
-    if (e == cudaSuccess && j->spec.spins_out)
-        e = cudaMemcpyAsync(j->spec.spins_out, j->spin, N, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && j->spec.labels_out)
-        e = cudaMemcpyAsync(j->spec.labels_out, j->label, N * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    uint64_t thr = j->thr;
-    if (e == cudaSuccess && j->pcc) e = cudaMemcpyAsync(&thr, j->thr_dev, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    std::memset(res, 0, sizeof(*res));
-    res->status = e == cudaSuccess ? SW_OK : SW_ERR_CUDA;
-    res->L = j->spec.L;
-    res->nsweeps = j->spec.nsweeps;
-    res->tile_h = j->TH;
-    res->threshold = thr;
-    for (const DevObs &o : obs) {
-        res->sum_bond_sum += (int64_t)o.bond_sum;
-        res->sum_abs_mag += std::llabs((long long)o.mag);
-        res->sum_nclusters += (int64_t)o.nclusters;
+    size_t need = 0;
+    for (Job *j : done) need += (size_t)j->spec.nsweeps + 1;   // + one record for the threshold
+    DevObs *stage = s->stage;
+    std::vector<DevObs> heap;
+    if (need > s->stage_cap) {
+        std::lock_guard<std::mutex> lk(sw_capture_mutex());
+        if (s->stage) cudaFreeHost(s->stage);
+        s->stage = nullptr;
+        s->stage_cap = 0;
+        const size_t cap = std::max(need, (size_t)2 * s->stage_cap + 4096);
+        if (cudaMallocHost(&s->stage, cap * sizeof(DevObs)) == cudaSuccess) {
+            s->stage_cap = cap;
+        } else {
+            cudaGetLastError();
+            s->stage = nullptr;
+        }
+        stage = s->stage;
     }
-    if (j->spec.obs_out) std::memcpy(j->spec.obs_out, obs.data(), obs.size() * sizeof(DevObs));
+    if (!stage) {   // no pinned memory: plain host memory (the copies then wait)
+        heap.resize(need);
+        stage = heap.data();
+    }
+    std::vector<size_t> at(done.size());
+    std::vector<cudaError_t> err(done.size(), cudaSuccess);
+    bool used[N_LANES] = {};
+    size_t off = 0;
+    for (size_t i = 0; i < done.size(); ++i) {
+        Job *j = done[i];
+        const cudaStream_t st = s->lanes[j->lane].stream;
+        used[j->lane] = true;
+        at[i] = off;
+        const size_t nobs = (size_t)j->spec.nsweeps, N = (size_t)j->spec.L * j->spec.L;
+        cudaError_t e = cudaMemcpyAsync(stage + off, j->obs, nobs * sizeof(DevObs), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && j->pcc)
+            e = cudaMemcpyAsync(stage + off + nobs, j->thr_dev, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && j->spec.spins_out)
+            e = cudaMemcpyAsync(j->spec.spins_out, j->spin, N, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && j->spec.labels_out)
+            e = cudaMemcpyAsync(j->spec.labels_out, j->label, N * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        err[i] = e;
+        off += nobs + 1;
+    }
+    cudaError_t lane_err[N_LANES] = {};
+    for (int l = 0; l < N_LANES; ++l)
+        if (used[l]) lane_err[l] = cudaStreamSynchronize(s->lanes[l].stream);
+    std::vector<sw_result> res(done.size());
     const auto now = Clock::now();
-    res->queued_s = secs(j->t_submit, j->t_admit);
-    res->run_s = secs(j->t_admit, now);
-    // release the lattice's tiles and slot
-    for (int i = 0; i < j->n_tiles; ++i) ln.tile_rep_host[j->tile_base + i] = -1;
-    ln.slot_job[j->slot] = nullptr;
-    ln.reps_host[j->slot] = Replica{};
-    ln.active -= 1;
-    ln.dirty = true;
-    free_job_device(j, st);
-    return res->status;
+    for (size_t i = 0; i < done.size(); ++i) {
+        Job *j = done[i];
+        Lane &ln = s->lanes[j->lane];
+        const size_t nobs = (size_t)j->spec.nsweeps;
+        const DevObs *obs = stage + at[i];
+        sw_result &r = res[i];
+        std::memset(&r, 0, sizeof(r));
+        r.status = (err[i] == cudaSuccess && lane_err[j->lane] == cudaSuccess) ? SW_OK : SW_ERR_CUDA;
+        r.L = j->spec.L;
+        r.nsweeps = j->spec.nsweeps;
+        r.tile_h = j->TH;
+        r.threshold = j->thr;
+        if (j->pcc) std::memcpy(&r.threshold, obs + nobs, sizeof(uint64_t));
+        for (size_t k = 0; k < nobs; ++k) {
+            r.sum_bond_sum += (int64_t)obs[k].bond_sum;
+            r.sum_abs_mag += std::llabs((long long)obs[k].mag);
+            r.sum_nclusters += (int64_t)obs[k].nclusters;
+        }
+        if (j->spec.obs_out) std::memcpy(j->spec.obs_out, obs, nobs * sizeof(DevObs));
+        r.queued_s = secs(j->t_submit, j->t_admit);
+        r.run_s = secs(j->t_admit, now);
+        lane_release(ln, j);
+        free_job_device(j, ln.stream);
+    }
+    // the frees complete before the budget counts the bytes as available
+    for (int l = 0; l < N_LANES; ++l)
+        if (used[l]) cudaStreamSynchronize(s->lanes[l].stream);
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (size_t i = 0; i < done.size(); ++i) {
+        Job *j = done[i];
+        s->used -= j->bytes;
+        s->finished[j->id] = res[i];
+        s->stats.finished += 1;
+        s->stats.site_updates += (int64_t)j->spec.L * j->spec.L * j->spec.nsweeps;
+        delete j;
+    }
+    s->cv_done.notify_all();
 }
 
 void worker_main(sw_server *s)
@@ -380,6 +474,7 @@ void worker_main(sw_server *s)
             if (rc == SW_OK) {
                 j->slot = lane_free_slot(ln);
                 j->tile_base = j->slot >= 0 ? lane_place_tiles(ln, j->n_tiles) : -1;
+                if (j->slot >= 0 && j->tile_base < 0) ln.free_slots.push_back(j->slot);
                 if (j->slot < 0 || j->tile_base < 0) rc = SW_ERR_NOMEM;
             }
             if (rc != SW_OK) {
@@ -442,24 +537,16 @@ void worker_main(sw_server *s)
             s->stats.launches += GROUPS_PER_STEP;
         }
         // ---- retire lattices whose last launch (jstart + nsweeps) has run
+        std::vector<Job *> done;
         for (auto it = s->running.begin(); it != s->running.end();) {
-            Job *j = *it;
-            if ((int64_t)j->jstart + j->spec.nsweeps < (int64_t)s->launch_index) {
-                sw_result res;
-                retire(s, j, &res);
-                cudaStreamSynchronize(s->lanes[j->lane].stream);
-                std::lock_guard<std::mutex> lk(s->mu);
-                s->used -= j->bytes;
-                s->finished[j->id] = res;
-                s->stats.finished += 1;
-                s->stats.site_updates += (int64_t)j->spec.L * j->spec.L * j->spec.nsweeps;
-                s->cv_done.notify_all();
-                delete j;
+            if ((int64_t)(*it)->jstart + (*it)->spec.nsweeps < (int64_t)s->launch_index) {
+                done.push_back(*it);
                 it = s->running.erase(it);
             } else {
                 ++it;
             }
         }
+        if (!done.empty()) retire_all(s, done);
     }
     cudaStreamDestroy(cap_stream);
 }
@@ -530,6 +617,7 @@ int sw_server_destroy(sw_server *s)
         if (ln.jbase_dev) cudaFree(ln.jbase_dev);
         if (ln.stream) cudaStreamDestroy(ln.stream);
     }
+    if (s->stage) cudaFreeHost(s->stage);
     delete s;
     return SW_OK;
 }
@@ -628,9 +716,60 @@ int sw_batch_wait_all(sw_server *s, double timeout_s)
     return s->worker_error;
 }
 
-// Autotuner: time a short run of an L_b x L_b lattice (L_b = L rounded up to a
-// power of two) for every tile height that fits and keep the fastest, per
-// (L_b, temperature regime).  Any height gives the same results.
+}  // extern "C"
+
+namespace {
+
+// Seconds per site update of tile height th on a batch of lattices of side
+// Lb (about 2^23 sites together, 20 sweeps) run through a private server:
+// the throughput that batched and served runs see, where a single small
+// lattice would leave most of the GPU idle and time latency instead.  The
+// faster of two runs (the first one also captures the lane's graph).
+double batch_cost(int Lb, double T, int th)
+{
+    sw_server *srv = nullptr;
+    if (sw_server_create(&srv, 0, 0) != SW_OK) return 0.0;
+    const int m = std::max(2, (1 << 23) / (Lb * Lb));
+    const int nsw = 20;
+    std::vector<sw_job> jobs((size_t)m);
+    for (int r = 0; r < m; ++r) {
+        sw_job &q = jobs[(size_t)r];
+        std::memset(&q, 0, sizeof(q));
+        q.L = Lb;
+        q.kind = SW_JOB_SW;
+        q.J = 1.0;
+        q.T = T;
+        q.seed = 12345 + (uint64_t)r;
+        q.nsweeps = nsw;
+        q.tile_h = th;
+    }
+    std::vector<uint64_t> ids((size_t)m);
+    double best = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {
+        const auto t0 = Clock::now();
+        if (sw_batch_submit(srv, jobs.data(), m, ids.data()) != SW_OK || sw_batch_wait_all(srv, 120.0) != SW_OK) {
+            best = 0.0;
+            break;
+        }
+        const double dt = secs(t0, Clock::now());
+        if (rep == 0 || dt < best) best = dt;
+        sw_result r;
+        for (uint64_t id : ids) sw_batch_poll(srv, id, &r);
+    }
+    sw_server_destroy(srv);
+    return best / ((double)m * Lb * Lb * nsw);
+}
+
+}  // namespace
+
+extern "C" {
+
+// Autotuner: per (L_b, temperature regime), with L_b = L rounded up to a power
+// of two, time every tile height that fits and keep the fastest.  Up to
+// 2048 x 2048 sites the candidates run as a batch of L_b x L_b lattices
+// through the server (batched and served runs share the GPU among many
+// lattices, so throughput is what counts); larger lattices fill the GPU on
+// their own and are timed alone.  Any height gives the same results.
 int sw_autotune(int32_t L, double T, int32_t *tile_h_out)
 {
     if (!tile_h_out || L < 2 || !(T > 0.0)) return SW_ERR_ARG;
@@ -654,8 +793,22 @@ int sw_autotune(int32_t L, double T, int32_t *tile_h_out)
     const int n = (int)std::min(200.0, std::max(4.0, target / ((double)Lb * Lb)));
     int best = Lb <= 32 ? 32 : (Lb <= 64 ? 64 : 128);
     double best_t = 1e300;
+    const bool batch = (int64_t)Lb * Lb <= ((int64_t)1 << 22);
+    if (Lb <= 32) {   // one candidate: nothing to time
+        cache[key] = 32;
+        *tile_h_out = 32;
+        return SW_OK;
+    }
     for (int c = 0; c < 4; ++c) {
         if (heights[c] > std::max(32, Lb)) continue;
+        if (batch) {
+            const double cost = batch_cost(Lb, Trep, heights[c]);
+            if (cost > 0.0 && cost < best_t) {
+                best_t = cost;
+                best = heights[c];
+            }
+            continue;
+        }
         sw_ctx *ctx = nullptr;
         if (sw_create(&ctx, Lb, 1.0, Trep, 12345, flags[c]) != SW_OK) continue;
         // direct launches with events around every kernel (no graph capture,
