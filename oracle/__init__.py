@@ -94,7 +94,7 @@ def lib():
             L.swo_threshold_p.restype = u64
             L.swo_hot_start.argtypes = [i32, u64, P]
             L.swo_hot_start.restype = None
-            L.swo_bonds.argtypes = [i32, u64, u64, u64, P, P]
+            L.swo_bonds.argtypes = [i32, u64, u64, u64, P, P, i32]
             L.swo_bonds.restype = i64
             L.swo_label.argtypes = [i32, P, P]
             L.swo_label.restype = i64
@@ -102,15 +102,17 @@ def lib():
             L.swo_count_clusters_batch.restype = None
             L.swo_assign.argtypes = [i32, u64, u64, P, P]
             L.swo_assign.restype = None
-            L.swo_measure.argtypes = [i32, P, P, P]
+            L.swo_measure.argtypes = [i32, P, i32, P, P]
             L.swo_measure.restype = None
             L.swo_spans.argtypes = [i32, P, P, P]
             L.swo_spans.restype = ctypes.c_int
+            L.swo_spans_open.argtypes = [i32, P, P, P]
+            L.swo_spans_open.restype = ctypes.c_int
             L.swo_pcc_delta.argtypes = [u64]
             L.swo_pcc_delta.restype = u64
             L.swo_pcc_update.argtypes = [u64, u64, i32]
             L.swo_pcc_update.restype = u64
-            L.swo_run.argtypes = [i32, u64, u64, i32, i32, P, P, P, P, P]
+            L.swo_run.argtypes = [i32, u64, u64, i32, i32, i32, P, P, P, P, P]
             L.swo_run.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -147,10 +149,10 @@ def hot_start(L: int, seed: int) -> np.ndarray:
     return spin
 
 
-def bonds(L: int, seed: int, sweep: int, thr: int, spin: np.ndarray):
+def bonds(L: int, seed: int, sweep: int, thr: int, spin: np.ndarray, open: bool = False):
     spin = np.ascontiguousarray(spin, dtype=np.uint8)
     bond = np.empty(L * L, dtype=np.uint8)
-    nb = lib().swo_bonds(L, seed, sweep, thr, _ptr(spin), _ptr(bond))
+    nb = lib().swo_bonds(L, seed, sweep, thr, _ptr(spin), _ptr(bond), 1 if open else 0)
     return bond, int(nb)
 
 
@@ -175,11 +177,11 @@ def assign(L: int, seed: int, sweep: int, lab: np.ndarray) -> np.ndarray:
     return spin
 
 
-def measure(L: int, spin: np.ndarray):
+def measure(L: int, spin: np.ndarray, open: bool = False):
     spin = np.ascontiguousarray(spin, dtype=np.uint8)
     bs = np.zeros(1, dtype=np.int64)
     m = np.zeros(1, dtype=np.int64)
-    lib().swo_measure(L, _ptr(spin), _ptr(bs), _ptr(m))
+    lib().swo_measure(L, _ptr(spin), 1 if open else 0, _ptr(bs), _ptr(m))
     return int(bs[0]), int(m[0])
 
 
@@ -192,6 +194,15 @@ def spans(L: int, lab: np.ndarray):
     return int(sx[0]), int(sy[0])
 
 
+def spans_open(L: int, lab: np.ndarray):
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    sx = np.zeros(1, dtype=np.int32)
+    sy = np.zeros(1, dtype=np.int32)
+    if lib().swo_spans_open(L, _ptr(lab), _ptr(sx), _ptr(sy)) != 0:
+        raise MemoryError("swo_spans_open")
+    return int(sx[0]), int(sy[0])
+
+
 def pcc_delta(sweep: int) -> int:
     return int(lib().swo_pcc_delta(sweep))
 
@@ -201,13 +212,14 @@ def pcc_update(thr: int, sweep: int, flag: bool) -> int:
 
 
 class Chain:
-    """A lattice state advanced by the oracle: (spins, seed, sweep, threshold)."""
+    """A lattice state advanced by the oracle: (spins, seed, sweep, threshold);
+    open=True gives open boundaries."""
 
     def __init__(self, L: int, seed: int, thr: int, pcc: bool = False,
-                 spin: np.ndarray | None = None, sweep: int = 0):
+                 spin: np.ndarray | None = None, sweep: int = 0, open: bool = False):
         if L < 2:
             raise ValueError("L must be >= 2")
-        self.L, self.seed, self.pcc = int(L), int(seed), bool(pcc)
+        self.L, self.seed, self.pcc, self.open = int(L), int(seed), bool(pcc), bool(open)
         self.thr = np.array([thr], dtype=np.uint64)
         self.sweep = int(sweep)
         self.spin = hot_start(L, seed) if spin is None else np.array(spin, dtype=np.uint8).ravel()
@@ -223,7 +235,7 @@ class Chain:
         if nsweeps <= 0:
             return obs
         rc = lib().swo_run(self.L, self.seed, self.sweep, nsweeps, 1 if self.pcc else 0,
-                           _ptr(self.thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond),
+                           1 if self.open else 0, _ptr(self.thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond),
                            _ptr(obs))
         if rc != 0:
             raise MemoryError("swo_run")
@@ -231,16 +243,16 @@ class Chain:
         return obs
 
 
-def sw_chain(L: int, J: float, T: float, seed: int) -> Chain:
-    return Chain(L, seed, threshold_T(J, T))
+def sw_chain(L: int, J: float, T: float, seed: int, open: bool = False) -> Chain:
+    return Chain(L, seed, threshold_T(J, T), open=open)
 
 
-def sw_chain_p(L: int, p: float, seed: int) -> Chain:
-    return Chain(L, seed, threshold_p(p))
+def sw_chain_p(L: int, p: float, seed: int, open: bool = False) -> Chain:
+    return Chain(L, seed, threshold_p(p), open=open)
 
 
-def pcc_chain(L: int, seed: int) -> Chain:
-    return Chain(L, seed, 1 << 31, pcc=True)
+def pcc_chain(L: int, seed: int, open: bool = False) -> Chain:
+    return Chain(L, seed, 1 << 31, pcc=True, open=open)
 
 
 def energy_per_site(obs: np.ndarray, L: int, J: float = 1.0) -> np.ndarray:

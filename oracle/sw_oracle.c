@@ -130,19 +130,32 @@ static uint64_t neighbour(int32_t L, uint64_t i, int d)
     return ((y + 1) % (uint64_t)L) * (uint64_t)L + x;
 }
 
+/* Does link d of site i exist?  Under periodic boundaries every link does;
+ * under open boundaries (Sec. III) the right link of the last column and the
+ * down link of the last row leave the lattice and do not exist. */
+static int link_exists(int32_t L, uint64_t i, int d, int32_t open)
+{
+    if (!open)
+        return 1;
+    uint64_t x = i % (uint64_t)L, y = i / (uint64_t)L;
+    return d == 0 ? x + 1 < (uint64_t)L : y + 1 < (uint64_t)L;
+}
+
 /* ------------------------------------------------------------------------
  * Step 1 (Sec. I; also DPM step 1 of Sec. II.B): traverse every link; a link
  * between equal spins becomes a bond with probability P.  Link l = 2i + d
  * draws word (l mod 4) of Philox(floor(l/4), k, BOND).
  * ---------------------------------------------------------------------- */
 int64_t swo_bonds(int32_t L, uint64_t seed, uint64_t sweep, uint64_t thr,
-                  const uint8_t *spin, uint8_t *bond)
+                  const uint8_t *spin, uint8_t *bond, int32_t open)
 {
     uint64_t N = (uint64_t)L * (uint64_t)L;
     int64_t nb = 0;
     for (uint64_t i = 0; i < N; i++) {
         uint8_t b = 0;
         for (int d = 0; d < 2; d++) {
+            if (!link_exists(L, i, d, open))
+                continue;
             uint64_t j = neighbour(L, i, d);
             uint64_t l = 2 * i + (uint64_t)d;
             uint32_t w[4];
@@ -255,7 +268,7 @@ void swo_assign(int32_t L, uint64_t seed, uint64_t sweep, const int32_t *label, 
 
 /* Energy E = -J * bond_sum with bond_sum = sum over links of sigma_i sigma_j
  * (the Hamiltonian of Sec. I), magnetisation M = sum of sigma_i. */
-void swo_measure(int32_t L, const uint8_t *spin, int64_t *bond_sum, int64_t *mag)
+void swo_measure(int32_t L, const uint8_t *spin, int32_t open, int64_t *bond_sum, int64_t *mag)
 {
     uint64_t N = (uint64_t)L * (uint64_t)L;
     int64_t bs = 0, m = 0;
@@ -263,6 +276,8 @@ void swo_measure(int32_t L, const uint8_t *spin, int64_t *bond_sum, int64_t *mag
         int64_t si = 2 * (int64_t)spin[i] - 1;
         m += si;
         for (int d = 0; d < 2; d++) {
+            if (!link_exists(L, i, d, open))
+                continue;
             int64_t sj = 2 * (int64_t)spin[neighbour(L, i, d)] - 1;
             bs += si * sj;
         }
@@ -320,6 +335,34 @@ int swo_spans(int32_t L, const int32_t *label, int32_t *spans_x, int32_t *spans_
 }
 
 /* ------------------------------------------------------------------------
+ * Percolation under open boundaries (Sec. III): a cluster spans x iff it
+ * holds a site of the leftmost column and a site of the rightmost column
+ * (spans y: topmost and bottommost rows).
+ * ---------------------------------------------------------------------- */
+int swo_spans_open(int32_t L, const int32_t *label, int32_t *spans_x, int32_t *spans_y)
+{
+    int64_t N = (int64_t)L * (int64_t)L;
+    uint8_t *mark = (uint8_t *)calloc((size_t)N, 1);
+    if (!mark)
+        return -1;
+    /* bit 0: the root has a site in column 0; bit 1: in row 0 */
+    for (int32_t b = 0; b < L; b++) {
+        mark[label[(int64_t)b * L]] |= 1;
+        mark[label[b]] |= 2;
+    }
+    *spans_x = 0;
+    *spans_y = 0;
+    for (int32_t b = 0; b < L; b++) {
+        if (mark[label[(int64_t)b * L + (L - 1)]] & 1)
+            *spans_x = 1;
+        if (mark[label[(int64_t)(L - 1) * L + b]] & 2)
+            *spans_y = 1;
+    }
+    free(mark);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
  * PCC feedback (the probability-changing cluster method the paper builds
  * on, Sec. I and Sec. III): after sweep k lower p if the clusters of that
  * sweep percolate, raise it otherwise.  The step is 2^-8 in p for sweeps
@@ -346,7 +389,7 @@ uint64_t swo_pcc_update(uint64_t thr, uint64_t sweep, int32_t flag)
 /* ------------------------------------------------------------------------
  * Whole sweeps, step by step in the paper's order (Sec. I steps 1-4).
  * ---------------------------------------------------------------------- */
-int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc,
+int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc, int32_t open,
             uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
 {
     int64_t N = (int64_t)L * (int64_t)L;
@@ -360,12 +403,14 @@ int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t 
         swo_obs o;
         memset(&o, 0, sizeof(o));
         o.threshold = t;
-        o.nbonds = swo_bonds(L, seed, k, t, spin, b);    /* step 1 */
+        o.nbonds = swo_bonds(L, seed, k, t, spin, b, open); /* step 1 */
         o.nclusters = swo_label(L, b, label);            /* step 2 */
         swo_assign(L, seed, k, label, spin);             /* step 3 */
-        swo_measure(L, spin, &o.bond_sum, &o.mag);
+        swo_measure(L, spin, open, &o.bond_sum, &o.mag);
         if (pcc) {
-            if (swo_spans(L, label, &o.spans_x, &o.spans_y) != 0) {
+            int src = open ? swo_spans_open(L, label, &o.spans_x, &o.spans_y)
+                           : swo_spans(L, label, &o.spans_x, &o.spans_y);
+            if (src != 0) {
                 rc = -1;
                 break;
             }

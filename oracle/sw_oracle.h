@@ -16,6 +16,8 @@
  *   - Spins are stored as uint8 s in {0,1}; sigma = 2*s - 1.
  *   - Bond bytes: bit 0 = link d=0 (right) is bonded, bit 1 = link d=1 (down).
  *   - Labels: int32 root(i) = the minimum site index of i's cluster.
+ *   - open != 0 selects open (free) boundaries: the right link of column L-1
+ *     and the down link of row L-1 do not exist (no bond, no energy term).
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11).  Key = (seed mod 2^32, seed >> 32).
@@ -60,7 +62,7 @@ void swo_hot_start(int32_t L, uint64_t seed, uint8_t *spin);
 
 /* Step 1: bond activation of sweep k.  Returns the number of bonds. */
 int64_t swo_bonds(int32_t L, uint64_t seed, uint64_t sweep, uint64_t thr,
-                  const uint8_t *spin, uint8_t *bond);
+                  const uint8_t *spin, uint8_t *bond, int32_t open);
 
 /* Step 2: clusters by Hoshen-Kopelman raster scan + union-find, labels are
  * the minimum site index of each cluster.  Returns the number of clusters. */
@@ -73,12 +75,17 @@ void swo_count_clusters_batch(int32_t L, int64_t nsets, const uint8_t *bonds, in
 void swo_assign(int32_t L, uint64_t seed, uint64_t sweep, const int32_t *label, uint8_t *spin);
 
 /* Energy and magnetisation sums of a spin field. */
-void swo_measure(int32_t L, const uint8_t *spin, int64_t *bond_sum, int64_t *mag);
+void swo_measure(int32_t L, const uint8_t *spin, int32_t open, int64_t *bond_sum, int64_t *mag);
 
 /* Extension rule under periodic boundaries (paper, Sec. III): spans_x is 1 iff
  * some cluster occupies all L columns, spans_y iff some cluster occupies all
  * L rows.  Returns 0, or -1 when memory is short. */
 int swo_spans(int32_t L, const int32_t *label, int32_t *spans_x, int32_t *spans_y);
+
+/* Percolation under open boundaries (paper, Sec. III): spans_x is 1 iff some
+ * cluster touches both the leftmost and the rightmost column, spans_y iff
+ * some cluster touches both the topmost and the bottommost row. */
+int swo_spans_open(int32_t L, const int32_t *label, int32_t *spans_x, int32_t *spans_y);
 
 /* PCC feedback step size after sweep k, in threshold units. */
 uint64_t swo_pcc_delta(uint64_t sweep);
@@ -87,10 +94,11 @@ uint64_t swo_pcc_update(uint64_t thr, uint64_t sweep, int32_t flag);
 
 /* nsweeps full sweeps k = sweep0 .. sweep0+nsweeps-1 on spin[] in place.
  * *thr is the threshold of the first sweep; with pcc != 0 it is updated by
- * the feedback after every sweep.  label[] receives the labels of the last
+ * the feedback after every sweep (spans by swo_spans, or swo_spans_open when
+ * open != 0).  label[] receives the labels of the last
  * sweep, bond[] (optional, may be NULL) its bonds, obs[nsweeps] the
  * per-sweep observables.  Returns 0, or -1 when memory is short. */
-int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc,
+int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc, int32_t open,
             uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
 
 #ifdef __cplusplus
