@@ -59,18 +59,26 @@ extern "C" {
 #define SW_FLAG_TILE_64 (1u << 9)
 #define SW_FLAG_TILE_128 (1u << 10)
 #define SW_FLAG_TILE_96 (1u << 11)
+/* Open (free) boundaries instead of periodic ones (Sec. III treats both):
+ * the right link of column L-1 and the down link of row L-1 do not exist --
+ * they never bond and add nothing to bond_sum -- and the PCC span test is
+ * the open-boundary one (a cluster touches both opposite borders). */
+#define SW_FLAG_OPEN (1u << 12)
 
 typedef struct sw_ctx sw_ctx; /* opaque; owned by the library */
 
 /* Observables of one sweep, all taken after the cluster flip of Sec. I
  * step 3 (a reading: the paper does not say when it measures). */
 typedef struct {
-    int64_t bond_sum;   /* sum over all 2N links of sigma_i sigma_j; E = -J bond_sum */
+    int64_t bond_sum;   /* sum over the links (2N periodic, 2L(L-1) open) of
+                           sigma_i sigma_j; E = -J bond_sum                    */
     int64_t mag;        /* sum of sigma_i                                      */
     int64_t nclusters;  /* clusters built in this sweep (Sec. I step 2)        */
     int64_t nbonds;     /* bonded links in this sweep (Sec. I step 1)          */
-    int32_t spans_x;    /* PCC: a cluster occupies all L columns (Sec. III)    */
-    int32_t spans_y;    /* PCC: a cluster occupies all L rows (Sec. III)       */
+    int32_t spans_x;    /* PCC: a cluster occupies all L columns (Sec. III);
+                           open boundaries: it touches columns 0 and L-1,
+                           which is the same for clusters without wrap links */
+    int32_t spans_y;    /* PCC: the same for rows                              */
     uint64_t threshold; /* bond threshold t used in this sweep                 */
 } sw_obs;
 
@@ -81,6 +89,8 @@ typedef struct {
     uint64_t seed;
     uint64_t sweep;     /* sweeps done since creation = index of the next one */
     uint64_t threshold; /* threshold the next sweep will use                 */
+    int32_t open;       /* 1 for open boundaries (SW_FLAG_OPEN)              */
+    int32_t tile_h;     /* rows per tile                                     */
 } sw_state;
 
 /* Name of a status code (static string). */
@@ -204,6 +214,7 @@ typedef struct {
     sw_obs *obs_out;    /* optional: nsweeps entries, written before completion */
     uint8_t *spins_out; /* optional: L*L final spins                            */
     int32_t *labels_out;/* optional: L*L labels of the last sweep               */
+    uint32_t flags;     /* SW_FLAG_OPEN or 0 (tile heights go in tile_h)        */
 } sw_job;
 /* The caller owns obs_out/spins_out/labels_out; they must stay valid until
  * sw_batch_poll reports the job finished. */

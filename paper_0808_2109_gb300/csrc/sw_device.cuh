@@ -50,6 +50,7 @@ constexpr uint32_t STREAM_INIT = 0u, STREAM_BOND = 1u, STREAM_SPIN = 2u;
 
 // Replica flags.
 constexpr int32_t RF_PCC = 1;
+constexpr int32_t RF_OPEN = 2;   // open boundaries: the links leaving the lattice do not exist
 
 // Per-sweep observables as the device accumulates them (layout of sw_obs).
 struct DevObs {
@@ -512,6 +513,10 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     if (!fin && !start) return;
     const Tile t = tile_of(R, g, TH);
     const int L = R.L;
+    // open boundaries: the last tile column has no right link in its last
+    // column, the last tile row no down link in its last row
+    const bool open_r = (R.flags & RF_OPEN) && t.tx == R.tiles_x - 1;
+    const bool open_b = (R.flags & RF_OPEN) && t.ty == R.tiles_y - 1;
     // site indices fit in 32 bits (N <= 2^30)
     const uint32_t uL = (uint32_t)L;
     const uint32_t gbase = (uint32_t)t.y0 * uL + (uint32_t)t.x0;   // global index of local site 0
@@ -594,12 +599,13 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         for (int w = tid; w < t.th * TWW; w += NT) {
             const int y = w >> 2, c = w & 3;
             const uint32_t vm = valid_mask(c, t.tw);
+            const uint32_t vr = open_r ? valid_mask(c, t.tw - 1) : vm;   // sites with a right link
+            const uint32_t vd = (open_b && y == t.th - 1) ? 0u : vm;      // sites with a down link
             const uint32_t cur = sm.sp[y][c];
             const uint32_t right = (cur >> 1) | (sm.sp[y][c + 1] << 31);
             const uint32_t down = sm.sp[y + 1][c];
-            const int nv = __popc(vm);
-            bs += 2 * nv - 2 * (__popc((cur ^ right) & vm) + __popc((cur ^ down) & vm));
-            mag += 2 * __popc(cur & vm) - nv;
+            bs += __popc(vr) - 2 * __popc((cur ^ right) & vr) + __popc(vd) - 2 * __popc((cur ^ down) & vd);
+            mag += 2 * __popc(cur & vm) - __popc(vm);
         }
         long long v[4] = {bs, mag, 0, 0};
         DevObs *o = R.obs + jf;
@@ -656,11 +662,13 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             const uint32_t rhc = c == 0 ? rh[0] : c == 1 ? rh[1] : c == 2 ? rh[2] : rh[3];
             const uint32_t rvc = c == 0 ? rv[0] : c == 1 ? rv[1] : c == 2 ? rv[2] : rv[3];
             const uint32_t vm = valid_mask(c, t.tw);
+            const uint32_t vr = open_r ? valid_mask(c, t.tw - 1) : vm;
+            const uint32_t vd = (open_b && y == t.th - 1) ? 0u : vm;
             const uint32_t cur = sm.sp[y][c];
             const uint32_t right = (cur >> 1) | (sm.sp[y][c + 1] << 31);
             const uint32_t down = sm.sp[y + 1][c];
-            const uint32_t h = rhc & ~(cur ^ right) & vm;
-            const uint32_t v = rvc & ~(cur ^ down) & vm;
+            const uint32_t h = rhc & ~(cur ^ right) & vr;
+            const uint32_t v = rvc & ~(cur ^ down) & vd;
             sm.bh[y][c] = h;
             sm.bv[y][c] = v;
             // intra-tile parts: the last column's right link and the last

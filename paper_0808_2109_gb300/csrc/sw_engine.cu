@@ -186,6 +186,7 @@ struct sw_ctx {
     int tiles_x = 0, tiles_y = 0, n_tiles = 0, S = 0;
     uint64_t seed = 0;
     bool pcc = false;
+    bool open = false;
     uint64_t sweep = 0;
     uint64_t thr = 0;
     bool swept = false;
@@ -284,6 +285,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
     c->n_tiles = c->tiles_x * c->tiles_y;
     c->seed = seed;
     c->pcc = pcc;
+    c->open = (flags & SW_FLAG_OPEN) != 0;
     c->thr = thr;
     const size_t N = (size_t)L * L;
     const size_t nt = (size_t)c->n_tiles;
@@ -328,7 +330,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
     R.key0 = k0;
     R.key1 = k1;
     R.nsweeps = 0;
-    R.flags = pcc ? RF_PCC : 0;
+    R.flags = (pcc ? RF_PCC : 0) | (c->open ? RF_OPEN : 0);
     R.sweep0 = 0;
     R.thr = thr;
     R.thr_dev = c->thr_dev;
@@ -737,6 +739,8 @@ int sw_get_state(sw_ctx *ctx, sw_state *out)
     out->seed = ctx->seed;
     out->sweep = ctx->sweep;
     out->threshold = thr;
+    out->open = ctx->open ? 1 : 0;
+    out->tile_h = ctx->TH;
     return SW_OK;
 }
 

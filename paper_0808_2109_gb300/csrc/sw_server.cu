@@ -205,7 +205,7 @@ Replica replica_of(const Job *j)
     R.key0 = (uint32_t)j->spec.seed;
     R.key1 = (uint32_t)(j->spec.seed >> 32);
     R.nsweeps = j->spec.nsweeps;
-    R.flags = j->pcc ? RF_PCC : 0;
+    R.flags = (j->pcc ? RF_PCC : 0) | ((j->spec.flags & SW_FLAG_OPEN) ? RF_OPEN : 0);
     R.sweep0 = 0;
     R.thr = j->thr;
     R.thr_dev = j->thr_dev;
@@ -637,7 +637,7 @@ int sw_batch_submit(sw_server *s, const sw_job *jobs, int32_t n, uint64_t *ids_o
         }
         made.push_back(j);
         j->spec = q;
-        if (q.L < 2 || q.L > SERVER_MAX_L || q.nsweeps < 1 ||
+        if (q.L < 2 || q.L > SERVER_MAX_L || q.nsweeps < 1 || (q.flags & ~SW_FLAG_OPEN) != 0 ||
             (q.tile_h != 0 && q.tile_h != 32 && q.tile_h != 64 && q.tile_h != 96 && q.tile_h != 128)) {
             rc = SW_ERR_ARG;
             break;

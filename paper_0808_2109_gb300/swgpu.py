@@ -41,6 +41,8 @@ class SwState(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("sweep", ctypes.c_uint64),
         ("threshold", ctypes.c_uint64),
+        ("open", ctypes.c_int32),
+        ("tile_h", ctypes.c_int32),
     ]
 
 
@@ -57,6 +59,7 @@ class SwKernelStats(ctypes.Structure):
 
 SW_JOB_SW, SW_JOB_SWP, SW_JOB_PCC = 0, 1, 2
 SW_FLAG_TILE = {32: 1 << 8, 64: 1 << 9, 96: 1 << 11, 128: 1 << 10}
+SW_FLAG_OPEN = 1 << 12
 
 
 class SwJob(ctypes.Structure):
@@ -72,6 +75,7 @@ class SwJob(ctypes.Structure):
         ("obs_out", ctypes.c_void_p),
         ("spins_out", ctypes.c_void_p),
         ("labels_out", ctypes.c_void_p),
+        ("flags", ctypes.c_uint32),
     ]
 
 
@@ -270,7 +274,7 @@ def sw_get_state(h) -> dict:
     st = SwState()
     _check(lib().sw_get_state(h, ctypes.byref(st)), "sw_get_state")
     return {"L": st.L, "pcc": bool(st.pcc), "seed": st.seed, "sweep": st.sweep,
-            "threshold": st.threshold}
+            "threshold": st.threshold, "open": bool(st.open), "tile_h": st.tile_h}
 
 
 def sw_sync(h) -> None:
@@ -344,12 +348,13 @@ def sw_autotune(L: int, T: float) -> int:
 # -------------------------------------------------------------- convenience
 
 class Lattice:
-    """One L x L lattice on the GPU (plain SW at J, T or p; or PCC)."""
+    """One L x L lattice on the GPU (plain SW at J, T or p; or PCC), with
+    periodic or (open=True) open boundaries."""
 
     def __init__(self, L: int, *, J: float = 1.0, T: float | None = None, p: float | None = None,
-                 seed: int = 1, pcc: bool = False, tile_h: int = 0):
+                 seed: int = 1, pcc: bool = False, tile_h: int = 0, open: bool = False):
         self.L = int(L)
-        flags = SW_FLAG_TILE.get(int(tile_h), 0)
+        flags = SW_FLAG_TILE.get(int(tile_h), 0) | (SW_FLAG_OPEN if open else 0)
         if pcc:
             self.h = pcc_create(self.L, seed, flags)
         elif p is not None:
@@ -437,7 +442,7 @@ class Server:
 
     def submit(self, specs, want_obs=True, want_spins=False, want_labels=False) -> list[int]:
         """specs: dicts with L, sweeps, seed and T (plain), p, or pcc=True;
-        optional tile_h."""
+        optional tile_h and open=True (open boundaries)."""
         jobs, outs = [], []
         for sp in specs:
             L, n = int(sp["L"]), int(sp["sweeps"])
@@ -454,6 +459,7 @@ class Server:
             else:
                 j.kind, j.T = SW_JOB_SW, float(sp["T"])
             j.tile_h = int(sp.get("tile_h", 0))
+            j.flags = SW_FLAG_OPEN if sp.get("open") else 0
             j.obs_out = o["obs"].ctypes.data if want_obs else None
             j.spins_out = o["spins"].ctypes.data if want_spins else None
             j.labels_out = o["labels"].ctypes.data if want_labels else None
