@@ -47,6 +47,7 @@ class Obs(ctypes.Structure):
         ("spans_x", ctypes.c_int32),
         ("spans_y", ctypes.c_int32),
         ("threshold", ctypes.c_uint64),
+        ("csize2", ctypes.c_int64),
     ]
 
 
@@ -59,9 +60,10 @@ OBS_DTYPE = np.dtype(
         ("spans_x", "<i4"),
         ("spans_y", "<i4"),
         ("threshold", "<u8"),
+        ("csize2", "<i8"),
     ]
 )
-assert OBS_DTYPE.itemsize == ctypes.sizeof(Obs) == 48
+assert OBS_DTYPE.itemsize == ctypes.sizeof(Obs) == 56
 
 
 def build(force: bool = False) -> str:
@@ -108,11 +110,13 @@ def lib():
             L.swo_spans.restype = ctypes.c_int
             L.swo_spans_open.argtypes = [i32, P, P, P]
             L.swo_spans_open.restype = ctypes.c_int
+            L.swo_csize2.argtypes = [i32, P]
+            L.swo_csize2.restype = i64
             L.swo_pcc_delta.argtypes = [u64]
             L.swo_pcc_delta.restype = u64
             L.swo_pcc_update.argtypes = [u64, u64, i32]
             L.swo_pcc_update.restype = u64
-            L.swo_run.argtypes = [i32, u64, u64, i32, i32, i32, P, P, P, P, P]
+            L.swo_run.argtypes = [i32, u64, u64, i32, i32, i32, i32, P, P, P, P, P]
             L.swo_run.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -194,6 +198,14 @@ def spans(L: int, lab: np.ndarray):
     return int(sx[0]), int(sy[0])
 
 
+def csize2(L: int, lab: np.ndarray) -> int:
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    v = int(lib().swo_csize2(L, _ptr(lab)))
+    if v < 0:
+        raise MemoryError("swo_csize2")
+    return v
+
+
 def spans_open(L: int, lab: np.ndarray):
     lab = np.ascontiguousarray(lab, dtype=np.int32)
     sx = np.zeros(1, dtype=np.int32)
@@ -213,13 +225,15 @@ def pcc_update(thr: int, sweep: int, flag: bool) -> int:
 
 class Chain:
     """A lattice state advanced by the oracle: (spins, seed, sweep, threshold);
-    open=True gives open boundaries."""
+    open=True gives open boundaries, csize=True fills obs["csize2"]."""
 
     def __init__(self, L: int, seed: int, thr: int, pcc: bool = False,
-                 spin: np.ndarray | None = None, sweep: int = 0, open: bool = False):
+                 spin: np.ndarray | None = None, sweep: int = 0, open: bool = False,
+                 csize: bool = False):
         if L < 2:
             raise ValueError("L must be >= 2")
         self.L, self.seed, self.pcc, self.open = int(L), int(seed), bool(pcc), bool(open)
+        self.csize = bool(csize)
         self.thr = np.array([thr], dtype=np.uint64)
         self.sweep = int(sweep)
         self.spin = hot_start(L, seed) if spin is None else np.array(spin, dtype=np.uint8).ravel()
@@ -235,7 +249,7 @@ class Chain:
         if nsweeps <= 0:
             return obs
         rc = lib().swo_run(self.L, self.seed, self.sweep, nsweeps, 1 if self.pcc else 0,
-                           1 if self.open else 0, _ptr(self.thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond),
+                           1 if self.open else 0, 1 if self.csize else 0, _ptr(self.thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond),
                            _ptr(obs))
         if rc != 0:
             raise MemoryError("swo_run")
@@ -243,16 +257,16 @@ class Chain:
         return obs
 
 
-def sw_chain(L: int, J: float, T: float, seed: int, open: bool = False) -> Chain:
-    return Chain(L, seed, threshold_T(J, T), open=open)
+def sw_chain(L: int, J: float, T: float, seed: int, open: bool = False, csize: bool = False) -> Chain:
+    return Chain(L, seed, threshold_T(J, T), open=open, csize=csize)
 
 
-def sw_chain_p(L: int, p: float, seed: int, open: bool = False) -> Chain:
-    return Chain(L, seed, threshold_p(p), open=open)
+def sw_chain_p(L: int, p: float, seed: int, open: bool = False, csize: bool = False) -> Chain:
+    return Chain(L, seed, threshold_p(p), open=open, csize=csize)
 
 
-def pcc_chain(L: int, seed: int, open: bool = False) -> Chain:
-    return Chain(L, seed, 1 << 31, pcc=True, open=open)
+def pcc_chain(L: int, seed: int, open: bool = False, csize: bool = False) -> Chain:
+    return Chain(L, seed, 1 << 31, pcc=True, open=open, csize=csize)
 
 
 def energy_per_site(obs: np.ndarray, L: int, J: float = 1.0) -> np.ndarray:

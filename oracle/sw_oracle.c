@@ -266,6 +266,23 @@ void swo_assign(int32_t L, uint64_t seed, uint64_t sweep, const int32_t *label, 
     }
 }
 
+/* Sum of |C|^2 over the clusters: count the sites of every root, then sum
+ * the squares of the counts. */
+int64_t swo_csize2(int32_t L, const int32_t *label)
+{
+    int64_t N = (int64_t)L * (int64_t)L;
+    int64_t *count = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+    if (!count)
+        return -1;
+    for (int64_t i = 0; i < N; i++)
+        count[label[i]]++;
+    int64_t s = 0;
+    for (int64_t r = 0; r < N; r++)
+        s += count[r] * count[r];
+    free(count);
+    return s;
+}
+
 /* Energy E = -J * bond_sum with bond_sum = sum over links of sigma_i sigma_j
  * (the Hamiltonian of Sec. I), magnetisation M = sum of sigma_i. */
 void swo_measure(int32_t L, const uint8_t *spin, int32_t open, int64_t *bond_sum, int64_t *mag)
@@ -390,7 +407,7 @@ uint64_t swo_pcc_update(uint64_t thr, uint64_t sweep, int32_t flag)
  * Whole sweeps, step by step in the paper's order (Sec. I steps 1-4).
  * ---------------------------------------------------------------------- */
 int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc, int32_t open,
-            uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
+            int32_t csize, uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
 {
     int64_t N = (int64_t)L * (int64_t)L;
     uint8_t *b = bond ? bond : (uint8_t *)malloc((size_t)N);
@@ -405,6 +422,13 @@ int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t 
         o.threshold = t;
         o.nbonds = swo_bonds(L, seed, k, t, spin, b, open); /* step 1 */
         o.nclusters = swo_label(L, b, label);            /* step 2 */
+        if (csize) {
+            o.csize2 = swo_csize2(L, label);
+            if (o.csize2 < 0) {
+                rc = -1;
+                break;
+            }
+        }
         swo_assign(L, seed, k, label, spin);             /* step 3 */
         swo_measure(L, spin, open, &o.bond_sum, &o.mag);
         if (pcc) {

@@ -45,6 +45,7 @@ typedef struct {
     int32_t spans_x;    /* PCC only: some cluster occupies all L columns     */
     int32_t spans_y;    /* PCC only: some cluster occupies all L rows        */
     uint64_t threshold; /* bond threshold used in this sweep                 */
+    int64_t csize2;     /* sum over this sweep's clusters of |C|^2           */
 } swo_obs;
 
 /* Philox4x32-10 of one counter block. */
@@ -74,6 +75,11 @@ void swo_count_clusters_batch(int32_t L, int64_t nsets, const uint8_t *bonds, in
 /* Step 3: every cluster takes bit (root mod 128) of Philox(root/128, k, SPIN). */
 void swo_assign(int32_t L, uint64_t seed, uint64_t sweep, const int32_t *label, uint8_t *spin);
 
+/* Sum over the clusters of |C|^2, from the labels.  Each cluster takes an
+ * independent fair sign, so its mean over the flip is M^2: the cluster
+ * ("improved") estimator of the susceptibility. */
+int64_t swo_csize2(int32_t L, const int32_t *label);
+
 /* Energy and magnetisation sums of a spin field. */
 void swo_measure(int32_t L, const uint8_t *spin, int32_t open, int64_t *bond_sum, int64_t *mag);
 
@@ -95,11 +101,11 @@ uint64_t swo_pcc_update(uint64_t thr, uint64_t sweep, int32_t flag);
 /* nsweeps full sweeps k = sweep0 .. sweep0+nsweeps-1 on spin[] in place.
  * *thr is the threshold of the first sweep; with pcc != 0 it is updated by
  * the feedback after every sweep (spans by swo_spans, or swo_spans_open when
- * open != 0).  label[] receives the labels of the last
+ * open != 0).  csize != 0 fills obs[].csize2 (else it stays 0).  label[] receives the labels of the last
  * sweep, bond[] (optional, may be NULL) its bonds, obs[nsweeps] the
  * per-sweep observables.  Returns 0, or -1 when memory is short. */
 int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc, int32_t open,
-            uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
+            int32_t csize, uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
 
 #ifdef __cplusplus
 }
