@@ -305,7 +305,7 @@ def run_gb300(args):
         h_in, h_out = h_out, h_in
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": world * N * w.sweeps * e2e_steps / (e2e_s * 1e9), "unit": UNIT,
-           "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + w.sweeps * 48,
+           "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + w.sweeps * swgpu.OBS_DTYPE.itemsize,
            "steps": e2e_steps}
     del o
 

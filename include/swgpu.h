@@ -64,6 +64,11 @@ extern "C" {
  * they never bond and add nothing to bond_sum -- and the PCC span test is
  * the open-boundary one (a cluster touches both opposite borders). */
 #define SW_FLAG_OPEN (1u << 12)
+/* Also sum |C|^2 over every sweep's clusters into sw_obs.csize2 (two more
+ * int32 per border node of device memory).  Each cluster takes an independent
+ * fair sign, so the mean of csize2 is <M^2>: the cluster ("improved")
+ * estimator of the susceptibility, with a smaller variance than M^2. */
+#define SW_FLAG_CSIZE (1u << 13)
 
 typedef struct sw_ctx sw_ctx; /* opaque; owned by the library */
 
@@ -80,6 +85,8 @@ typedef struct {
                            which is the same for clusters without wrap links */
     int32_t spans_y;    /* PCC: the same for rows                              */
     uint64_t threshold; /* bond threshold t used in this sweep                 */
+    int64_t csize2;     /* SW_FLAG_CSIZE: sum over this sweep's clusters of
+                           |C|^2; 0 without the flag                          */
 } sw_obs;
 
 /* Snapshot of a lattice's scalar state (the spins are read separately). */
@@ -214,7 +221,8 @@ typedef struct {
     sw_obs *obs_out;    /* optional: nsweeps entries, written before completion */
     uint8_t *spins_out; /* optional: L*L final spins                            */
     int32_t *labels_out;/* optional: L*L labels of the last sweep               */
-    uint32_t flags;     /* SW_FLAG_OPEN or 0 (tile heights go in tile_h)        */
+    uint32_t flags;     /* SW_FLAG_OPEN, SW_FLAG_CSIZE or 0 (tile heights go in
+                           tile_h)                                              */
 } sw_job;
 /* The caller owns obs_out/spins_out/labels_out; they must stay valid until
  * sw_batch_poll reports the job finished. */

@@ -51,14 +51,16 @@ constexpr uint32_t STREAM_INIT = 0u, STREAM_BOND = 1u, STREAM_SPIN = 2u;
 // Replica flags.
 constexpr int32_t RF_PCC = 1;
 constexpr int32_t RF_OPEN = 2;   // open boundaries: the links leaving the lattice do not exist
+constexpr int32_t RF_CSIZE = 4;  // also sum |C|^2 over the clusters (psize, csize below)
 
 // Per-sweep observables as the device accumulates them (layout of sw_obs).
 struct DevObs {
     unsigned long long bond_sum, mag, nclusters, nbonds;
     int32_t spans_x, spans_y;
     unsigned long long threshold;
+    unsigned long long csize2;
 };
-static_assert(sizeof(DevObs) == 48, "DevObs must match sw_obs");
+static_assert(sizeof(DevObs) == 56, "DevObs must match sw_obs");
 
 // One lattice of a launch.  A single sw_sweep call is a batch of one.
 struct Replica {
@@ -88,7 +90,10 @@ struct Replica {
     int32_t *cid;           // tiles * S * 2: candidate id + 2 of a root node (x, y), 0 = none
     int32_t *cand;          // [2][L] candidate roots (x, then y)
     int32_t *ncand;         // [2] candidate counts
-    uint32_t *cov;          // [L][tiles_x][4] column coverage, then [L][tiles_y][4] row coverage
+    uint32_t *cov;
+    // cluster sizes (RF_CSIZE): sites of each border piece at its
+    // representative node, and of each cluster at its root node
+    int32_t *psize, *csize;          // [L][tiles_x][4] column coverage, then [L][tiles_y][4] row coverage
 };
 
 // A launch: every tile of every lattice in the tile table (entries of -1
@@ -275,9 +280,10 @@ struct TileCfg {
     static constexpr int NT = 4 * TH;           // threads per CTA
     static constexpr int NW = NT / 32;          // warps = sub-tiles
     static constexpr int SUBY = TH / 32;        // sub-tile rows
-    // CTAs per SM the register allocation must leave room for (96-row tiles:
-    // three, which the shared memory also allows)
-    static constexpr int MINB = TH == 96 ? 3 : 1;
+    // CTAs per SM the register allocation must leave room for: as many as
+    // the shared memory allows (at most 64 registers a thread; 56 for three
+    // 384-thread CTAs of 96-row tiles)
+    static constexpr int MINB = TH == 32 ? 8 : TH == 64 ? 4 : TH == 96 ? 3 : 2;
 };
 
 // Root of x without writing (a forest no thread is changing any more).
@@ -487,7 +493,12 @@ constexpr size_t tile_smem(bool pcc)
 }
 
 // ----------------------------------------------------------------- k_tile
-template <int TH>
+// Optional features of the tile kernel, compiled in only where a launch has a
+// lattice that needs them, so the plain kernel carries none of their code.
+constexpr int FEAT_CSIZE = 1;   // cluster sizes (RF_CSIZE)
+constexpr int FEAT_OPEN = 2;    // open boundaries (RF_OPEN)
+
+template <int TH, int F>
 __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(const SweepArgs a)
 {
     using SL = Slots<TH>;
@@ -515,8 +526,8 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     const int L = R.L;
     // open boundaries: the last tile column has no right link in its last
     // column, the last tile row no down link in its last row
-    const bool open_r = (R.flags & RF_OPEN) && t.tx == R.tiles_x - 1;
-    const bool open_b = (R.flags & RF_OPEN) && t.ty == R.tiles_y - 1;
+    const bool open_r = (F & FEAT_OPEN) && (R.flags & RF_OPEN) && t.tx == R.tiles_x - 1;
+    const bool open_b = (F & FEAT_OPEN) && (R.flags & RF_OPEN) && t.ty == R.tiles_y - 1;
     // site indices fit in 32 bits (N <= 2^30)
     const uint32_t uL = (uint32_t)L;
     const uint32_t gbase = (uint32_t)t.y0 * uL + (uint32_t)t.x0;   // global index of local site 0
@@ -607,9 +618,17 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             bs += __popc(vr) - 2 * __popc((cur ^ right) & vr) + __popc(vd) - 2 * __popc((cur ^ down) & vd);
             mag += 2 * __popc(cur & vm) - __popc(vm);
         }
-        long long v[4] = {bs, mag, 0, 0};
+        // clusters that touch a tile border: their sizes were summed at their
+        // root nodes by the merge; each root node is in exactly one tile
+        long long c2 = 0;
+        if ((F & FEAT_CSIZE) && (R.flags & RF_CSIZE))
+            for (int s = tid; s < S; s += NT) {
+                const long long c = R.csize[(size_t)t.lt * S + s];
+                c2 += c * c;
+            }
+        long long v[4] = {bs, mag, c2, 0};
         DevObs *o = R.obs + jf;
-        unsigned long long *const dst[4] = {&o->bond_sum, &o->mag, nullptr, nullptr};
+        unsigned long long *const dst[4] = {&o->bond_sum, &o->mag, &o->csize2, nullptr};
         block_sum_atomic<NT, 4>(v, dst, sm.red);
         __syncthreads();
     }
@@ -812,6 +831,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             R.npar[node] = (int32_t)node;
             R.nkey[node] = (int32_t)KEY_NONE;
         }
+        if ((F & FEAT_CSIZE) && (R.flags & RF_CSIZE)) R.csize[node] = 0;   // the merge adds piece sizes at root nodes
     }
     // Every run head learns its root; every interior root gets its record
     // (the cluster's new spin, Sec. I step 3, drawn here) and is counted.
@@ -844,6 +864,27 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         }
     }
     __syncthreads();
+    const bool csz = (F & FEAT_CSIZE) && (R.flags & RF_CSIZE) != 0;
+    if (csz) {
+        // cluster sizes: every run adds its length to bits 16-30 of its root's
+        // record (a piece holds at most TW*TH = 2^14 sites, an interior
+        // cluster at most (TW-2)(TH-2) < 2^14, so neither field overflows
+        // into the record's flag bits); the codes below read bits 0-15 only
+        for (int w = tid; w < t.th * TWW; w += NT) {
+            const int y = w % t.th, c = w / t.th;
+            const int base = y * PW + 32 * c;
+            const int vw = min(32, t.tw - 32 * c);   // real sites in this word
+            for (uint32_t bits = run_heads(sm.ih[y][c]); bits;) {
+                const int hx = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (hx >= vw) break;
+                const int nx = bits ? __ffs(bits) - 1 : 32;
+                const int v = sm.par[base + hx];
+                const int root = (v < 0 || (uint32_t)v >= INFO_INTERIOR) ? base + hx : v;
+                atomicAdd((int *)&sm.par[root], (min(nx, vw) - hx) << 16);
+            }
+        }
+    }
     // Every site's 2-byte code (the low half of its root's record): border
     // pieces by node slot, interior clusters by local root and new spin.
     // 8 sites per 16-byte store.
@@ -891,9 +932,29 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         __syncthreads();
         for (int q = tid; q < S * 8; q += NT) R.pmask[(size_t)t.lt * S * 8 + q] = (&sm.pm[0][0])[q];
     }
-    long long v4[4] = {nb, ncl_interior, 0, 0};
+    long long c2 = 0;
+    if (csz) {
+        // every root: an interior cluster adds its |C|^2; a border piece
+        // hands its size to its representative node for the merge
+        __syncthreads();
+        for (int w = tid; w < t.th * TWW; w += NT) {
+            const int y = w % t.th, c = w / t.th;
+            const int base = y * PW + 32 * c;
+            const int vw = min(32, t.tw - 32 * c);
+            for (uint32_t bits = run_heads(sm.ih[y][c]) & valid_mask(0, vw); bits; bits &= bits - 1) {
+                const int v = sm.par[base + __ffs(bits) - 1];
+                if (v < 0) {   // piece size: bits 16-30 (bit 31 is the border flag)
+                    R.psize[(size_t)t.lt * S + (v & 0x3FF)] = (int32_t)(((uint32_t)v >> 16) & 0x7FFFu);
+                } else if ((uint32_t)v >= INFO_INTERIOR) {   // bits 16-29 (bit 30 is the flag)
+                    const long long size = ((uint32_t)v >> 16) & 0x3FFFu;
+                    c2 += size * size;
+                }
+            }
+        }
+    }
+    long long v4[4] = {nb, ncl_interior, c2, 0};
     DevObs *o = R.obs + j;
-    unsigned long long *const dst[4] = {&o->nbonds, &o->nclusters, nullptr, nullptr};
+    unsigned long long *const dst[4] = {&o->nbonds, &o->nclusters, &o->csize2, nullptr};
     block_sum_atomic<NT, 4>(v4, dst, sm.red);
 }
 
@@ -1043,6 +1104,7 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
                 x = nx;
             }
             nroots += r[q] == n;
+            if (R.flags & RF_CSIZE) atomicAdd(R.csize + r[q], R.psize[n]);
             const U4 u = stream_block(R, rkey[q] >> 7, k, STREAM_SPIN);
             const int bit = rkey[q] & 127;
             const uint32_t spin = (u4_word(u, bit >> 5) >> (bit & 31)) & 1u;

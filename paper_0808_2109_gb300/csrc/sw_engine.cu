@@ -28,17 +28,25 @@ cudaError_t tile_prepare()
     static bool done = false;
     static cudaError_t err = cudaSuccess;
     if (!done) {
-        err = cudaFuncSetAttribute(k_tile<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)tile_smem<TH>(true));
+        const void *fn[4] = {(const void *)k_tile<TH, 0>, (const void *)k_tile<TH, 1>, (const void *)k_tile<TH, 2>,
+                             (const void *)k_tile<TH, 3>};
+        for (int f = 0; f < 4 && err == cudaSuccess; ++f)
+            err = cudaFuncSetAttribute(fn[f], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<TH>(true));
         done = true;
     }
     return err;
 }
 
 template <int TH>
-void launch_tile(const SweepArgs &a, bool pcc, cudaStream_t st)
+void launch_tile(const SweepArgs &a, bool pcc, int feat, cudaStream_t st)
 {
-    k_tile<TH><<<a.n_tiles, TileCfg<TH>::NT, tile_smem<TH>(pcc), st>>>(a);
+    const size_t smem = tile_smem<TH>(pcc);
+    switch (feat & 3) {
+    case 0: k_tile<TH, 0><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a); break;
+    case 1: k_tile<TH, 1><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a); break;
+    case 2: k_tile<TH, 2><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a); break;
+    default: k_tile<TH, 3><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a); break;
+    }
 }
 
 // The merge of launch group j: unions across tile edges, pointer jumping,
@@ -64,13 +72,13 @@ void launch_merge(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
     }
 }
 
-cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, cudaStream_t st)
+cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, int feat, cudaStream_t st)
 {
     switch (TH) {
-    case 32: launch_tile<32>(a, pcc, st); break;
-    case 64: launch_tile<64>(a, pcc, st); break;
-    case 96: launch_tile<96>(a, pcc, st); break;
-    default: launch_tile<128>(a, pcc, st); break;
+    case 32: launch_tile<32>(a, pcc, feat, st); break;
+    case 64: launch_tile<64>(a, pcc, feat, st); break;
+    case 96: launch_tile<96>(a, pcc, feat, st); break;
+    default: launch_tile<128>(a, pcc, feat, st); break;
     }
     return cudaGetLastError();
 }
@@ -87,9 +95,9 @@ cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int n_reps, cuda
 }
 
 // One launch group: the tile kernel of launch j, then the merge of sweep j.
-cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
+cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, bool pcc, int feat, int n_reps, cudaStream_t st)
 {
-    cudaError_t e = enqueue_tile(TH, a, pcc, st);
+    cudaError_t e = enqueue_tile(TH, a, pcc, feat, st);
     if (e != cudaSuccess) return e;
     return enqueue_merge(TH, a, pcc, n_reps, st);
 }
@@ -211,6 +219,8 @@ struct sw_ctx {
     uint32_t *pmask = nullptr;
     int32_t *cid = nullptr, *cand = nullptr, *ncand = nullptr;
     uint32_t *cov = nullptr;
+    // cluster sizes (SW_FLAG_CSIZE)
+    int32_t *psize = nullptr, *csize = nullptr;
 
     DevObs *obs = nullptr;
     int64_t obs_cap = 0, obs_head = 0, obs_tail = 0;
@@ -240,7 +250,7 @@ void ctx_free(sw_ctx *c)
     c->ev_pool.clear();
     void *ptrs[] = {c->spin, c->label, c->code, c->bondbits, c->cross, c->npar, c->nkey,
                     c->nfinal, c->thr_dev, c->rep_dev, c->tile_rep, c->jbase, c->bond_bytes, c->obs,
-                    c->pmask, c->cid, c->cand, c->ncand, c->cov};
+                    c->pmask, c->cid, c->cand, c->ncand, c->cov, c->psize, c->csize};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -317,6 +327,10 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
         if ((e = cudaMemsetAsync(c->ncand, 0, 2 * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
         if ((e = cudaMemsetAsync(c->cov, 0, ncov * sizeof(uint32_t), c->stream)) != cudaSuccess) return fail(e);
     }
+    if (flags & SW_FLAG_CSIZE) {
+        if ((e = dalloc(&c->psize, nt * c->S)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->csize, nt * c->S)) != cudaSuccess) return fail(e);
+    }
     if ((e = cudaMemcpyAsync(c->thr_dev, &c->thr, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
         return fail(e);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -330,7 +344,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
     R.key0 = k0;
     R.key1 = k1;
     R.nsweeps = 0;
-    R.flags = (pcc ? RF_PCC : 0) | (c->open ? RF_OPEN : 0);
+    R.flags = (pcc ? RF_PCC : 0) | (c->open ? RF_OPEN : 0) | (c->psize ? RF_CSIZE : 0);
     R.sweep0 = 0;
     R.thr = thr;
     R.thr_dev = c->thr_dev;
@@ -350,10 +364,18 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
     R.cand = c->cand;
     R.ncand = c->ncand;
     R.cov = c->cov;
+    R.psize = c->psize;
+    R.csize = c->csize;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
     lk.unlock();
     *out = c;
     return SW_OK;
+}
+
+// Tile-kernel features this lattice needs (FEAT_*).
+int ctx_features(const sw_ctx *c)
+{
+    return (c->psize ? FEAT_CSIZE : 0) | (c->open ? FEAT_OPEN : 0);
 }
 
 int ensure_obs(sw_ctx *c, int64_t n)
@@ -398,7 +420,7 @@ int graph_for(sw_ctx *c, int m, cudaGraphExec_t *out)
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < m && e == cudaSuccess; ++j) {
         a.j = j;
-        e = enqueue_launch_th(c->TH, a, c->pcc, 1, c->cap_stream);
+        e = enqueue_launch_th(c->TH, a, c->pcc, ctx_features(c), 1, c->cap_stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -440,7 +462,7 @@ int enqueue_profiled(sw_ctx *c, int32_t n)
         SW_CUDA(next_event(c, &e2));
         a.j = j;
         SW_CUDA(cudaEventRecord(e0, c->stream));
-        SW_CUDA(enqueue_tile(c->TH, a, c->pcc, c->stream));
+        SW_CUDA(enqueue_tile(c->TH, a, c->pcc, ctx_features(c), c->stream));
         SW_CUDA(cudaEventRecord(e1, c->stream));
         if (j < n) SW_CUDA(enqueue_merge(c->TH, a, c->pcc, 1, c->stream));
         SW_CUDA(cudaEventRecord(e2, c->stream));
@@ -492,7 +514,7 @@ int run_sweeps(sw_ctx *c, int32_t n)
             SweepArgs a = args_of(c);
             for (int j = 0; j < m; ++j) {
                 a.j = j;
-                SW_CUDA(enqueue_launch_th(c->TH, a, c->pcc, 1, c->stream));
+                SW_CUDA(enqueue_launch_th(c->TH, a, c->pcc, ctx_features(c), 1, c->stream));
             }
         }
         done += m;

@@ -17,11 +17,14 @@ constexpr int MERGE_JUMPS = 3;     // pointer-jumping rounds between unions and 
 // the shared-memory attribute set by prepare_th applies to the copy that
 // runs).
 __attribute__((visibility("hidden"))) cudaError_t prepare_th(int TH);
-__attribute__((visibility("hidden"))) cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, cudaStream_t st);
+// feat: FEAT_* bits of the tile-kernel variant to launch (the union of what
+// the launch's lattices need)
+__attribute__((visibility("hidden"))) cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, int feat,
+                                                               cudaStream_t st);
 __attribute__((visibility("hidden"))) cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int n_reps,
                                                                 cudaStream_t st);
-__attribute__((visibility("hidden"))) cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, bool pcc, int n_reps,
-                                                                    cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, bool pcc, int feat,
+                                                                    int n_reps, cudaStream_t st);
 __attribute__((visibility("hidden"))) cudaError_t enqueue_hot_start(uint8_t *spin, int64_t N, uint64_t seed,
                                                                     cudaStream_t st);
 __attribute__((visibility("hidden"))) cudaError_t enqueue_job_init(uint8_t *spin, int64_t N, uint64_t seed, void *obs,

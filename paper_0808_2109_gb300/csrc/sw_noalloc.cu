@@ -147,8 +147,8 @@ extern "C" int sw_sweep_static(const uint8_t *spin_in, uint8_t *spin_out, int32_
     a.n_tiles = tiles_x * tiles_y;
     a.jbase = reinterpret_cast<const int32_t *>(scratch + OFF_JBASE);
     a.j = 0;   // start the sweep (bonds, tile labels, border nodes) ...
-    if (enqueue_launch_th(TH_STATIC, a, false, 1, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (enqueue_launch_th(TH_STATIC, a, false, 0, 1, st) != cudaSuccess) return SW_ERR_CUDA;
     a.j = 1;   // ... and finish it (cluster flip, spins, labels, observables)
-    if (enqueue_tile(TH_STATIC, a, false, st) != cudaSuccess) return SW_ERR_CUDA;
+    if (enqueue_tile(TH_STATIC, a, false, 0, st) != cudaSuccess) return SW_ERR_CUDA;
     return SW_OK;
 }

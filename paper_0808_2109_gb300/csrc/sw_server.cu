@@ -62,6 +62,7 @@ struct Job {
     int32_t *npar = nullptr, *nkey = nullptr, *cid = nullptr, *cand = nullptr, *ncand = nullptr;
     uint64_t *thr_dev = nullptr;
     DevObs *obs = nullptr;
+    int32_t *psize = nullptr, *csize = nullptr;   // SW_FLAG_CSIZE
     // placement
     int lane = -1, slot = -1, tile_base = -1;
     int32_t jstart = 0;
@@ -70,11 +71,11 @@ struct Job {
 // Byte offsets of a job's buffers inside its one device block, each on a
 // 256-byte boundary; PCC scratch last, in one range that starts zeroed.
 struct JobLayout {
-    size_t spin, label, code, bondbits, cross, npar, nkey, nfinal, thr, obs;
+    size_t spin, label, code, bondbits, cross, npar, nkey, nfinal, thr, obs, psize, csize;
     size_t pmask, cid, cand, ncand, cov, pcc_end, total;
 };
 
-JobLayout job_layout(int L, int TH, int nsweeps, bool pcc)
+JobLayout job_layout(int L, int TH, int nsweeps, bool pcc, bool csize)
 {
     const size_t N = (size_t)L * L;
     const size_t tx = (L + TW - 1) / TW, ty = (L + TH - 1) / TH, nt = tx * ty;
@@ -96,6 +97,11 @@ JobLayout job_layout(int L, int TH, int nsweeps, bool pcc)
     o.nfinal = take(nt * S * 4);
     o.thr = take(8);
     o.obs = take((size_t)nsweeps * sizeof(DevObs));
+    o.psize = o.csize = at;
+    if (csize) {
+        o.psize = take(nt * S * 4);
+        o.csize = take(nt * S * 4);
+    }
     o.pmask = o.cid = o.cand = o.ncand = o.cov = o.pcc_end = at;
     if (pcc) {
         o.pmask = take(nt * S * 8 * 4);
@@ -109,7 +115,10 @@ JobLayout job_layout(int L, int TH, int nsweeps, bool pcc)
     return o;
 }
 
-size_t job_bytes(int L, int TH, int nsweeps, bool pcc) { return job_layout(L, TH, nsweeps, pcc).total; }
+size_t job_bytes(int L, int TH, int nsweeps, bool pcc, bool csize)
+{
+    return job_layout(L, TH, nsweeps, pcc, csize).total;
+}
 
 struct Lane {
     int TH = 128;
@@ -125,6 +134,7 @@ struct Lane {
     int tail = 0;                  // every tile from here on is free
     cudaGraphExec_t graph = nullptr;
     bool graph_pcc = false;
+    int graph_feat = 0;         // FEAT_* of the captured tile kernel
     bool dirty = true;       // tables changed since the last upload
     bool recapture = true;   // capacity or mode changed since the last capture
     int active = 0;
@@ -166,7 +176,8 @@ void free_job_device(Job *j, cudaStream_t st)
 cudaError_t job_alloc(Job *j, cudaStream_t st)
 {
     const size_t N = (size_t)j->spec.L * j->spec.L;
-    const JobLayout o = job_layout(j->spec.L, j->TH, j->spec.nsweeps, j->pcc);
+    const bool csz = (j->spec.flags & SW_FLAG_CSIZE) != 0;
+    const JobLayout o = job_layout(j->spec.L, j->TH, j->spec.nsweeps, j->pcc, csz);
     cudaError_t e = cudaMallocAsync(&j->block, o.total, st);
     if (e != cudaSuccess) {
         j->block = nullptr;
@@ -183,6 +194,10 @@ cudaError_t job_alloc(Job *j, cudaStream_t st)
     j->nfinal = reinterpret_cast<uint32_t *>(b + o.nfinal);
     j->thr_dev = reinterpret_cast<uint64_t *>(b + o.thr);
     j->obs = reinterpret_cast<DevObs *>(b + o.obs);
+    if (csz) {
+        j->psize = reinterpret_cast<int32_t *>(b + o.psize);
+        j->csize = reinterpret_cast<int32_t *>(b + o.csize);
+    }
     if (j->pcc) {
         j->pmask = reinterpret_cast<uint32_t *>(b + o.pmask);
         j->cid = reinterpret_cast<int32_t *>(b + o.cid);
@@ -205,7 +220,8 @@ Replica replica_of(const Job *j)
     R.key0 = (uint32_t)j->spec.seed;
     R.key1 = (uint32_t)(j->spec.seed >> 32);
     R.nsweeps = j->spec.nsweeps;
-    R.flags = (j->pcc ? RF_PCC : 0) | ((j->spec.flags & SW_FLAG_OPEN) ? RF_OPEN : 0);
+    R.flags = (j->pcc ? RF_PCC : 0) | ((j->spec.flags & SW_FLAG_OPEN) ? RF_OPEN : 0) |
+              ((j->spec.flags & SW_FLAG_CSIZE) ? RF_CSIZE : 0);
     R.sweep0 = 0;
     R.thr = j->thr;
     R.thr_dev = j->thr_dev;
@@ -225,6 +241,8 @@ Replica replica_of(const Job *j)
     R.cand = j->cand;
     R.ncand = j->ncand;
     R.cov = j->cov;
+    R.psize = j->psize;
+    R.csize = j->csize;
     return R;
 }
 
@@ -315,7 +333,7 @@ SweepArgs lane_args(Lane &ln)
     return a;
 }
 
-cudaError_t lane_capture(Lane &ln, cudaStream_t cap_stream, bool pcc)
+cudaError_t lane_capture(Lane &ln, cudaStream_t cap_stream, bool pcc, int feat)
 {
     if (ln.graph) {
         cudaGraphExecDestroy(ln.graph);
@@ -328,7 +346,7 @@ cudaError_t lane_capture(Lane &ln, cudaStream_t cap_stream, bool pcc)
     SweepArgs a = lane_args(ln);
     for (int j = 0; j < GROUPS_PER_STEP && e == cudaSuccess; ++j) {
         a.j = j;
-        e = enqueue_launch_th(ln.TH, a, pcc, ln.cap_reps, cap_stream);
+        e = enqueue_launch_th(ln.TH, a, pcc, feat, ln.cap_reps, cap_stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -338,6 +356,7 @@ cudaError_t lane_capture(Lane &ln, cudaStream_t cap_stream, bool pcc)
     e = cudaGraphInstantiate(&ln.graph, g, 0);
     cudaGraphDestroy(g);
     ln.graph_pcc = pcc;
+    ln.graph_feat = feat;
     ln.recapture = false;
     return e;
 }
@@ -508,9 +527,13 @@ void worker_main(sw_server *s)
             if (ln.active == 0) continue;
             any = true;
             bool pcc = false;
-            for (Job *j : ln.slot_job)
-                if (j && j->pcc) pcc = true;
-            if (pcc != ln.graph_pcc) ln.recapture = true;
+            int feat = 0;
+            for (Job *j : ln.slot_job) {
+                if (!j) continue;
+                pcc = pcc || j->pcc;
+                feat |= (j->psize ? FEAT_CSIZE : 0) | ((j->spec.flags & SW_FLAG_OPEN) ? FEAT_OPEN : 0);
+            }
+            if (pcc != ln.graph_pcc || feat != ln.graph_feat) ln.recapture = true;
             if (ln.dirty) {
                 cudaMemcpyAsync(ln.tile_rep_dev, ln.tile_rep_host.data(), (size_t)ln.cap_tiles * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, ln.stream);
@@ -519,7 +542,7 @@ void worker_main(sw_server *s)
                 ln.dirty = false;
             }
             if (ln.recapture || !ln.graph) {
-                if (lane_capture(ln, cap_stream, pcc) != cudaSuccess) {
+                if (lane_capture(ln, cap_stream, pcc, feat) != cudaSuccess) {
                     std::lock_guard<std::mutex> lk(s->mu);
                     s->worker_error = SW_ERR_CUDA;
                 }
@@ -637,7 +660,7 @@ int sw_batch_submit(sw_server *s, const sw_job *jobs, int32_t n, uint64_t *ids_o
         }
         made.push_back(j);
         j->spec = q;
-        if (q.L < 2 || q.L > SERVER_MAX_L || q.nsweeps < 1 || (q.flags & ~SW_FLAG_OPEN) != 0 ||
+        if (q.L < 2 || q.L > SERVER_MAX_L || q.nsweeps < 1 || (q.flags & ~(SW_FLAG_OPEN | SW_FLAG_CSIZE)) != 0 ||
             (q.tile_h != 0 && q.tile_h != 32 && q.tile_h != 64 && q.tile_h != 96 && q.tile_h != 128)) {
             rc = SW_ERR_ARG;
             break;
@@ -664,7 +687,7 @@ int sw_batch_submit(sw_server *s, const sw_job *jobs, int32_t n, uint64_t *ids_o
         j->tiles_y = (q.L + j->TH - 1) / j->TH;
         j->n_tiles = j->tiles_x * j->tiles_y;
         j->S = slots_of(j->TH);
-        j->bytes = job_bytes(q.L, j->TH, q.nsweeps, j->pcc);
+        j->bytes = job_bytes(q.L, j->TH, q.nsweeps, j->pcc, (q.flags & SW_FLAG_CSIZE) != 0);
         if (j->bytes > s->budget) rc = SW_ERR_NOMEM;
     }
     if (rc != SW_OK) {

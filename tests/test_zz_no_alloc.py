@@ -35,7 +35,7 @@ def test_static_sweep_equals_sw_sweep_twice(env, L, T, seed):
         s_in = torch.from_numpy(spins0).to(dev)
         s_out = torch.empty_like(s_in)
         labels = torch.empty(L * L, dtype=torch.int32, device=dev)
-        obs = torch.full((48,), 0xAB, dtype=torch.uint8, device=dev)   # zeroed by the call
+        obs = torch.full((sw.OBS_DTYPE.itemsize,), 0xAB, dtype=torch.uint8, device=dev)   # zeroed by the call
         stream = torch.cuda.current_stream()
         for k in range(2):
             src = s_in if k == 0 else s_out   # second call in place
