@@ -82,3 +82,27 @@ def test_csize2_mean_is_exact_m2_4x4(orc, T, open_bc):
 def test_csize2_off_by_default(orc):
     ch = orc.sw_chain(16, 1.0, 2.3, seed=1)
     assert (ch.run(3)["csize2"] == 0).all()
+
+
+@pytest.mark.parametrize("T", [2.0, 2.269185, 3.0])
+def test_bond_count_energy_estimator_4x4(orc, T):
+    """<sum sigma sigma> = 2 <nbonds> / P - n_links: each link bonds with
+    probability P exactly when its spins agree, so the bond count is an
+    energy estimator too (exact value from enumeration)."""
+    L = 4
+    N = L * L
+    states = np.arange(1 << N, dtype=np.int64)
+    sig = 2 * ((states[:, None] >> np.arange(N)) & 1) - 1
+    i = np.arange(N)
+    x, y = i % L, i // L
+    a = np.concatenate([i, i])
+    b = np.concatenate([y * L + (x + 1) % L, ((y + 1) % L) * L + x])
+    bs = (sig[:, a] * sig[:, b]).sum(axis=1)
+    w = np.exp((bs - bs.max()) / T)
+    exact = float((w * bs).sum() / w.sum())
+    P = orc.threshold_T(1.0, T) / 2.0 ** 32
+    ch = orc.sw_chain(L, 1.0, T, seed=11)
+    ch.run(1000)
+    obs = ch.run(400_000)
+    est, se = _binned(2.0 * obs["nbonds"] / P - 2 * N, 1000)
+    assert abs(est - exact) < 4 * se, (est, exact, se)
