@@ -110,13 +110,15 @@ def lib():
             L.swo_spans.restype = ctypes.c_int
             L.swo_spans_open.argtypes = [i32, P, P, P]
             L.swo_spans_open.restype = ctypes.c_int
+            L.swo_windings.argtypes = [i32, P, P, P]
+            L.swo_windings.restype = ctypes.c_int
             L.swo_csize2.argtypes = [i32, P]
             L.swo_csize2.restype = i64
             L.swo_pcc_delta.argtypes = [u64]
             L.swo_pcc_delta.restype = u64
             L.swo_pcc_update.argtypes = [u64, u64, i32]
             L.swo_pcc_update.restype = u64
-            L.swo_run.argtypes = [i32, u64, u64, i32, i32, i32, i32, P, P, P, P, P]
+            L.swo_run.argtypes = [i32, u64, u64, i32, i32, i32, i32, i32, P, P, P, P, P]
             L.swo_run.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -206,6 +208,15 @@ def csize2(L: int, lab: np.ndarray) -> int:
     return v
 
 
+def windings(L: int, bond: np.ndarray):
+    bond = np.ascontiguousarray(bond, dtype=np.uint8)
+    wx = np.zeros(1, dtype=np.int32)
+    wy = np.zeros(1, dtype=np.int32)
+    if lib().swo_windings(L, _ptr(bond), _ptr(wx), _ptr(wy)) != 0:
+        raise MemoryError("swo_windings")
+    return int(wx[0]), int(wy[0])
+
+
 def spans_open(L: int, lab: np.ndarray):
     lab = np.ascontiguousarray(lab, dtype=np.int32)
     sx = np.zeros(1, dtype=np.int32)
@@ -225,15 +236,16 @@ def pcc_update(thr: int, sweep: int, flag: bool) -> int:
 
 class Chain:
     """A lattice state advanced by the oracle: (spins, seed, sweep, threshold);
-    open=True gives open boundaries, csize=True fills obs["csize2"]."""
+    open=True gives open boundaries, csize=True fills obs["csize2"], wind=True
+    reports (and, for PCC, feeds back on) the topological rule in spans_x/y."""
 
     def __init__(self, L: int, seed: int, thr: int, pcc: bool = False,
                  spin: np.ndarray | None = None, sweep: int = 0, open: bool = False,
-                 csize: bool = False):
+                 csize: bool = False, wind: bool = False):
         if L < 2:
             raise ValueError("L must be >= 2")
         self.L, self.seed, self.pcc, self.open = int(L), int(seed), bool(pcc), bool(open)
-        self.csize = bool(csize)
+        self.csize, self.wind = bool(csize), bool(wind)
         self.thr = np.array([thr], dtype=np.uint64)
         self.sweep = int(sweep)
         self.spin = hot_start(L, seed) if spin is None else np.array(spin, dtype=np.uint8).ravel()
@@ -249,7 +261,8 @@ class Chain:
         if nsweeps <= 0:
             return obs
         rc = lib().swo_run(self.L, self.seed, self.sweep, nsweeps, 1 if self.pcc else 0,
-                           1 if self.open else 0, 1 if self.csize else 0, _ptr(self.thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond),
+                           1 if self.open else 0, 1 if self.csize else 0, 1 if self.wind else 0,
+                           _ptr(self.thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond),
                            _ptr(obs))
         if rc != 0:
             raise MemoryError("swo_run")
@@ -257,16 +270,18 @@ class Chain:
         return obs
 
 
-def sw_chain(L: int, J: float, T: float, seed: int, open: bool = False, csize: bool = False) -> Chain:
-    return Chain(L, seed, threshold_T(J, T), open=open, csize=csize)
+def sw_chain(L: int, J: float, T: float, seed: int, open: bool = False, csize: bool = False,
+             wind: bool = False) -> Chain:
+    return Chain(L, seed, threshold_T(J, T), open=open, csize=csize, wind=wind)
 
 
-def sw_chain_p(L: int, p: float, seed: int, open: bool = False, csize: bool = False) -> Chain:
-    return Chain(L, seed, threshold_p(p), open=open, csize=csize)
+def sw_chain_p(L: int, p: float, seed: int, open: bool = False, csize: bool = False,
+               wind: bool = False) -> Chain:
+    return Chain(L, seed, threshold_p(p), open=open, csize=csize, wind=wind)
 
 
-def pcc_chain(L: int, seed: int, open: bool = False, csize: bool = False) -> Chain:
-    return Chain(L, seed, 1 << 31, pcc=True, open=open, csize=csize)
+def pcc_chain(L: int, seed: int, open: bool = False, csize: bool = False, wind: bool = False) -> Chain:
+    return Chain(L, seed, 1 << 31, pcc=True, open=open, csize=csize, wind=wind)
 
 
 def energy_per_site(obs: np.ndarray, L: int, J: float = 1.0) -> np.ndarray:

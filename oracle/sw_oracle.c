@@ -352,6 +352,77 @@ int swo_spans(int32_t L, const int32_t *label, int32_t *spans_x, int32_t *spans_
 }
 
 /* ------------------------------------------------------------------------
+ * Topological rule (Sec. III): a cluster percolates in x if it winds around
+ * the box in x, i.e. holds a closed path of bonds whose net displacement in
+ * x is a non-zero multiple of L (likewise y).  Each cluster is explored
+ * breadth first, giving every site an unwrapped position (its start at 0,
+ * each bond moving by one lattice step); a bond that reaches an explored
+ * site at a position other than the one it predicts closes a cycle whose
+ * displacement is that difference.  Every cycle is a sum of such cycles, so
+ * a winding cluster always shows one.
+ * ---------------------------------------------------------------------- */
+int swo_windings(int32_t L, const uint8_t *bond, int32_t *wraps_x, int32_t *wraps_y)
+{
+    int64_t N = (int64_t)L * (int64_t)L;
+    int64_t *ux = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *uy = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    uint8_t *seen = (uint8_t *)calloc((size_t)N, 1);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    if (!ux || !uy || !seen || !queue) {
+        free(ux);
+        free(uy);
+        free(seen);
+        free(queue);
+        return -1;
+    }
+    *wraps_x = 0;
+    *wraps_y = 0;
+    for (int64_t s = 0; s < N; s++) {
+        if (seen[s])
+            continue;
+        int64_t head = 0, tail = 0;
+        seen[s] = 1;
+        ux[s] = 0;
+        uy[s] = 0;
+        queue[tail++] = s;
+        while (head < tail) {
+            int64_t i = queue[head++];
+            int64_t x = i % L, y = i / L;
+            /* the four links at site i: its own right and down links, and the
+             * right link of its left neighbour and the down link of the site
+             * above (each a bond or not) */
+            int64_t nb[4], dx[4], dy[4];
+            int has[4];
+            nb[0] = y * L + (x + 1) % L;       dx[0] = 1;  dy[0] = 0;  has[0] = bond[i] & 1;
+            nb[1] = ((y + 1) % L) * L + x;     dx[1] = 0;  dy[1] = 1;  has[1] = (bond[i] >> 1) & 1;
+            nb[2] = y * L + (x + L - 1) % L;   dx[2] = -1; dy[2] = 0;  has[2] = bond[nb[2]] & 1;
+            nb[3] = ((y + L - 1) % L) * L + x; dx[3] = 0;  dy[3] = -1; has[3] = (bond[nb[3]] >> 1) & 1;
+            for (int q = 0; q < 4; q++) {
+                if (!has[q])
+                    continue;
+                int64_t j = nb[q], px = ux[i] + dx[q], py = uy[i] + dy[q];
+                if (!seen[j]) {
+                    seen[j] = 1;
+                    ux[j] = px;
+                    uy[j] = py;
+                    queue[tail++] = j;
+                } else {
+                    if (ux[j] != px)
+                        *wraps_x = 1;
+                    if (uy[j] != py)
+                        *wraps_y = 1;
+                }
+            }
+        }
+    }
+    free(ux);
+    free(uy);
+    free(seen);
+    free(queue);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
  * Percolation under open boundaries (Sec. III): a cluster spans x iff it
  * holds a site of the leftmost column and a site of the rightmost column
  * (spans y: topmost and bottommost rows).
@@ -407,7 +478,7 @@ uint64_t swo_pcc_update(uint64_t thr, uint64_t sweep, int32_t flag)
  * Whole sweeps, step by step in the paper's order (Sec. I steps 1-4).
  * ---------------------------------------------------------------------- */
 int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc, int32_t open,
-            int32_t csize, uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
+            int32_t csize, int32_t wind, uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
 {
     int64_t N = (int64_t)L * (int64_t)L;
     uint8_t *b = bond ? bond : (uint8_t *)malloc((size_t)N);
@@ -431,14 +502,16 @@ int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t 
         }
         swo_assign(L, seed, k, label, spin);             /* step 3 */
         swo_measure(L, spin, open, &o.bond_sum, &o.mag);
-        if (pcc) {
-            int src = open ? swo_spans_open(L, label, &o.spans_x, &o.spans_y)
-                           : swo_spans(L, label, &o.spans_x, &o.spans_y);
+        if (pcc || wind) {
+            int src = wind   ? swo_windings(L, b, &o.spans_x, &o.spans_y)
+                      : open ? swo_spans_open(L, label, &o.spans_x, &o.spans_y)
+                             : swo_spans(L, label, &o.spans_x, &o.spans_y);
             if (src != 0) {
                 rc = -1;
                 break;
             }
-            *thr = swo_pcc_update(t, k, o.spans_x || o.spans_y);
+            if (pcc)
+                *thr = swo_pcc_update(t, k, o.spans_x || o.spans_y);
         }
         obs[n] = o;
     }

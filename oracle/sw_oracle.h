@@ -93,6 +93,12 @@ int swo_spans(int32_t L, const int32_t *label, int32_t *spans_x, int32_t *spans_
  * some cluster touches both the topmost and the bottommost row. */
 int swo_spans_open(int32_t L, const int32_t *label, int32_t *spans_x, int32_t *spans_y);
 
+/* Topological rule (paper, Sec. III): wraps_x is 1 iff some cluster of the
+ * bond set winds around the box in x (holds a closed path of bonds whose net
+ * x displacement is a non-zero multiple of L); wraps_y likewise.  Returns 0,
+ * or -1 when memory is short. */
+int swo_windings(int32_t L, const uint8_t *bond, int32_t *wraps_x, int32_t *wraps_y);
+
 /* PCC feedback step size after sweep k, in threshold units. */
 uint64_t swo_pcc_delta(uint64_t sweep);
 /* PCC feedback: t -= delta if flag else t += delta, clamped to [0, 2^32]. */
@@ -101,11 +107,13 @@ uint64_t swo_pcc_update(uint64_t thr, uint64_t sweep, int32_t flag);
 /* nsweeps full sweeps k = sweep0 .. sweep0+nsweeps-1 on spin[] in place.
  * *thr is the threshold of the first sweep; with pcc != 0 it is updated by
  * the feedback after every sweep (spans by swo_spans, or swo_spans_open when
- * open != 0).  csize != 0 fills obs[].csize2 (else it stays 0).  label[] receives the labels of the last
+ * open != 0).  csize != 0 fills obs[].csize2 (else it stays 0).  wind != 0
+ * switches the span test to the topological rule (swo_windings) and reports
+ * it every sweep, PCC or not.  label[] receives the labels of the last
  * sweep, bond[] (optional, may be NULL) its bonds, obs[nsweeps] the
  * per-sweep observables.  Returns 0, or -1 when memory is short. */
 int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc, int32_t open,
-            int32_t csize, uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
+            int32_t csize, int32_t wind, uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
 
 #ifdef __cplusplus
 }
