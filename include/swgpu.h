@@ -69,6 +69,12 @@ extern "C" {
  * fair sign, so the mean of csize2 is <M^2>: the cluster ("improved")
  * estimator of the susceptibility, with a smaller variance than M^2. */
 #define SW_FLAG_CSIZE (1u << 13)
+/* Topological rule (Sec. III): spans_x / spans_y report, every sweep,
+ * whether some cluster winds around the box in x / y (holds a closed path of
+ * bonds whose net displacement is a non-zero multiple of L), and a PCC
+ * lattice feeds back on that instead of the extension rule.  One more 8-byte
+ * word per border node of device memory. */
+#define SW_FLAG_WIND (1u << 14)
 
 typedef struct sw_ctx sw_ctx; /* opaque; owned by the library */
 
@@ -221,8 +227,8 @@ typedef struct {
     sw_obs *obs_out;    /* optional: nsweeps entries, written before completion */
     uint8_t *spins_out; /* optional: L*L final spins                            */
     int32_t *labels_out;/* optional: L*L labels of the last sweep               */
-    uint32_t flags;     /* SW_FLAG_OPEN, SW_FLAG_CSIZE or 0 (tile heights go in
-                           tile_h)                                              */
+    uint32_t flags;     /* SW_FLAG_OPEN | SW_FLAG_CSIZE | SW_FLAG_WIND, or 0
+                           (tile heights go in tile_h)                          */
 } sw_job;
 /* The caller owns obs_out/spins_out/labels_out; they must stay valid until
  * sw_batch_poll reports the job finished. */

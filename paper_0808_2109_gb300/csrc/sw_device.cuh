@@ -52,6 +52,7 @@ constexpr uint32_t STREAM_INIT = 0u, STREAM_BOND = 1u, STREAM_SPIN = 2u;
 constexpr int32_t RF_PCC = 1;
 constexpr int32_t RF_OPEN = 2;   // open boundaries: the links leaving the lattice do not exist
 constexpr int32_t RF_CSIZE = 4;  // also sum |C|^2 over the clusters (psize, csize below)
+constexpr int32_t RF_WIND = 8;   // topological rule: spans = a cluster winds around the box (nlink)
 
 // Per-sweep observables as the device accumulates them (layout of sw_obs).
 struct DevObs {
@@ -93,7 +94,11 @@ struct Replica {
     uint32_t *cov;
     // cluster sizes (RF_CSIZE): sites of each border piece at its
     // representative node, and of each cluster at its root node
-    int32_t *psize, *csize;          // [L][tiles_x][4] column coverage, then [L][tiles_y][4] row coverage
+    int32_t *psize, *csize;
+    // topological rule (RF_WIND): per node, parent (low 32 bits) and the
+    // node's unwrapped displacement from its parent (high 32 bits, see
+    // wind_off) -- one 64-bit word, so both change together
+    unsigned long long *nlink;          // [L][tiles_x][4] column coverage, then [L][tiles_y][4] row coverage
 };
 
 // A launch: every tile of every lattice in the tile table (entries of -1
@@ -497,6 +502,7 @@ constexpr size_t tile_smem(bool pcc)
 // lattice that needs them, so the plain kernel carries none of their code.
 constexpr int FEAT_CSIZE = 1;   // cluster sizes (RF_CSIZE)
 constexpr int FEAT_OPEN = 2;    // open boundaries (RF_OPEN)
+constexpr int FEAT_WIND = 4;    // topological rule (RF_WIND; merge kernels only)
 
 template <int TH, int F>
 __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(const SweepArgs a)
@@ -958,6 +964,100 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     block_sum_atomic<NT, 4>(v4, dst, sm.red);
 }
 
+// ------------------------------------------------ union-find with offsets
+// Topological rule (Sec. III): a cluster winds around the box when one of
+// its cycles has a non-zero net displacement.  Nodes carry their unwrapped
+// displacement from their parent; each component is held as a residue mod
+// WIND_M, a prime above any lattice side.  A cycle's net displacement is
+// (n_x L, n_y L) with |n| <= L, which is zero mod WIND_M only for n = 0.
+constexpr uint32_t WIND_M = 65521u;
+
+__device__ __forceinline__ uint32_t wind_off(int dx, int dy)
+{
+    int x = dx % (int)WIND_M, y = dy % (int)WIND_M;
+    x += x < 0 ? (int)WIND_M : 0;
+    y += y < 0 ? (int)WIND_M : 0;
+    return (uint32_t)x | ((uint32_t)y << 16);
+}
+
+__device__ __forceinline__ uint32_t wind_add(uint32_t a, uint32_t b)
+{
+    uint32_t x = (a & 0xFFFFu) + (b & 0xFFFFu), y = (a >> 16) + (b >> 16);
+    x -= x >= WIND_M ? WIND_M : 0u;
+    y -= y >= WIND_M ? WIND_M : 0u;
+    return x | (y << 16);
+}
+
+__device__ __forceinline__ uint32_t wind_neg(uint32_t a)
+{
+    const uint32_t x = a & 0xFFFFu, y = a >> 16;
+    return (x ? WIND_M - x : 0u) | ((y ? WIND_M - y : 0u) << 16);
+}
+
+__device__ __forceinline__ unsigned long long wind_link(int parent, uint32_t off)
+{
+    return (unsigned long long)(uint32_t)parent | ((unsigned long long)off << 32);
+}
+
+__device__ __forceinline__ unsigned long long wload(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+
+// Root of x and x's displacement from it, halving the path on the way (a
+// node's link only ever moves to an ancestor, with the summed displacement).
+__device__ __forceinline__ int wfind(unsigned long long *lk, int x, uint32_t &off)
+{
+    off = 0u;
+    unsigned long long v = wload(lk + x);
+    int p = (int)(uint32_t)v;
+    while (p != x) {
+        const unsigned long long w = wload(lk + p);
+        const int gp = (int)(uint32_t)w;
+        if (gp != p) {
+            const uint32_t o = wind_add((uint32_t)(v >> 32), (uint32_t)(w >> 32));
+            *(volatile unsigned long long *)(lk + x) = wind_link(gp, o);
+            off = wind_add(off, o);
+            x = gp;
+        } else {
+            off = wind_add(off, (uint32_t)(v >> 32));
+            x = p;
+        }
+        v = wload(lk + x);
+        p = (int)(uint32_t)v;
+    }
+    return x;
+}
+
+// Union by key (as gunite_by_key) of the nodes a and b joined by a bond that
+// moves by d from a to b.  If they already share a root, the bond closes a
+// cycle: a non-zero displacement around it is a winding, recorded in the
+// sweep's spans_x / spans_y.
+__device__ __forceinline__ void wunite(unsigned long long *lk, const int32_t *key, int a, int b, uint32_t d,
+                                       DevObs *o)
+{
+    for (;;) {
+        uint32_t oa, ob;
+        const int ra = wfind(lk, a, oa);
+        const int rb = wfind(lk, b, ob);
+        const uint32_t rel = wind_add(wind_add(oa, d), wind_neg(ob));   // U(rb) - U(ra)
+        if (ra == rb) {
+            if (rel & 0xFFFFu) atomicOr(&o->spans_x, 1);
+            if (rel >> 16) atomicOr(&o->spans_y, 1);
+            return;
+        }
+        int lo = ra, hi = rb;
+        uint32_t off = rel;
+        if ((uint32_t)key[ra] > (uint32_t)key[rb]) {
+            lo = rb;
+            hi = ra;
+            off = wind_neg(rel);
+        }
+        const unsigned long long root = (unsigned long long)(uint32_t)hi;   // self link, offset 0
+        if (atomicCAS(lk + hi, root, wind_link(lo, off)) == root) return;
+    }
+}
+
 // ------------------------------------------------------------- merge phase
 // Launch shape of the merge kernels: one block per tile (blockIdx.x = the
 // tile's index in the tile table) of S/4 threads; thread i takes the slots
@@ -988,7 +1088,9 @@ __device__ __forceinline__ const Replica *merge_lattice(const SweepArgs &a, int 
 // activated on the "new lattice" of border sites.  Link e < TH joins row e
 // of the tile's right column to the left column of the tile to its right;
 // link TH + x joins column x of its bottom row to the top row below it.
-template <int TH>
+// W: compiled with the topological rule (lattices with RF_WIND unite their
+// nodes with displacements in nlink); every kernel of the merge has it.
+template <int TH, bool W>
 __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_union(const SweepArgs a)
 {
     using SL = Slots<TH>;
@@ -1018,16 +1120,49 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_union(const SweepArg
             }
         }
     }
+    const bool wind = W && (R.flags & RF_WIND);
 #pragma unroll
-    for (int q = 0; q < MC::EPT; ++q)
-        if (na[q] >= 0) gunite_by_key(R.npar, R.nkey, na[q], nb[q]);
+    for (int q = 0; q < MC::EPT; ++q) {
+        if (na[q] < 0) continue;
+        if (wind) {   // a right link moves by (+1, 0), a down link by (0, +1)
+            const bool right = threadIdx.x + q * MC::MT < TH;
+            wunite(R.nlink, R.nkey, na[q], nb[q], right ? wind_off(1, 0) : wind_off(0, 1), R.obs + j);
+        } else {
+            gunite_by_key(R.npar, R.nkey, na[q], nb[q]);
+        }
+    }
+}
+
+// Topological rule: every node's link before the unions -- its parent from
+// the tile kernel (a piece's representative, or itself) and its displacement
+// from it, both inside one tile.
+template <int TH>
+__global__ void __launch_bounds__(MergeCfg<TH>::MT) k_wind_init(const SweepArgs a)
+{
+    using MC = MergeCfg<TH>;
+    int j;
+    const Replica *Rp = merge_lattice(a, blockIdx.x, j);
+    if (!Rp || !(Rp->flags & RF_WIND)) return;
+    const Replica &R = *Rp;
+    const Tile t = tile_of(R, blockIdx.x, TH);
+    const int base = (blockIdx.x - R.tile_base) * MC::S;
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) {
+        const int s = threadIdx.x + q * MC::MT, n = base + s;
+        const int p = R.npar[n];
+        uint32_t off = 0u;
+        int site, rsite;
+        if (p != n && slot_site<TH>(s, t.tw, t.th, site) && slot_site<TH>(p - base, t.tw, t.th, rsite))
+            off = wind_off(site % TW - rsite % TW, site / TW - rsite / TW);
+        R.nlink[n] = wind_link(p, off);
+    }
 }
 
 // One round of pointer jumping over the representatives (every parent
 // replaced by its grandparent): a few rounds between the unions and the
 // compression cut the depth of the chains that unions across many tiles
 // leave behind.  Other slots only alias their piece's representative.
-template <int TH>
+template <int TH, bool W>
 __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs a)
 {
     using MC = MergeCfg<TH>;
@@ -1036,6 +1171,21 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs
     if (!Rp) return;
     const Replica &R = *Rp;
     const int base = (blockIdx.x - R.tile_base) * MC::S;   // the lattice's own nodes
+    if (W && (R.flags & RF_WIND)) {
+        unsigned long long v[MC::NPT], w[MC::NPT];
+#pragma unroll
+        for (int q = 0; q < MC::NPT; ++q)
+            v[q] = ((uint32_t)R.nkey[base + threadIdx.x + q * MC::MT] & KEY_REP)
+                       ? wload(R.nlink + base + threadIdx.x + q * MC::MT) : ~0ull;
+#pragma unroll
+        for (int q = 0; q < MC::NPT; ++q) w[q] = v[q] != ~0ull ? wload(R.nlink + (uint32_t)v[q]) : ~0ull;
+#pragma unroll
+        for (int q = 0; q < MC::NPT; ++q)
+            if (v[q] != ~0ull && (uint32_t)w[q] != (uint32_t)v[q])
+                *(volatile unsigned long long *)(R.nlink + base + threadIdx.x + q * MC::MT) =
+                    wind_link((int)(uint32_t)w[q], wind_add((uint32_t)(v[q] >> 32), (uint32_t)(w[q] >> 32)));
+        return;
+    }
     uint32_t key[MC::NPT];
     int p[MC::NPT], gp[MC::NPT];
 #pragma unroll
@@ -1056,7 +1206,7 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs
 // bit (root mod 128) of Philox(root/128, k, SPIN) (Sec. I step 3).  Any
 // other slot stores FINAL_ALIAS | its representative.  Counts the clusters
 // that touch a tile border (one root node each).
-template <int TH>
+template <int TH, bool W>
 __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepArgs a)
 {
     using MC = MergeCfg<TH>;
@@ -1065,6 +1215,8 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
     if (!Rp) return;
     const Replica &R = *Rp;
     const int base = (blockIdx.x - R.tile_base) * MC::S;
+    const bool wind = W && (R.flags & RF_WIND);   // the forest lives in nlink
+    auto parent = [&](int x) { return wind ? (int)(uint32_t)wload(R.nlink + x) : gload(R.npar + x); };
     uint32_t key[MC::NPT];
     int r[MC::NPT], p[MC::NPT];
 #pragma unroll
@@ -1072,7 +1224,9 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
 #pragma unroll
     for (int q = 0; q < MC::NPT; ++q) {
         r[q] = base + threadIdx.x + q * MC::MT;
-        p[q] = gload(R.npar + r[q]);
+        // a representative walks its forest; any other slot keeps its parent
+        // from the tile kernel (its representative) for the alias below
+        p[q] = (wind && (key[q] & KEY_REP)) ? parent(r[q]) : gload(R.npar + r[q]);
     }
     // the walks of the thread's representatives advance in lock step
     for (;;) {
@@ -1087,7 +1241,7 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
         if (!more) break;
 #pragma unroll
         for (int q = 0; q < MC::NPT; ++q)
-            if (key[q] & KEY_REP) p[q] = gload(R.npar + r[q]);
+            if (key[q] & KEY_REP) p[q] = parent(r[q]);
     }
     uint32_t rkey[MC::NPT];
 #pragma unroll
@@ -1098,10 +1252,27 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
     for (int q = 0; q < MC::NPT; ++q) {
         const int n = base + threadIdx.x + q * MC::MT;
         if (key[q] & KEY_REP) {
-            for (int x = n; x != r[q];) {
-                const int nx = gload(R.npar + x);
-                *(volatile int32_t *)(R.npar + x) = r[q];
-                x = nx;
+            if (wind) {
+                // displacement from the root along the walk, then every link
+                // of the walk rewritten to the root with its own displacement
+                uint32_t tot = 0u;
+                for (int x = n; x != r[q];) {
+                    const unsigned long long v = wload(R.nlink + x);
+                    tot = wind_add(tot, (uint32_t)(v >> 32));
+                    x = (int)(uint32_t)v;
+                }
+                for (int x = n; x != r[q];) {
+                    const unsigned long long v = wload(R.nlink + x);
+                    *(volatile unsigned long long *)(R.nlink + x) = wind_link(r[q], tot);
+                    tot = wind_add(tot, wind_neg((uint32_t)(v >> 32)));
+                    x = (int)(uint32_t)v;
+                }
+            } else {
+                for (int x = n; x != r[q];) {
+                    const int nx = gload(R.npar + x);
+                    *(volatile int32_t *)(R.npar + x) = r[q];
+                    x = nx;
+                }
             }
             nroots += r[q] == n;
             if (R.flags & RF_CSIZE) atomicAdd(R.csize + r[q], R.psize[n]);
@@ -1147,7 +1318,7 @@ __global__ void k_pcc_candidates(const SweepArgs a)
     if (ri < 0) return;
     const Replica &R = a.reps[ri];
     const int j = lattice_launch(a, R);
-    if (!(R.flags & RF_PCC) || j < 0 || j >= R.nsweeps) return;
+    if (!(R.flags & RF_PCC) || (R.flags & RF_WIND) || j < 0 || j >= R.nsweeps) return;
     const Tile t = tile_of(R, g, TH);
     int axis, node;
     if (e < TH) {
@@ -1183,7 +1354,7 @@ __global__ void k_pcc_cover(const SweepArgs a)
     if (ri < 0) return;
     const Replica &R = a.reps[ri];
     const int j = lattice_launch(a, R);
-    if (!(R.flags & RF_PCC) || j < 0 || j >= R.nsweeps) return;
+    if (!(R.flags & RF_PCC) || (R.flags & RF_WIND) || j < 0 || j >= R.nsweeps) return;
     const int64_t nl = n - (int64_t)R.tile_base * S;   // the lattice's own node
     const uint4 *pm4 = reinterpret_cast<const uint4 *>(R.pmask + (size_t)nl * 8);
     const uint4 c4 = pm4[0], r4 = pm4[1];
@@ -1212,7 +1383,8 @@ __global__ void k_pcc_cover(const SweepArgs a)
 // Record the flags, apply the PCC feedback to the threshold for the next
 // sweep -- down by delta_k if the clusters percolate, up otherwise, delta_k =
 // 2^(32 - min(8 + floor(k/1000), 20)), clamped to [0, 2^32] -- and clear the
-// scratch.
+// scratch.  Under the topological rule (RF_WIND) the flags are the windings
+// the unions recorded.
 template <int TH>
 __global__ void k_pcc_decide(const SweepArgs a, int n_reps)
 {
@@ -1250,6 +1422,10 @@ __global__ void k_pcc_decide(const SweepArgs a, int n_reps)
     }
     sx = __syncthreads_or(sx);
     sy = __syncthreads_or(sy);
+    if (R.flags & RF_WIND) {   // topological rule: the unions recorded the windings
+        sx = R.obs[j].spans_x;
+        sy = R.obs[j].spans_y;
+    }
     for (int64_t q = threadIdx.x; q < (int64_t)nx * R.tiles_x * 4; q += blockDim.x) R.cov[q] = 0u;
     for (int64_t q = threadIdx.x; q < (int64_t)ny * R.tiles_y * 4; q += blockDim.x)
         R.cov[(size_t)R.L * R.tiles_x * 4 + q] = 0u;

@@ -52,8 +52,8 @@ void launch_tile(const SweepArgs &a, bool pcc, int feat, cudaStream_t st)
 // The merge of launch group j: unions across tile edges, pointer jumping,
 // compression; for PCC lattices the span test and the feedback; then every
 // node's resolved root and new spin.
-template <int TH>
-void launch_merge(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
+template <int TH, bool W>
+void launch_merge_w(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
 {
     constexpr int S = Slots<TH>::S;
     constexpr int MT = MergeCfg<TH>::MT;
@@ -62,14 +62,24 @@ void launch_merge(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
     const unsigned bu = (unsigned)((nu + MERGE_THREADS - 1) / MERGE_THREADS);
     const unsigned bn = (unsigned)((nn + MERGE_THREADS - 1) / MERGE_THREADS);
     const unsigned tiles = (unsigned)a.n_tiles;
-    k_merge_union<TH><<<tiles, MT, 0, st>>>(a);
-    for (int r = 0; r < MERGE_JUMPS; ++r) k_merge_jump<TH><<<tiles, MT, 0, st>>>(a);
-    k_merge_resolve<TH><<<tiles, MT, 0, st>>>(a);
+    if (W) k_wind_init<TH><<<tiles, MT, 0, st>>>(a);
+    k_merge_union<TH, W><<<tiles, MT, 0, st>>>(a);
+    for (int r = 0; r < MERGE_JUMPS; ++r) k_merge_jump<TH, W><<<tiles, MT, 0, st>>>(a);
+    k_merge_resolve<TH, W><<<tiles, MT, 0, st>>>(a);
     if (pcc) {   // reads the compressed forest; the spins do not depend on it
         k_pcc_candidates<TH><<<bu, MERGE_THREADS, 0, st>>>(a);
         k_pcc_cover<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
         k_pcc_decide<TH><<<n_reps, 256, 0, st>>>(a, n_reps);
     }
+}
+
+template <int TH>
+void launch_merge(const SweepArgs &a, bool pcc, int feat, int n_reps, cudaStream_t st)
+{
+    if (feat & FEAT_WIND)
+        launch_merge_w<TH, true>(a, pcc, n_reps, st);
+    else
+        launch_merge_w<TH, false>(a, pcc, n_reps, st);
 }
 
 cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, int feat, cudaStream_t st)
@@ -83,13 +93,13 @@ cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, int feat, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
+cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int feat, int n_reps, cudaStream_t st)
 {
     switch (TH) {
-    case 32: launch_merge<32>(a, pcc, n_reps, st); break;
-    case 64: launch_merge<64>(a, pcc, n_reps, st); break;
-    case 96: launch_merge<96>(a, pcc, n_reps, st); break;
-    default: launch_merge<128>(a, pcc, n_reps, st); break;
+    case 32: launch_merge<32>(a, pcc, feat, n_reps, st); break;
+    case 64: launch_merge<64>(a, pcc, feat, n_reps, st); break;
+    case 96: launch_merge<96>(a, pcc, feat, n_reps, st); break;
+    default: launch_merge<128>(a, pcc, feat, n_reps, st); break;
     }
     return cudaGetLastError();
 }
@@ -99,7 +109,7 @@ cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, bool pcc, int feat, in
 {
     cudaError_t e = enqueue_tile(TH, a, pcc, feat, st);
     if (e != cudaSuccess) return e;
-    return enqueue_merge(TH, a, pcc, n_reps, st);
+    return enqueue_merge(TH, a, pcc, feat, n_reps, st);
 }
 
 cudaError_t prepare_th(int TH)
@@ -195,6 +205,7 @@ struct sw_ctx {
     uint64_t seed = 0;
     bool pcc = false;
     bool open = false;
+    bool wind = false;
     uint64_t sweep = 0;
     uint64_t thr = 0;
     bool swept = false;
@@ -221,6 +232,8 @@ struct sw_ctx {
     uint32_t *cov = nullptr;
     // cluster sizes (SW_FLAG_CSIZE)
     int32_t *psize = nullptr, *csize = nullptr;
+    // topological rule (SW_FLAG_WIND)
+    unsigned long long *nlink = nullptr;
 
     DevObs *obs = nullptr;
     int64_t obs_cap = 0, obs_head = 0, obs_tail = 0;
@@ -250,7 +263,7 @@ void ctx_free(sw_ctx *c)
     c->ev_pool.clear();
     void *ptrs[] = {c->spin, c->label, c->code, c->bondbits, c->cross, c->npar, c->nkey,
                     c->nfinal, c->thr_dev, c->rep_dev, c->tile_rep, c->jbase, c->bond_bytes, c->obs,
-                    c->pmask, c->cid, c->cand, c->ncand, c->cov, c->psize, c->csize};
+                    c->pmask, c->cid, c->cand, c->ncand, c->cov, c->psize, c->csize, c->nlink};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -296,6 +309,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
     c->seed = seed;
     c->pcc = pcc;
     c->open = (flags & SW_FLAG_OPEN) != 0;
+    c->wind = (flags & SW_FLAG_WIND) != 0;
     c->thr = thr;
     const size_t N = (size_t)L * L;
     const size_t nt = (size_t)c->n_tiles;
@@ -331,6 +345,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
         if ((e = dalloc(&c->psize, nt * c->S)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&c->csize, nt * c->S)) != cudaSuccess) return fail(e);
     }
+    if (c->wind && (e = dalloc(&c->nlink, nt * c->S)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(c->thr_dev, &c->thr, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
         return fail(e);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -344,7 +359,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
     R.key0 = k0;
     R.key1 = k1;
     R.nsweeps = 0;
-    R.flags = (pcc ? RF_PCC : 0) | (c->open ? RF_OPEN : 0) | (c->psize ? RF_CSIZE : 0);
+    R.flags = (pcc ? RF_PCC : 0) | (c->open ? RF_OPEN : 0) | (c->psize ? RF_CSIZE : 0) | (c->wind ? RF_WIND : 0);
     R.sweep0 = 0;
     R.thr = thr;
     R.thr_dev = c->thr_dev;
@@ -366,6 +381,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
     R.cov = c->cov;
     R.psize = c->psize;
     R.csize = c->csize;
+    R.nlink = c->nlink;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
     lk.unlock();
     *out = c;
@@ -375,7 +391,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
 // Tile-kernel features this lattice needs (FEAT_*).
 int ctx_features(const sw_ctx *c)
 {
-    return (c->psize ? FEAT_CSIZE : 0) | (c->open ? FEAT_OPEN : 0);
+    return (c->psize ? FEAT_CSIZE : 0) | (c->open ? FEAT_OPEN : 0) | (c->wind ? FEAT_WIND : 0);
 }
 
 int ensure_obs(sw_ctx *c, int64_t n)
@@ -464,7 +480,7 @@ int enqueue_profiled(sw_ctx *c, int32_t n)
         SW_CUDA(cudaEventRecord(e0, c->stream));
         SW_CUDA(enqueue_tile(c->TH, a, c->pcc, ctx_features(c), c->stream));
         SW_CUDA(cudaEventRecord(e1, c->stream));
-        if (j < n) SW_CUDA(enqueue_merge(c->TH, a, c->pcc, 1, c->stream));
+        if (j < n) SW_CUDA(enqueue_merge(c->TH, a, c->pcc, ctx_features(c), 1, c->stream));
         SW_CUDA(cudaEventRecord(e2, c->stream));
         c->ev_marks.push_back(e0);
         c->ev_marks.push_back(e1);

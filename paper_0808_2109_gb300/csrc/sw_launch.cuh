@@ -21,8 +21,8 @@ __attribute__((visibility("hidden"))) cudaError_t prepare_th(int TH);
 // the launch's lattices need)
 __attribute__((visibility("hidden"))) cudaError_t enqueue_tile(int TH, const SweepArgs &a, bool pcc, int feat,
                                                                cudaStream_t st);
-__attribute__((visibility("hidden"))) cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int n_reps,
-                                                                cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t enqueue_merge(int TH, const SweepArgs &a, bool pcc, int feat,
+                                                                int n_reps, cudaStream_t st);
 __attribute__((visibility("hidden"))) cudaError_t enqueue_launch_th(int TH, const SweepArgs &a, bool pcc, int feat,
                                                                     int n_reps, cudaStream_t st);
 __attribute__((visibility("hidden"))) cudaError_t enqueue_hot_start(uint8_t *spin, int64_t N, uint64_t seed,

@@ -63,6 +63,7 @@ struct Job {
     uint64_t *thr_dev = nullptr;
     DevObs *obs = nullptr;
     int32_t *psize = nullptr, *csize = nullptr;   // SW_FLAG_CSIZE
+    unsigned long long *nlink = nullptr;          // SW_FLAG_WIND
     // placement
     int lane = -1, slot = -1, tile_base = -1;
     int32_t jstart = 0;
@@ -71,11 +72,11 @@ struct Job {
 // Byte offsets of a job's buffers inside its one device block, each on a
 // 256-byte boundary; PCC scratch last, in one range that starts zeroed.
 struct JobLayout {
-    size_t spin, label, code, bondbits, cross, npar, nkey, nfinal, thr, obs, psize, csize;
+    size_t spin, label, code, bondbits, cross, npar, nkey, nfinal, thr, obs, psize, csize, nlink;
     size_t pmask, cid, cand, ncand, cov, pcc_end, total;
 };
 
-JobLayout job_layout(int L, int TH, int nsweeps, bool pcc, bool csize)
+JobLayout job_layout(int L, int TH, int nsweeps, bool pcc, bool csize, bool wind)
 {
     const size_t N = (size_t)L * L;
     const size_t tx = (L + TW - 1) / TW, ty = (L + TH - 1) / TH, nt = tx * ty;
@@ -102,6 +103,7 @@ JobLayout job_layout(int L, int TH, int nsweeps, bool pcc, bool csize)
         o.psize = take(nt * S * 4);
         o.csize = take(nt * S * 4);
     }
+    o.nlink = wind ? take(nt * S * 8) : at;
     o.pmask = o.cid = o.cand = o.ncand = o.cov = o.pcc_end = at;
     if (pcc) {
         o.pmask = take(nt * S * 8 * 4);
@@ -115,9 +117,9 @@ JobLayout job_layout(int L, int TH, int nsweeps, bool pcc, bool csize)
     return o;
 }
 
-size_t job_bytes(int L, int TH, int nsweeps, bool pcc, bool csize)
+size_t job_bytes(int L, int TH, int nsweeps, bool pcc, uint32_t flags)
 {
-    return job_layout(L, TH, nsweeps, pcc, csize).total;
+    return job_layout(L, TH, nsweeps, pcc, (flags & SW_FLAG_CSIZE) != 0, (flags & SW_FLAG_WIND) != 0).total;
 }
 
 struct Lane {
@@ -177,7 +179,8 @@ cudaError_t job_alloc(Job *j, cudaStream_t st)
 {
     const size_t N = (size_t)j->spec.L * j->spec.L;
     const bool csz = (j->spec.flags & SW_FLAG_CSIZE) != 0;
-    const JobLayout o = job_layout(j->spec.L, j->TH, j->spec.nsweeps, j->pcc, csz);
+    const bool wnd = (j->spec.flags & SW_FLAG_WIND) != 0;
+    const JobLayout o = job_layout(j->spec.L, j->TH, j->spec.nsweeps, j->pcc, csz, wnd);
     cudaError_t e = cudaMallocAsync(&j->block, o.total, st);
     if (e != cudaSuccess) {
         j->block = nullptr;
@@ -198,6 +201,7 @@ cudaError_t job_alloc(Job *j, cudaStream_t st)
         j->psize = reinterpret_cast<int32_t *>(b + o.psize);
         j->csize = reinterpret_cast<int32_t *>(b + o.csize);
     }
+    if (wnd) j->nlink = reinterpret_cast<unsigned long long *>(b + o.nlink);
     if (j->pcc) {
         j->pmask = reinterpret_cast<uint32_t *>(b + o.pmask);
         j->cid = reinterpret_cast<int32_t *>(b + o.cid);
@@ -221,7 +225,7 @@ Replica replica_of(const Job *j)
     R.key1 = (uint32_t)(j->spec.seed >> 32);
     R.nsweeps = j->spec.nsweeps;
     R.flags = (j->pcc ? RF_PCC : 0) | ((j->spec.flags & SW_FLAG_OPEN) ? RF_OPEN : 0) |
-              ((j->spec.flags & SW_FLAG_CSIZE) ? RF_CSIZE : 0);
+              ((j->spec.flags & SW_FLAG_CSIZE) ? RF_CSIZE : 0) | ((j->spec.flags & SW_FLAG_WIND) ? RF_WIND : 0);
     R.sweep0 = 0;
     R.thr = j->thr;
     R.thr_dev = j->thr_dev;
@@ -243,6 +247,7 @@ Replica replica_of(const Job *j)
     R.cov = j->cov;
     R.psize = j->psize;
     R.csize = j->csize;
+    R.nlink = j->nlink;
     return R;
 }
 
@@ -531,7 +536,8 @@ void worker_main(sw_server *s)
             for (Job *j : ln.slot_job) {
                 if (!j) continue;
                 pcc = pcc || j->pcc;
-                feat |= (j->psize ? FEAT_CSIZE : 0) | ((j->spec.flags & SW_FLAG_OPEN) ? FEAT_OPEN : 0);
+                feat |= (j->psize ? FEAT_CSIZE : 0) | ((j->spec.flags & SW_FLAG_OPEN) ? FEAT_OPEN : 0) |
+                        (j->nlink ? FEAT_WIND : 0);
             }
             if (pcc != ln.graph_pcc || feat != ln.graph_feat) ln.recapture = true;
             if (ln.dirty) {
@@ -660,7 +666,7 @@ int sw_batch_submit(sw_server *s, const sw_job *jobs, int32_t n, uint64_t *ids_o
         }
         made.push_back(j);
         j->spec = q;
-        if (q.L < 2 || q.L > SERVER_MAX_L || q.nsweeps < 1 || (q.flags & ~(SW_FLAG_OPEN | SW_FLAG_CSIZE)) != 0 ||
+        if (q.L < 2 || q.L > SERVER_MAX_L || q.nsweeps < 1 || (q.flags & ~(SW_FLAG_OPEN | SW_FLAG_CSIZE | SW_FLAG_WIND)) != 0 ||
             (q.tile_h != 0 && q.tile_h != 32 && q.tile_h != 64 && q.tile_h != 96 && q.tile_h != 128)) {
             rc = SW_ERR_ARG;
             break;
@@ -687,7 +693,7 @@ int sw_batch_submit(sw_server *s, const sw_job *jobs, int32_t n, uint64_t *ids_o
         j->tiles_y = (q.L + j->TH - 1) / j->TH;
         j->n_tiles = j->tiles_x * j->tiles_y;
         j->S = slots_of(j->TH);
-        j->bytes = job_bytes(q.L, j->TH, q.nsweeps, j->pcc, (q.flags & SW_FLAG_CSIZE) != 0);
+        j->bytes = job_bytes(q.L, j->TH, q.nsweeps, j->pcc, q.flags);
         if (j->bytes > s->budget) rc = SW_ERR_NOMEM;
     }
     if (rc != SW_OK) {

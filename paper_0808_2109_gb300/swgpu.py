@@ -62,6 +62,7 @@ SW_JOB_SW, SW_JOB_SWP, SW_JOB_PCC = 0, 1, 2
 SW_FLAG_TILE = {32: 1 << 8, 64: 1 << 9, 96: 1 << 11, 128: 1 << 10}
 SW_FLAG_OPEN = 1 << 12
 SW_FLAG_CSIZE = 1 << 13
+SW_FLAG_WIND = 1 << 14
 
 
 class SwJob(ctypes.Structure):
@@ -352,14 +353,15 @@ def sw_autotune(L: int, T: float) -> int:
 class Lattice:
     """One L x L lattice on the GPU (plain SW at J, T or p; or PCC), with
     periodic or (open=True) open boundaries; csize=True also reports
-    sum |C|^2 per sweep (obs["csize2"])."""
+    sum |C|^2 per sweep (obs["csize2"]); wind=True reports the topological
+    rule in spans_x/spans_y (and PCC feeds back on it)."""
 
     def __init__(self, L: int, *, J: float = 1.0, T: float | None = None, p: float | None = None,
                  seed: int = 1, pcc: bool = False, tile_h: int = 0, open: bool = False,
-                 csize: bool = False):
+                 csize: bool = False, wind: bool = False):
         self.L = int(L)
         flags = (SW_FLAG_TILE.get(int(tile_h), 0) | (SW_FLAG_OPEN if open else 0)
-                 | (SW_FLAG_CSIZE if csize else 0))
+                 | (SW_FLAG_CSIZE if csize else 0) | (SW_FLAG_WIND if wind else 0))
         if pcc:
             self.h = pcc_create(self.L, seed, flags)
         elif p is not None:
@@ -447,7 +449,7 @@ class Server:
 
     def submit(self, specs, want_obs=True, want_spins=False, want_labels=False) -> list[int]:
         """specs: dicts with L, sweeps, seed and T (plain), p, or pcc=True;
-        optional tile_h, open=True (open boundaries) and csize=True."""
+        optional tile_h, open=True (open boundaries), csize=True and wind=True."""
         jobs, outs = [], []
         for sp in specs:
             L, n = int(sp["L"]), int(sp["sweeps"])
@@ -464,7 +466,8 @@ class Server:
             else:
                 j.kind, j.T = SW_JOB_SW, float(sp["T"])
             j.tile_h = int(sp.get("tile_h", 0))
-            j.flags = (SW_FLAG_OPEN if sp.get("open") else 0) | (SW_FLAG_CSIZE if sp.get("csize") else 0)
+            j.flags = ((SW_FLAG_OPEN if sp.get("open") else 0) | (SW_FLAG_CSIZE if sp.get("csize") else 0)
+                       | (SW_FLAG_WIND if sp.get("wind") else 0))
             j.obs_out = o["obs"].ctypes.data if want_obs else None
             j.spins_out = o["spins"].ctypes.data if want_spins else None
             j.labels_out = o["labels"].ctypes.data if want_labels else None
