@@ -498,11 +498,16 @@ constexpr size_t tile_smem(bool pcc)
 }
 
 // ----------------------------------------------------------------- k_tile
-// Optional features of the tile kernel, compiled in only where a launch has a
-// lattice that needs them, so the plain kernel carries none of their code.
+// Optional features, compiled in only where a launch has a lattice that
+// needs them, so the plain kernels carry none of their code.  The tile kernel
+// comes in two variants, plain (F = 0) and with every tile feature (F =
+// FEAT_TILE, each feature then checked per lattice); the merge kernels with
+// and without FEAT_WIND.
 constexpr int FEAT_CSIZE = 1;   // cluster sizes (RF_CSIZE)
 constexpr int FEAT_OPEN = 2;    // open boundaries (RF_OPEN)
 constexpr int FEAT_WIND = 4;    // topological rule (RF_WIND; merge kernels only)
+constexpr int FEAT_PCC = 8;     // PCC piece masks (RF_PCC)
+constexpr int FEAT_TILE = FEAT_CSIZE | FEAT_OPEN | FEAT_PCC;
 
 template <int TH, int F>
 __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(const SweepArgs a)
@@ -665,7 +670,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         }
         __syncthreads();
     }
-    const bool pcc = (R.flags & RF_PCC) != 0;
+    const bool pcc = (F & FEAT_PCC) && (R.flags & RF_PCC) != 0;
     if (pcc)
         for (int q = tid; q < S * 8; q += NT) (&sm.pm[0][0])[q] = 0u;
     if (t.lt == 0 && tid == 0) {
@@ -906,12 +911,17 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         const int base = y * PW + 32 * c;
         int slot = -1;            // PCC: border piece of the sites gathered in cols
         uint32_t cols = 0u;
+        int info = 0;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int x = xb + e;
             if (x >= t.tw) break;
-            const int v = sm.par[head_of(heads, base, x & 31)];
-            const int info = (v < 0 || (uint32_t)v >= INFO_INTERIOR) ? v : sm.par[v];
+            // a site inside a run shares the run head's code: look up only
+            // where a run starts (and for the group's first site)
+            if (e == 0 || ((heads >> (x & 31)) & 1u)) {
+                const int v = sm.par[e == 0 ? head_of(heads, base, x & 31) : base + (x & 31)];
+                info = ((uint32_t)v >= INFO_INTERIOR) ? v : sm.par[v];   // records: negative or >= INFO_INTERIOR
+            }
             wv[e >> 1] |= ((uint32_t)info & 0xFFFFu) << (16 * (e & 1));
             if (pcc && info < 0) {
                 // the columns and rows each border piece occupies (only a

@@ -28,9 +28,8 @@ cudaError_t tile_prepare()
     static bool done = false;
     static cudaError_t err = cudaSuccess;
     if (!done) {
-        const void *fn[4] = {(const void *)k_tile<TH, 0>, (const void *)k_tile<TH, 1>, (const void *)k_tile<TH, 2>,
-                             (const void *)k_tile<TH, 3>};
-        for (int f = 0; f < 4 && err == cudaSuccess; ++f)
+        const void *fn[2] = {(const void *)k_tile<TH, 0>, (const void *)k_tile<TH, FEAT_TILE>};
+        for (int f = 0; f < 2 && err == cudaSuccess; ++f)
             err = cudaFuncSetAttribute(fn[f], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<TH>(true));
         done = true;
     }
@@ -41,12 +40,10 @@ template <int TH>
 void launch_tile(const SweepArgs &a, bool pcc, int feat, cudaStream_t st)
 {
     const size_t smem = tile_smem<TH>(pcc);
-    switch (feat & 3) {
-    case 0: k_tile<TH, 0><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a); break;
-    case 1: k_tile<TH, 1><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a); break;
-    case 2: k_tile<TH, 2><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a); break;
-    default: k_tile<TH, 3><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a); break;
-    }
+    if (pcc || (feat & FEAT_TILE))
+        k_tile<TH, FEAT_TILE><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a);
+    else
+        k_tile<TH, 0><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a);
 }
 
 // The merge of launch group j: unions across tile edges, pointer jumping,
