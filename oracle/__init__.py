@@ -112,6 +112,22 @@ def lib():
             L.swo_spans_open.restype = ctypes.c_int
             L.swo_windings.argtypes = [i32, P, P, P]
             L.swo_windings.restype = ctypes.c_int
+            L.swo_threshold_potts.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.swo_threshold_potts.restype = u64
+            L.swo_potts_hot_start.argtypes = [i32, i32, i32, u64, P]
+            L.swo_potts_hot_start.restype = None
+            L.swo_potts_bonds.argtypes = [i32, i32, u64, u64, u64, P, P]
+            L.swo_potts_bonds.restype = i64
+            L.swo_label_nd.argtypes = [i32, i32, P, P]
+            L.swo_label_nd.restype = i64
+            L.swo_count_clusters_nd.argtypes = [i32, i32, i64, P, P]
+            L.swo_count_clusters_nd.restype = None
+            L.swo_potts_assign.argtypes = [i32, i32, i32, u64, u64, P, P]
+            L.swo_potts_assign.restype = None
+            L.swo_potts_measure.argtypes = [i32, i32, i32, P, P, P]
+            L.swo_potts_measure.restype = None
+            L.swo_potts_run.argtypes = [i32, i32, i32, u64, u64, i32, i32, u64, P, P, P, P]
+            L.swo_potts_run.restype = ctypes.c_int
             L.swo_csize2.argtypes = [i32, P]
             L.swo_csize2.restype = i64
             L.swo_pcc_delta.argtypes = [u64]
@@ -287,3 +303,77 @@ def pcc_chain(L: int, seed: int, open: bool = False, csize: bool = False, wind: 
 def energy_per_site(obs: np.ndarray, L: int, J: float = 1.0) -> np.ndarray:
     """E/N = -J * bond_sum / N per sweep, in float64."""
     return -J * obs["bond_sum"].astype(np.float64) / float(L * L)
+
+
+# ------------------------------------------------- q-state Potts, d = 2 or 3
+
+def threshold_potts(J: float, T: float) -> int:
+    return int(lib().swo_threshold_potts(float(J), float(T)))
+
+
+def potts_hot_start(dim: int, L: int, q: int, seed: int) -> np.ndarray:
+    spin = np.empty(L ** dim, dtype=np.uint8)
+    lib().swo_potts_hot_start(dim, L, q, seed, _ptr(spin))
+    return spin
+
+
+def potts_bonds(dim: int, L: int, seed: int, sweep: int, thr: int, spin: np.ndarray):
+    spin = np.ascontiguousarray(spin, dtype=np.uint8)
+    bond = np.empty(L ** dim, dtype=np.uint8)
+    nb = lib().swo_potts_bonds(dim, L, seed, sweep, thr, _ptr(spin), _ptr(bond))
+    return bond, int(nb)
+
+
+def label_nd(dim: int, L: int, bond: np.ndarray):
+    bond = np.ascontiguousarray(bond, dtype=np.uint8)
+    lab = np.empty(L ** dim, dtype=np.int32)
+    nc = lib().swo_label_nd(dim, L, _ptr(bond), _ptr(lab))
+    return lab, int(nc)
+
+
+def count_clusters_nd(dim: int, L: int, bond_sets: np.ndarray) -> np.ndarray:
+    bond_sets = np.ascontiguousarray(bond_sets, dtype=np.uint8).reshape(-1, L ** dim)
+    counts = np.empty(bond_sets.shape[0], dtype=np.int64)
+    lib().swo_count_clusters_nd(dim, L, bond_sets.shape[0], _ptr(bond_sets), _ptr(counts))
+    return counts
+
+
+def potts_assign(dim: int, L: int, q: int, seed: int, sweep: int, lab: np.ndarray) -> np.ndarray:
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    spin = np.empty(L ** dim, dtype=np.uint8)
+    lib().swo_potts_assign(dim, L, q, seed, sweep, _ptr(lab), _ptr(spin))
+    return spin
+
+
+def potts_measure(dim: int, L: int, q: int, spin: np.ndarray):
+    spin = np.ascontiguousarray(spin, dtype=np.uint8)
+    bs = np.zeros(1, dtype=np.int64)
+    m = np.zeros(1, dtype=np.int64)
+    lib().swo_potts_measure(dim, L, q, _ptr(spin), _ptr(bs), _ptr(m))
+    return int(bs[0]), int(m[0])
+
+
+class PottsChain:
+    """A q-state Potts lattice (d = 2 or 3) advanced by the oracle."""
+
+    def __init__(self, dim: int, L: int, q: int, J: float, T: float, seed: int, csize: bool = False):
+        if dim not in (2, 3) or L < 2 or not 2 <= q <= 256:
+            raise ValueError("dim in {2, 3}, L >= 2, 2 <= q <= 256")
+        self.dim, self.L, self.q, self.seed, self.csize = int(dim), int(L), int(q), int(seed), bool(csize)
+        self.threshold = threshold_potts(J, T)
+        self.sweep = 0
+        self.spin = potts_hot_start(dim, L, q, seed)
+        self.label = np.arange(L ** dim, dtype=np.int32)
+        self.bond = np.zeros(L ** dim, dtype=np.uint8)
+
+    def run(self, nsweeps: int) -> np.ndarray:
+        obs = np.zeros(nsweeps, dtype=OBS_DTYPE)
+        if nsweeps <= 0:
+            return obs
+        rc = lib().swo_potts_run(self.dim, self.L, self.q, self.seed, self.sweep, nsweeps,
+                                 1 if self.csize else 0, self.threshold, _ptr(self.spin),
+                                 _ptr(self.label), _ptr(self.bond), _ptr(obs))
+        if rc != 0:
+            raise MemoryError("swo_potts_run")
+        self.sweep += nsweeps
+        return obs

@@ -519,3 +519,170 @@ int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t 
         free(b);
     return rc;
 }
+
+/* ========================================================================
+ * q-state Potts model on the periodic d-dimensional lattice (d = 2 or 3).
+ * The paper states the cluster update for general d (Sec. II); the Potts
+ * form of SW replaces "equal spins" by "equal states" and a fair bit by a
+ * uniform state.  Conventions (a reading: the paper fixes none of them):
+ *   - N = L^d sites, i = x + L*y (+ L*L*z); site i owns link dir = 0 (+x),
+ *     1 (+y), 2 (+z), link index l = d*i + dir.
+ *   - H = -J sum over links of delta(s_i, s_j); a link between equal states
+ *     bonds with P = 1 - exp(-J/T) (for q = 2 this is the Ising update with
+ *     J_Ising = J/2), drawing word (l mod 4) of Philox(l/4, k, BOND).
+ *   - A cluster with root r takes state floor(w*q / 2^32), w = word (r mod 4)
+ *     of Philox(r/4, k, QSPIN); the hot start takes the same function of
+ *     word (i mod 4) of Philox(i/4, 0, INIT).
+ *   - bond_sum = sum over links of (2 delta - 1) (for q = 2: sum sigma sigma),
+ *     mag = sum over sites of (q [s_i = 0] - 1).
+ * ======================================================================== */
+static uint64_t nd_neighbour(int32_t dim, int32_t L, uint64_t i, int dir)
+{
+    uint64_t l = (uint64_t)L, x = i % l, y = (i / l) % l, z = i / (l * l);
+    if (dir == 0)
+        x = (x + 1) % l;
+    else if (dir == 1)
+        y = (y + 1) % l;
+    else
+        z = (z + 1) % l;
+    return dim == 2 ? y * l + x : (z * l + y) * l + x;
+}
+
+static uint64_t nd_sites(int32_t dim, int32_t L)
+{
+    uint64_t n = (uint64_t)L * (uint64_t)L;
+    return dim == 3 ? n * (uint64_t)L : n;
+}
+
+static uint8_t potts_state(uint32_t w, int32_t q)
+{
+    return (uint8_t)(((uint64_t)w * (uint64_t)q) >> 32);
+}
+
+uint64_t swo_threshold_potts(double J, double T)
+{
+    return swo_threshold_p(1.0 - exp(-J / T));
+}
+
+void swo_potts_hot_start(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint8_t *spin)
+{
+    uint64_t N = nd_sites(dim, L);
+    for (uint64_t i = 0; i < N; i++) {
+        uint32_t w[4];
+        stream_block(seed, i / 4, 0, SWO_STREAM_INIT, w);
+        spin[i] = potts_state(w[i % 4], q);
+    }
+}
+
+int64_t swo_potts_bonds(int32_t dim, int32_t L, uint64_t seed, uint64_t sweep, uint64_t thr,
+                        const uint8_t *spin, uint8_t *bond)
+{
+    uint64_t N = nd_sites(dim, L);
+    int64_t nb = 0;
+    for (uint64_t i = 0; i < N; i++) {
+        uint8_t b = 0;
+        for (int dir = 0; dir < dim; dir++) {
+            uint64_t j = nd_neighbour(dim, L, i, dir);
+            uint64_t l = (uint64_t)dim * i + (uint64_t)dir;
+            uint32_t w[4];
+            stream_block(seed, l / 4, sweep, SWO_STREAM_BOND, w);
+            if (spin[i] == spin[j] && (uint64_t)w[l % 4] < thr) {
+                b |= (uint8_t)(1u << dir);
+                nb++;
+            }
+        }
+        bond[i] = b;
+    }
+    return nb;
+}
+
+/* Clusters of a d-dimensional bond set: union of the ends of every bond,
+ * the smaller root winning, then every site's root (its cluster minimum). */
+int64_t swo_label_nd(int32_t dim, int32_t L, const uint8_t *bond, int32_t *label)
+{
+    uint64_t N = nd_sites(dim, L);
+    for (uint64_t i = 0; i < N; i++)
+        label[i] = (int32_t)i;
+    for (uint64_t i = 0; i < N; i++)
+        for (int dir = 0; dir < dim; dir++)
+            if ((bond[i] >> dir) & 1u)
+                uf_unite(label, (int32_t)i, (int32_t)nd_neighbour(dim, L, i, dir));
+    int64_t nclusters = 0;
+    for (uint64_t i = 0; i < N; i++) {
+        label[i] = uf_find(label, (int32_t)i);
+        if ((uint64_t)label[i] == i)
+            nclusters++;
+    }
+    return nclusters;
+}
+
+void swo_count_clusters_nd(int32_t dim, int32_t L, int64_t nsets, const uint8_t *bonds, int64_t *counts)
+{
+    uint64_t N = nd_sites(dim, L);
+    int32_t *label = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    for (int64_t s = 0; s < nsets; s++)
+        counts[s] = label ? swo_label_nd(dim, L, bonds + s * (int64_t)N, label) : -1;
+    free(label);
+}
+
+void swo_potts_assign(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep,
+                      const int32_t *label, uint8_t *spin)
+{
+    uint64_t N = nd_sites(dim, L);
+    for (uint64_t i = 0; i < N; i++) {
+        uint64_t r = (uint64_t)label[i];
+        uint32_t w[4];
+        stream_block(seed, r / 4, sweep, SWO_STREAM_QSPIN, w);
+        spin[i] = potts_state(w[r % 4], q);
+    }
+}
+
+void swo_potts_measure(int32_t dim, int32_t L, int32_t q, const uint8_t *spin, int64_t *bond_sum,
+                       int64_t *mag)
+{
+    uint64_t N = nd_sites(dim, L);
+    int64_t bs = 0, m = 0;
+    for (uint64_t i = 0; i < N; i++) {
+        m += spin[i] == 0 ? q - 1 : -1;
+        for (int dir = 0; dir < dim; dir++)
+            bs += spin[i] == spin[nd_neighbour(dim, L, i, dir)] ? 1 : -1;
+    }
+    *bond_sum = bs;
+    *mag = m;
+}
+
+int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
+                  int32_t csize, uint64_t thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
+{
+    uint64_t N = nd_sites(dim, L);
+    uint8_t *b = bond ? bond : (uint8_t *)malloc((size_t)N);
+    if (!b)
+        return -1;
+    int rc = 0;
+    for (int32_t n = 0; n < nsweeps; n++) {
+        uint64_t k = sweep0 + (uint64_t)n;
+        swo_obs o;
+        memset(&o, 0, sizeof(o));
+        o.threshold = thr;
+        o.nbonds = swo_potts_bonds(dim, L, seed, k, thr, spin, b);
+        o.nclusters = swo_label_nd(dim, L, b, label);
+        if (csize) {
+            int64_t *count = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+            if (!count) {
+                rc = -1;
+                break;
+            }
+            for (uint64_t i = 0; i < N; i++)
+                count[label[i]]++;
+            for (uint64_t r = 0; r < N; r++)
+                o.csize2 += count[r] * count[r];
+            free(count);
+        }
+        swo_potts_assign(dim, L, q, seed, k, label, spin);
+        swo_potts_measure(dim, L, q, spin, &o.bond_sum, &o.mag);
+        obs[n] = o;
+    }
+    if (!bond)
+        free(b);
+    return rc;
+}

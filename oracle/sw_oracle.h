@@ -35,6 +35,7 @@ extern "C" {
 #define SWO_STREAM_INIT 0u
 #define SWO_STREAM_BOND 1u
 #define SWO_STREAM_SPIN 2u
+#define SWO_STREAM_QSPIN 3u   /* Potts cluster states */
 
 /* Observables of one sweep (all taken after the cluster flip). */
 typedef struct {
@@ -114,6 +115,27 @@ uint64_t swo_pcc_update(uint64_t thr, uint64_t sweep, int32_t flag);
  * per-sweep observables.  Returns 0, or -1 when memory is short. */
 int swo_run(int32_t L, uint64_t seed, uint64_t sweep0, int32_t nsweeps, int32_t pcc, int32_t open,
             int32_t csize, int32_t wind, uint64_t *thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
+
+/* ---- q-state Potts model on the periodic d-dimensional lattice (d = 2, 3).
+ * Site i = x + L*y (+ L*L*z), link l = d*i + dir (dir 0: +x, 1: +y, 2: +z),
+ * bond bytes bit dir.  H = -J sum delta(s_i, s_j), bonds with P = 1 - exp(-J/T).
+ * States: floor(w*q / 2^32) of a Philox word (hot start: word i mod 4 of
+ * Philox(i/4, 0, INIT); cluster with root r: word r mod 4 of Philox(r/4, k,
+ * QSPIN)).  bond_sum = sum over links of (2 delta - 1); mag = sum over sites of
+ * (q [s_i = 0] - 1). */
+uint64_t swo_threshold_potts(double J, double T);
+void swo_potts_hot_start(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint8_t *spin);
+int64_t swo_potts_bonds(int32_t dim, int32_t L, uint64_t seed, uint64_t sweep, uint64_t thr,
+                        const uint8_t *spin, uint8_t *bond);
+int64_t swo_label_nd(int32_t dim, int32_t L, const uint8_t *bond, int32_t *label);
+void swo_count_clusters_nd(int32_t dim, int32_t L, int64_t nsets, const uint8_t *bonds, int64_t *counts);
+void swo_potts_assign(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep,
+                      const int32_t *label, uint8_t *spin);
+void swo_potts_measure(int32_t dim, int32_t L, int32_t q, const uint8_t *spin, int64_t *bond_sum,
+                       int64_t *mag);
+/* nsweeps sweeps at the fixed threshold thr (obs[].csize2 filled when csize). */
+int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
+                  int32_t csize, uint64_t thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
 
 #ifdef __cplusplus
 }
