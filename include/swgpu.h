@@ -103,7 +103,9 @@ typedef struct {
     uint64_t sweep;     /* sweeps done since creation = index of the next one */
     uint64_t threshold; /* threshold the next sweep will use                 */
     int32_t open;       /* 1 for open boundaries (SW_FLAG_OPEN)              */
-    int32_t tile_h;     /* rows per tile                                     */
+    int32_t tile_h;     /* rows per tile (0 for a Potts lattice)             */
+    int32_t dim;        /* 2, or 3 for a 3D Potts lattice                    */
+    int32_t q;          /* states per site (2 for the Ising lattices)        */
 } sw_state;
 
 /* Name of a status code (static string). */
@@ -135,6 +137,23 @@ int sw_create_p(sw_ctx **out, int32_t L, double p, uint64_t seed, uint32_t flags
  * the extension rule under periodic boundaries, up otherwise, clamped to
  * [0, 2^32].  Errors as sw_create. */
 int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags);
+
+/* A q-state Potts lattice (2 <= q <= 256) on the periodic d-dimensional
+ * torus, d = 2 or 3, L^d <= 2^30 sites: the cluster update of Sec. I with
+ * equal states bonding (H = -J sum delta(s_i, s_j), P = 1 - exp(-J/T); q = 2
+ * is Ising at J/2) on the d-dimensional lattice the paper states its method
+ * for (Sec. II).  A site-level path, slower than the tiled 2D Ising one.
+ * Sites i = x + L y (+ L^2 z); link l = d i + dir (dir 0: +x, 1: +y, 2: +z)
+ * draws word (l mod 4) of Philox(l/4, k, BOND); a cluster with root r takes
+ * state floor(w q / 2^32), w = word (r mod 4) of Philox(r/4, k, stream 3);
+ * the hot start is the same of word (i mod 4) of Philox(i/4, 0, INIT).
+ * Observables: bond_sum = sum over links of (2 delta - 1), mag = sum over
+ * sites of (q [s_i = 0] - 1).  flags: SW_FLAG_CSIZE or 0.  The other calls
+ * take the context as usual (spins, labels and bond bytes have L^d entries,
+ * bond bit dir); pcc_step and sw_profile answer SW_ERR_STATE.  Errors:
+ * SW_ERR_ARG, SW_ERR_NOMEM, SW_ERR_CUDA. */
+int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, double T, uint64_t seed,
+                    uint32_t flags);
 
 /* Release the context and all its device memory.  NULL is accepted. */
 int sw_destroy(sw_ctx *ctx);

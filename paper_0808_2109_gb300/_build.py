@@ -11,7 +11,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD, "libswgpu.so")
 
-SOURCES = ["sw_engine.cu", "sw_server.cu", "sw_noalloc.cu"]
+SOURCES = ["sw_engine.cu", "sw_server.cu", "sw_noalloc.cu", "sw_potts.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -231,6 +231,11 @@ struct sw_ctx {
     int32_t *psize = nullptr, *csize = nullptr;
     // topological rule (SW_FLAG_WIND)
     unsigned long long *nlink = nullptr;
+    // a q-state Potts lattice (sw_create_potts): spin, label, bond_bytes and
+    // psize hold its state; none of the tile scratch exists
+    bool is_potts = false;
+    PottsDev pd{};
+    int64_t nsites = 0;   // L^d
 
     DevObs *obs = nullptr;
     int64_t obs_cap = 0, obs_head = 0, obs_tail = 0;
@@ -298,6 +303,7 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
     cudaError_t e = cudaGetDevice(&c->dev);
     if (e != cudaSuccess) return fail(e);
     c->L = L;
+    c->nsites = (int64_t)L * L;
     c->TH = pick_tile_height(L, flags);
     c->S = slots_of(c->TH);
     c->tiles_x = (L + TW - 1) / TW;
@@ -494,6 +500,16 @@ int run_sweeps(sw_ctx *c, int32_t n)
     cudaGetLastError();   // a stale error of an unrelated earlier call is not ours
     int rc = ensure_obs(c, n);
     if (rc != SW_OK) return rc;
+    if (c->is_potts) {
+        DevObs *obs = c->obs + c->obs_tail;
+        SW_CUDA(cudaMemsetAsync(obs, 0, (size_t)n * sizeof(DevObs), c->stream));
+        for (int32_t k = 0; k < n; ++k)
+            SW_CUDA(potts_enqueue_sweep(c->pd, c->sweep + (uint64_t)k, obs + k, c->stream));
+        c->obs_tail += n;
+        c->sweep += (uint64_t)n;
+        c->swept = true;
+        return SW_OK;
+    }
     Replica &R = c->rep;
     R.sweep0 = c->sweep;
     R.nsweeps = n;
@@ -615,6 +631,60 @@ int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags)
     return ctx_create(out, L, (uint64_t)1 << 31, seed, true, flags);   // p = 1/2
 }
 
+int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, double T, uint64_t seed,
+                    uint32_t flags)
+{
+    if (!out) return SW_ERR_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || L < 2 || q < 2 || q > 256 || (flags & ~SW_FLAG_CSIZE) != 0) return SW_ERR_ARG;
+    const int64_t N = dim == 2 ? (int64_t)L * L : (int64_t)L * L * L;
+    if (N > ((int64_t)1 << 30)) return SW_ERR_ARG;
+    // P = 1 - exp(-J/T): the Ising threshold at J/2 (the same double)
+    uint64_t thr = 0;
+    int rc = sw_threshold(0.5 * J, T, &thr);
+    if (rc != SW_OK) return rc;
+    cudaGetLastError();
+    sw_ctx *c = new (std::nothrow) sw_ctx();
+    if (!c) return SW_ERR_NOMEM;
+    std::unique_lock<std::mutex> lk(sw_capture_mutex());
+    auto fail = [&](cudaError_t e) {
+        rc = sw_cuda_fail(e, __LINE__);
+        lk.unlock();
+        ctx_free(c);
+        return rc;
+    };
+    cudaError_t e = cudaGetDevice(&c->dev);
+    if (e != cudaSuccess) return fail(e);
+    c->is_potts = true;
+    c->L = L;
+    c->nsites = N;
+    c->seed = seed;
+    c->thr = thr;
+    if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    c->stream = c->own_stream;
+    if ((e = dalloc(&c->spin, (size_t)N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->label, (size_t)N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->bond_bytes, (size_t)N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->jbase, 1)) != cudaSuccess) return fail(e);
+    if ((flags & SW_FLAG_CSIZE) && (e = dalloc(&c->psize, (size_t)N)) != cudaSuccess) return fail(e);
+    PottsDev &p = c->pd;
+    p.dim = dim;
+    p.L = L;
+    p.q = q;
+    p.N = N;
+    p.thr = thr;
+    p.seed = seed;
+    p.spin = c->spin;
+    p.bond = c->bond_bytes;
+    p.label = c->label;
+    p.size = c->psize;
+    if ((e = potts_enqueue_hot_start(p, c->stream)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
+    lk.unlock();
+    *out = c;
+    return SW_OK;
+}
+
 int sw_destroy(sw_ctx *ctx)
 {
     if (!ctx) return SW_OK;
@@ -665,8 +735,7 @@ int sw_get_spins(sw_ctx *ctx, uint8_t *host_out)
 {
     if (!ctx || !host_out) return SW_ERR_ARG;
     SW_CUDA(cudaSetDevice(ctx->dev));
-    SW_CUDA(cudaMemcpyAsync(host_out, ctx->spin, (size_t)ctx->L * ctx->L, cudaMemcpyDeviceToHost,
-                            ctx->stream));
+    SW_CUDA(cudaMemcpyAsync(host_out, ctx->spin, (size_t)ctx->nsites, cudaMemcpyDeviceToHost, ctx->stream));
     SW_CUDA(cudaStreamSynchronize(ctx->stream));
     return SW_OK;
 }
@@ -674,15 +743,21 @@ int sw_get_spins(sw_ctx *ctx, uint8_t *host_out)
 int sw_set_spins(sw_ctx *ctx, const uint8_t *host_in)
 {
     if (!ctx || !host_in) return SW_ERR_ARG;
-    const size_t N = (size_t)ctx->L * ctx->L;
+    const size_t N = (size_t)ctx->nsites;
     SW_CUDA(cudaSetDevice(ctx->dev));
-    // Stage in the site-code buffer (free between calls; at least N bytes),
-    // check every byte on the device, and only then replace the spins.
-    uint8_t *stage = reinterpret_cast<uint8_t *>(ctx->code);
+    // Stage in a buffer that is free between calls (the site codes, or a
+    // Potts lattice's bond bytes; at least N bytes), check every byte on the
+    // device, and only then replace the spins.
+    uint8_t *stage = ctx->is_potts ? ctx->bond_bytes : reinterpret_cast<uint8_t *>(ctx->code);
     int32_t *bad = ctx->jbase;   // scratch word, rewritten by every sweep call
     SW_CUDA(cudaMemcpyAsync(stage, host_in, N, cudaMemcpyHostToDevice, ctx->stream));
     SW_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), ctx->stream));
-    k_check_spins<<<(unsigned)std::min<size_t>((N + 4095) / 4096, 4096), 256, 0, ctx->stream>>>(stage, (int64_t)N, bad);
+    if (ctx->is_potts) {
+        SW_CUDA(potts_enqueue_check(stage, (int64_t)N, ctx->pd.q, bad, ctx->stream));
+    } else {
+        k_check_spins<<<(unsigned)std::min<size_t>((N + 4095) / 4096, 4096), 256, 0, ctx->stream>>>(stage, (int64_t)N,
+                                                                                                   bad);
+    }
     SW_CUDA(cudaGetLastError());
     int32_t hbad = 0;
     SW_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -696,6 +771,7 @@ int sw_set_spins(sw_ctx *ctx, const uint8_t *host_in)
 int sw_profile(sw_ctx *ctx, int32_t enable)
 {
     if (!ctx) return SW_ERR_ARG;
+    if (ctx->is_potts) return SW_ERR_STATE;
     ctx->profiling = enable != 0;
     return SW_OK;
 }
@@ -731,8 +807,8 @@ int sw_get_labels(sw_ctx *ctx, int32_t *host_out)
     if (!ctx || !host_out) return SW_ERR_ARG;
     if (!ctx->swept) return SW_ERR_STATE;
     SW_CUDA(cudaSetDevice(ctx->dev));
-    SW_CUDA(cudaMemcpyAsync(host_out, ctx->label, (size_t)ctx->L * ctx->L * sizeof(int32_t),
-                            cudaMemcpyDeviceToHost, ctx->stream));
+    SW_CUDA(cudaMemcpyAsync(host_out, ctx->label, (size_t)ctx->nsites * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            ctx->stream));
     SW_CUDA(cudaStreamSynchronize(ctx->stream));
     return SW_OK;
 }
@@ -742,7 +818,12 @@ int sw_get_bonds(sw_ctx *ctx, uint8_t *host_out)
     if (!ctx || !host_out) return SW_ERR_ARG;
     if (!ctx->swept) return SW_ERR_STATE;
     SW_CUDA(cudaSetDevice(ctx->dev));
-    const size_t N = (size_t)ctx->L * ctx->L;
+    const size_t N = (size_t)ctx->nsites;
+    if (ctx->is_potts) {   // the bond bytes of the last sweep, as they are
+        SW_CUDA(cudaMemcpyAsync(host_out, ctx->bond_bytes, N, cudaMemcpyDeviceToHost, ctx->stream));
+        SW_CUDA(cudaStreamSynchronize(ctx->stream));
+        return SW_OK;
+    }
     if (!ctx->bond_bytes) {
         std::lock_guard<std::mutex> lk(sw_capture_mutex());
         SW_CUDA(dalloc(&ctx->bond_bytes, N));
@@ -775,7 +856,9 @@ int sw_get_state(sw_ctx *ctx, sw_state *out)
     out->sweep = ctx->sweep;
     out->threshold = thr;
     out->open = ctx->open ? 1 : 0;
-    out->tile_h = ctx->TH;
+    out->tile_h = ctx->is_potts ? 0 : ctx->TH;
+    out->dim = ctx->is_potts ? ctx->pd.dim : 2;
+    out->q = ctx->is_potts ? ctx->pd.q : 2;
     return SW_OK;
 }
 

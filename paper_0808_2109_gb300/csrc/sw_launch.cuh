@@ -33,4 +33,19 @@ __attribute__((visibility("hidden"))) cudaError_t enqueue_job_init(uint8_t *spin
 
 inline int slots_of(int TH) { return 2 * TW + 2 * TH; }
 
+// A q-state Potts lattice on the periodic d-dimensional torus (sw_potts.cu):
+// N = L^d sites; size is null unless cluster sizes are summed.
+struct PottsDev {
+    int32_t dim, L, q;
+    int64_t N;
+    uint64_t thr, seed;
+    uint8_t *spin, *bond;
+    int32_t *label, *size;
+};
+__attribute__((visibility("hidden"))) cudaError_t potts_enqueue_hot_start(const PottsDev &p, cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t potts_enqueue_sweep(const PottsDev &p, uint64_t sweep, DevObs *obs,
+                                                                      cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t potts_enqueue_check(const uint8_t *s, int64_t n, int q, int32_t *bad,
+                                                                      cudaStream_t st);
+
 }  // namespace swg

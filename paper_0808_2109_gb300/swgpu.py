@@ -44,6 +44,8 @@ class SwState(ctypes.Structure):
         ("threshold", ctypes.c_uint64),
         ("open", ctypes.c_int32),
         ("tile_h", ctypes.c_int32),
+        ("dim", ctypes.c_int32),
+        ("q", ctypes.c_int32),
     ]
 
 
@@ -136,6 +138,7 @@ SIGNATURES = {
     "sw_create": ([_P, _i32, _dbl, _dbl, _u64, _u32], ctypes.c_int),
     "sw_create_p": ([_P, _i32, _dbl, _u64, _u32], ctypes.c_int),
     "pcc_create": ([_P, _i32, _u64, _u32], ctypes.c_int),
+    "sw_create_potts": ([_P, _i32, _i32, _i32, _dbl, _dbl, _u64, _u32], ctypes.c_int),
     "sw_destroy": ([_P], ctypes.c_int),
     "sw_set_stream": ([_P, _P], ctypes.c_int),
     "sw_sweep": ([_P, _i32], ctypes.c_int),
@@ -224,6 +227,12 @@ def pcc_create(L: int, seed: int, flags: int = 0) -> ctypes.c_void_p:
     return h
 
 
+def sw_create_potts(dim: int, L: int, q: int, J: float, T: float, seed: int, flags: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().sw_create_potts(ctypes.byref(h), dim, L, q, J, T, seed, flags), "sw_create_potts")
+    return h
+
+
 def sw_destroy(h) -> None:
     _check(lib().sw_destroy(h), "sw_destroy")
 
@@ -277,7 +286,8 @@ def sw_get_state(h) -> dict:
     st = SwState()
     _check(lib().sw_get_state(h, ctypes.byref(st)), "sw_get_state")
     return {"L": st.L, "pcc": bool(st.pcc), "seed": st.seed, "sweep": st.sweep,
-            "threshold": st.threshold, "open": bool(st.open), "tile_h": st.tile_h}
+            "threshold": st.threshold, "open": bool(st.open), "tile_h": st.tile_h,
+            "dim": st.dim, "q": st.q}
 
 
 def sw_sync(h) -> None:
@@ -421,6 +431,62 @@ class Lattice:
 
     def profile_read(self) -> dict:
         return sw_profile_read(self.h)
+
+
+class PottsLattice:
+    """A q-state Potts lattice on the periodic d-dimensional torus (d = 2, 3)."""
+
+    def __init__(self, dim: int, L: int, q: int, *, J: float = 1.0, T: float, seed: int = 1,
+                 csize: bool = False):
+        self.dim, self.L, self.q = int(dim), int(L), int(q)
+        self.N = self.L ** self.dim
+        self.h = sw_create_potts(self.dim, self.L, self.q, J, T, seed, SW_FLAG_CSIZE if csize else 0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sweep(self, n: int):
+        sw_sweep(self.h, n)
+
+    def observables(self, max_entries: int = 1 << 20) -> np.ndarray:
+        return sw_observables(self.h, max_entries)
+
+    def _get(self, fn, dtype):
+        out = np.empty(self.N, dtype=dtype)
+        _check(getattr(lib(), fn)(self.h, _ptr(out)), fn)
+        return out
+
+    def spins(self) -> np.ndarray:
+        return self._get("sw_get_spins", np.uint8)
+
+    def labels(self) -> np.ndarray:
+        return self._get("sw_get_labels", np.int32)
+
+    def bonds(self) -> np.ndarray:
+        return self._get("sw_get_bonds", np.uint8)
+
+    def set_spins(self, spins: np.ndarray):
+        sw_set_spins(self.h, spins)
+
+    def state(self) -> dict:
+        return sw_get_state(self.h)
+
+    def sync(self):
+        sw_sync(self.h)
 
 
 class Server:
