@@ -37,11 +37,15 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int GROUPS_PER_STEP = 16;   // launch groups between admissions
-constexpr int N_LANES = 4;            // tile heights 32, 64, 96, 128
+// Lanes: one per tile height (32, 64, 96, 128) for plain lattices and one
+// per height for lattices that need a kernel feature (PCC, open boundaries,
+// cluster sizes, the topological rule), so plain lattices keep the plain
+// kernels whatever else is being served.
+constexpr int N_LANES = 8;
 constexpr int32_t SERVER_MAX_L = 4096;
 
 int lane_of_th(int th) { return th == 32 ? 0 : th == 64 ? 1 : th == 96 ? 2 : 3; }
-int th_of_lane(int l) { return l == 0 ? 32 : l == 1 ? 64 : l == 2 ? 96 : 128; }
+int th_of_lane(int l) { return (l & 3) == 0 ? 32 : (l & 3) == 1 ? 64 : (l & 3) == 2 ? 96 : 128; }
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -489,8 +493,8 @@ void worker_main(sw_server *s)
             s->stats.pending = (int64_t)s->pending.size();
         }
         for (Job *j : admit) {
-            Lane &ln = s->lanes[lane_of_th(j->TH)];
-            j->lane = lane_of_th(j->TH);
+            j->lane = lane_of_th(j->TH) + ((j->pcc || j->spec.flags) ? 4 : 0);
+            Lane &ln = s->lanes[j->lane];
             j->t_admit = Clock::now();
             j->jstart = s->launch_index;
             int rc = SW_OK;
