@@ -221,6 +221,34 @@ int sw_profile(sw_ctx *ctx, int32_t enable);
 /* Synchronise, return the accumulated kernel times and reset them. */
 int sw_profile_read(sw_ctx *ctx, sw_kernel_stats *out);
 
+/* ---------------------------------------------------- checkpoint / resume
+ * (The paper has no counterpart.)  A lattice's state is its spins, seed,
+ * sweep counter and threshold (plus its kind: PCC, open boundaries, the
+ * topological rule, d and q); labels and bonds are rebuilt by the next
+ * sweep.  Because every random number is a counter-based Philox draw, a chain
+ * saved after n sweeps and resumed for m more equals a straight run of n + m
+ * sweeps bit for bit. */
+
+/* Size in bytes of a checkpoint of this lattice (a header and L^d bytes). */
+int sw_checkpoint_bytes(sw_ctx *ctx, uint64_t *bytes);
+
+/* Write the state into the caller's host buffer (at least
+ * sw_checkpoint_bytes); waits for the sweeps queued on the context. */
+int sw_save(sw_ctx *ctx, void *host_buf, uint64_t bytes);
+
+/* Replace the context's state by a saved one.  The context must be of the same
+ * kind, L, d and q (its seed may differ: the saved seed is taken); else
+ * SW_ERR_ARG, as for a corrupt buffer or out-of-range states.  sw_get_labels
+ * and sw_get_bonds answer SW_ERR_STATE until the next sweep. */
+int sw_load(sw_ctx *ctx, const void *host_buf, uint64_t bytes);
+
+/* Fault injection for tests (host side; the paper has no counterpart): of
+ * the library's next device allocations, the first `skip` proceed and the n
+ * after them report out-of-memory without allocating, so callers see
+ * SW_ERR_NOMEM (contexts) or a job result with that status (servers).
+ * n = 0 switches it off. */
+int sw_debug_fail_allocations(int32_t skip, int32_t n);
+
 /* ------------------------------------------------- batched and served runs
  * Many independent lattices on one GPU at once (the paper's decompositions
  * spread ONE lattice over processors, Sec. II; here independent lattices

@@ -7,8 +7,10 @@
 #include "sw_launch.cuh"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -178,15 +180,30 @@ int pick_tile_height(int L, uint32_t flags)
     return 96;
 }
 
+std::atomic<int> g_alloc_skip{0}, g_alloc_failures{0};   // sw_debug_fail_allocations
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t count)
 {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (sw_inject_alloc_failure()) return cudaErrorMemoryAllocation;
     return cudaMalloc((void **)p, count * sizeof(T));
 }
 
 }  // namespace
+
+bool sw_inject_alloc_failure()
+{
+    if (g_alloc_failures.load() <= 0) return false;
+    int s = g_alloc_skip.load();
+    while (s > 0)
+        if (g_alloc_skip.compare_exchange_weak(s, s - 1)) return false;   // this one still succeeds
+    int n = g_alloc_failures.load();
+    while (n > 0)
+        if (g_alloc_failures.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
 
 std::mutex &sw_capture_mutex()
 {
@@ -397,6 +414,12 @@ int ctx_features(const sw_ctx *c)
     return (c->psize ? FEAT_CSIZE : 0) | (c->open ? FEAT_OPEN : 0) | (c->wind ? FEAT_WIND : 0);
 }
 
+// An NVTX range for tracing tools (free when none is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 int ensure_obs(sw_ctx *c, int64_t n)
 {
     if (c->obs_head == c->obs_tail) c->obs_head = c->obs_tail = 0;
@@ -496,6 +519,7 @@ int run_sweeps(sw_ctx *c, int32_t n)
 {
     if (n < 0) return SW_ERR_ARG;
     if (n == 0) return SW_OK;
+    NvtxRange range(c->is_potts ? "sw_sweep (Potts)" : c->pcc ? "pcc_step" : "sw_sweep");
     SW_CUDA(cudaSetDevice(c->dev));
     cudaGetLastError();   // a stale error of an unrelated earlier call is not ours
     int rc = ensure_obs(c, n);
@@ -867,6 +891,79 @@ int sw_sync(sw_ctx *ctx)
     if (!ctx) return SW_ERR_ARG;
     SW_CUDA(cudaSetDevice(ctx->dev));
     SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SW_OK;
+}
+
+// ---- checkpoint / resume: a header, then the spins (one byte a site)
+namespace {
+constexpr uint64_t CKPT_MAGIC = 0x3130504b43575353ull;   // "SSWCKP01"
+struct CkptHeader {
+    uint64_t magic;
+    int32_t L, dim, q, kind;   // kind bits: 1 PCC, 2 open, 4 winding
+    uint64_t seed, sweep, threshold, nsites;
+};
+int ctx_kind(const sw_ctx *c) { return (c->pcc ? 1 : 0) | (c->open ? 2 : 0) | (c->wind ? 4 : 0); }
+}  // namespace
+
+int sw_checkpoint_bytes(sw_ctx *ctx, uint64_t *bytes)
+{
+    if (!ctx || !bytes) return SW_ERR_ARG;
+    *bytes = sizeof(CkptHeader) + (uint64_t)ctx->nsites;
+    return SW_OK;
+}
+
+int sw_save(sw_ctx *ctx, void *host_buf, uint64_t bytes)
+{
+    if (!ctx || !host_buf || bytes < sizeof(CkptHeader) + (uint64_t)ctx->nsites) return SW_ERR_ARG;
+    sw_state st{};
+    int rc = sw_get_state(ctx, &st);   // waits for the queued sweeps
+    if (rc != SW_OK) return rc;
+    CkptHeader h{};
+    h.magic = CKPT_MAGIC;
+    h.L = ctx->L;
+    h.dim = st.dim;
+    h.q = st.q;
+    h.kind = ctx_kind(ctx);
+    h.seed = ctx->seed;
+    h.sweep = ctx->sweep;
+    h.threshold = st.threshold;
+    h.nsites = (uint64_t)ctx->nsites;
+    std::memcpy(host_buf, &h, sizeof(h));
+    return sw_get_spins(ctx, static_cast<uint8_t *>(host_buf) + sizeof(h));
+}
+
+int sw_load(sw_ctx *ctx, const void *host_buf, uint64_t bytes)
+{
+    if (!ctx || !host_buf || bytes < sizeof(CkptHeader)) return SW_ERR_ARG;
+    CkptHeader h;
+    std::memcpy(&h, host_buf, sizeof(h));
+    const int dim = ctx->is_potts ? ctx->pd.dim : 2, q = ctx->is_potts ? ctx->pd.q : 2;
+    if (h.magic != CKPT_MAGIC || h.L != ctx->L || h.dim != dim || h.q != q || h.kind != ctx_kind(ctx) ||
+        h.nsites != (uint64_t)ctx->nsites || bytes < sizeof(h) + h.nsites || h.threshold > ((uint64_t)1 << 32))
+        return SW_ERR_ARG;
+    int rc = sw_set_spins(ctx, static_cast<const uint8_t *>(host_buf) + sizeof(h));   // checks every state
+    if (rc != SW_OK) return rc;
+    ctx->seed = h.seed;
+    ctx->sweep = h.sweep;
+    ctx->thr = h.threshold;
+    ctx->rep.key0 = (uint32_t)h.seed;
+    ctx->rep.key1 = (uint32_t)(h.seed >> 32);
+    ctx->pd.seed = h.seed;
+    ctx->pd.thr = h.threshold;
+    if (ctx->pcc) {
+        SW_CUDA(cudaMemcpyAsync(ctx->thr_dev, &h.threshold, sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+        SW_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->swept = false;   // labels and bonds come back with the next sweep
+    return SW_OK;
+}
+
+int sw_debug_fail_allocations(int32_t skip, int32_t n)
+{
+    if (skip < 0 || n < 0) return SW_ERR_ARG;
+    g_alloc_failures.store(0);
+    g_alloc_skip.store(skip);
+    g_alloc_failures.store(n);
     return SW_OK;
 }
 

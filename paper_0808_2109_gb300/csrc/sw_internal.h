@@ -20,4 +20,9 @@ __attribute__((visibility("hidden"))) int sw_threshold_p_internal(double p, uint
 // synchronising calls (cudaMalloc, cudaFree): such a call made by another
 // host thread in the middle of a capture invalidates it.
 __attribute__((visibility("hidden"))) std::mutex &sw_capture_mutex();
+
+// Fault injection for tests (sw_debug_fail_allocations): true while injected
+// allocation failures remain, consuming one.  Every device allocation of the
+// library asks first and reports cudaErrorMemoryAllocation instead.
+__attribute__((visibility("hidden"))) bool sw_inject_alloc_failure();
 #endif

@@ -17,6 +17,7 @@
 #include "sw_launch.cuh"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -185,7 +186,7 @@ cudaError_t job_alloc(Job *j, cudaStream_t st)
     const bool csz = (j->spec.flags & SW_FLAG_CSIZE) != 0;
     const bool wnd = (j->spec.flags & SW_FLAG_WIND) != 0;
     const JobLayout o = job_layout(j->spec.L, j->TH, j->spec.nsweeps, j->pcc, csz, wnd);
-    cudaError_t e = cudaMallocAsync(&j->block, o.total, st);
+    cudaError_t e = sw_inject_alloc_failure() ? cudaErrorMemoryAllocation : cudaMallocAsync(&j->block, o.total, st);
     if (e != cudaSuccess) {
         j->block = nullptr;
         return e;
@@ -531,6 +532,7 @@ void worker_main(sw_server *s)
             s->stats.admitted += 1;
         }
         // ---- one step of every busy lane
+        nvtxRangePushA("server step");
         bool any = false;
         for (Lane &ln : s->lanes) {
             if (ln.active == 0) continue;
@@ -561,10 +563,14 @@ void worker_main(sw_server *s)
             cudaMemcpyAsync(ln.jbase_dev, &jb, sizeof(int32_t), cudaMemcpyHostToDevice, ln.stream);
             if (ln.graph) cudaGraphLaunch(ln.graph, ln.stream);
         }
-        if (!any) continue;
+        if (!any) {
+            nvtxRangePop();
+            continue;
+        }
         s->launch_index += GROUPS_PER_STEP;
         for (Lane &ln : s->lanes)
             if (ln.active) cudaStreamSynchronize(ln.stream);
+        nvtxRangePop();
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->stats.launches += GROUPS_PER_STEP;

@@ -139,6 +139,10 @@ SIGNATURES = {
     "sw_create_p": ([_P, _i32, _dbl, _u64, _u32], ctypes.c_int),
     "pcc_create": ([_P, _i32, _u64, _u32], ctypes.c_int),
     "sw_create_potts": ([_P, _i32, _i32, _i32, _dbl, _dbl, _u64, _u32], ctypes.c_int),
+    "sw_checkpoint_bytes": ([_P, _P], ctypes.c_int),
+    "sw_save": ([_P, _P, _u64], ctypes.c_int),
+    "sw_load": ([_P, _P, _u64], ctypes.c_int),
+    "sw_debug_fail_allocations": ([_i32, _i32], ctypes.c_int),
     "sw_destroy": ([_P], ctypes.c_int),
     "sw_set_stream": ([_P, _P], ctypes.c_int),
     "sw_sweep": ([_P, _i32], ctypes.c_int),
@@ -231,6 +235,23 @@ def sw_create_potts(dim: int, L: int, q: int, J: float, T: float, seed: int, fla
     h = ctypes.c_void_p()
     _check(lib().sw_create_potts(ctypes.byref(h), dim, L, q, J, T, seed, flags), "sw_create_potts")
     return h
+
+
+def sw_save(h) -> bytes:
+    n = ctypes.c_uint64()
+    _check(lib().sw_checkpoint_bytes(h, ctypes.byref(n)), "sw_checkpoint_bytes")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().sw_save(h, buf, n.value), "sw_save")
+    return buf.raw
+
+
+def sw_load(h, data: bytes) -> None:
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(lib().sw_load(h, buf, len(data)), "sw_load")
+
+
+def sw_debug_fail_allocations(n: int, skip: int = 0) -> None:
+    _check(lib().sw_debug_fail_allocations(skip, n), "sw_debug_fail_allocations")
 
 
 def sw_destroy(h) -> None:
@@ -420,6 +441,12 @@ class Lattice:
     def state(self) -> dict:
         return sw_get_state(self.h)
 
+    def save(self) -> bytes:
+        return sw_save(self.h)
+
+    def load(self, data: bytes):
+        sw_load(self.h, data)
+
     def set_stream(self, stream):
         sw_set_stream(self.h, stream)
 
@@ -484,6 +511,12 @@ class PottsLattice:
 
     def state(self) -> dict:
         return sw_get_state(self.h)
+
+    def save(self) -> bytes:
+        return sw_save(self.h)
+
+    def load(self, data: bytes):
+        sw_load(self.h, data)
 
     def sync(self):
         sw_sync(self.h)
