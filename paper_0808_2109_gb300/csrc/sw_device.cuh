@@ -356,11 +356,9 @@ __device__ void tile_label(volatile int *par, const uint32_t (*H)[TWW], const ui
         const uint32_t v = (row_ok && lane < 31) ? V[y][sx] : 0u;
         const uint32_t u = v & (~(v << 1) | heads | heads_below);
         const int base = y * PW + 32 * sx;
-        if (row_ok) {
-            for (uint32_t b = heads; b; b &= b - 1) {
-                const int x = __ffs(b) - 1;
-                par[base + x] = base + x;
-            }
+        if (row_ok) {   // every site of the row its own root (only run heads are used)
+#pragma unroll
+            for (int x = 0; x < 32; ++x) par[base + x] = base + x;
         }
         __syncwarp();
         for (uint32_t b = u; b; b &= b - 1) {
@@ -861,7 +859,10 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
                 p = sm.par[x];
             }
             if (x != hd) {
-                sm.par[hd] = x;
+                // the root's record itself where it is already there (codes
+                // then need one load); the root otherwise.  Cluster sizes add
+                // at roots, so the feature variant keeps root indices.
+                sm.par[hd] = (!(F & FEAT_CSIZE) && (uint32_t)p >= INFO_INTERIOR && p != x) ? p : x;
             } else if (p == hd && 32 * c + hx < t.tw) {
                 // an interior root inside the tile
                 const uint32_t rowg = gbase + (uint32_t)y * uL;
