@@ -684,11 +684,18 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     const uint32_t tm1 = (uint32_t)(thr - 1);     // t in [1, 2^32] -> t - 1 fits 32 bits
     // the bonds of row y from its two horizontal-and-vertical draw words per
     // 32-site word (rh, rv): keep the links whose spins agree, store them
-    auto store_row = [&](int y, const uint32_t (&rh)[TWW], const uint32_t (&rv)[TWW]) {
-        if (lane < TWW) {
-            const int c = lane;
-            const uint32_t rhc = c == 0 ? rh[0] : c == 1 ? rh[1] : c == 2 ? rh[2] : rh[3];
-            const uint32_t rvc = c == 0 ? rv[0] : c == 1 ? rv[1] : c == 2 ? rv[2] : rv[3];
+    // rows yA and yB at once: lane c < 4 takes word c of row yA, lane 4 + c
+    // word c of row yB (skipped when yB is past the tile)
+    auto store_rows = [&](int yA, const uint32_t (&rhA)[TWW], const uint32_t (&rvA)[TWW], int yB,
+                          const uint32_t (&rhB)[TWW], const uint32_t (&rvB)[TWW]) {
+        const bool second = lane >= TWW;
+        const int y = second ? yB : yA;
+        if (lane < 2 * TWW && y < t.th) {
+            const int c = lane & (TWW - 1);
+            const uint32_t rhc = second ? (c == 0 ? rhB[0] : c == 1 ? rhB[1] : c == 2 ? rhB[2] : rhB[3])
+                                        : (c == 0 ? rhA[0] : c == 1 ? rhA[1] : c == 2 ? rhA[2] : rhA[3]);
+            const uint32_t rvc = second ? (c == 0 ? rvB[0] : c == 1 ? rvB[1] : c == 2 ? rvB[2] : rvB[3])
+                                        : (c == 0 ? rvA[0] : c == 1 ? rvA[1] : c == 2 ? rvA[2] : rvA[3]);
             const uint32_t vm = valid_mask(c, t.tw);
             const uint32_t vr = open_r ? valid_mask(c, t.tw - 1) : vm;
             const uint32_t vd = (open_b && y == t.th - 1) ? 0u : vm;
@@ -704,6 +711,9 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             sm.ih[y][c] = h & valid_mask(c, t.tw - 1);
             sm.iv[y][c] = (y < t.th - 1) ? v : 0u;
         }
+    };
+    auto store_row = [&](int y, const uint32_t (&rh)[TWW], const uint32_t (&rv)[TWW]) {
+        store_rows(y, rh, rv, t.th, rh, rv);
     };
     // aligned row: lane l drew the blocks of sites (2l, 2l+1) (r0) and
     // (64+2l, 65+2l) (r1); lane x of each 32-site word fetches its two bits
@@ -732,13 +742,10 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             const U4 r1 = philox4x32_10(b0 + 32, klo, khi, STREAM_BOND, R.key0, R.key1);
             const U4 r2 = philox4x32_10(b2, klo, khi, STREAM_BOND, R.key0, R.key1);
             const U4 r3 = philox4x32_10(b2 + 32, klo, khi, STREAM_BOND, R.key0, R.key1);
-            uint32_t rh[TWW], rv[TWW];
+            uint32_t rh[TWW], rv[TWW], rh2[TWW], rv2[TWW];
             draws_aligned(r0, r1, rh, rv);
-            store_row(y, rh, rv);
-            if (y2 < t.th) {
-                draws_aligned(r2, r3, rh, rv);
-                store_row(y2, rh, rv);
-            }
+            draws_aligned(r2, r3, rh2, rv2);
+            store_rows(y, rh, rv, y2, rh2, rv2);
         }
     } else {
         for (int y = warp; y < t.th; y += NW) {
@@ -864,12 +871,12 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
                 // at roots, so the feature variant keeps root indices.
                 sm.par[hd] = (!(F & FEAT_CSIZE) && (uint32_t)p >= INFO_INTERIOR && p != x) ? p : x;
             } else if (p == hd && 32 * c + hx < t.tw) {
-                // an interior root inside the tile
-                const uint32_t rowg = gbase + (uint32_t)y * uL;
-                const uint32_t gv = rowg + (uint32_t)(32 * c + hx);
-                const int b = (int)((gv >> 7) - (rowg >> 7));
-                const int bit = (int)(gv & 127);
-                const uint32_t spin = (sm.spb[y][4 * b + (bit >> 5)] >> (bit & 31)) & 1u;
+                // an interior root inside the tile: bit (g mod 128) of block
+                // g / 128 for its global index g; the row's two blocks start
+                // at the one holding the row's first site, so the bit sits
+                // at position (row start mod 128) + x of spb[y]
+                const uint32_t pos = ((gbase + (uint32_t)y * uL) & 127u) + (uint32_t)(32 * c + hx);
+                const uint32_t spin = (sm.spb[y][pos >> 5] >> (pos & 31)) & 1u;
                 sm.par[hd] = (int)(INFO_INTERIOR | (spin << 14) | (uint32_t)(y * TW + 32 * c + hx));
                 ++ncl_interior;
             }
