@@ -264,6 +264,22 @@ __device__ __forceinline__ int sfind(volatile int *par, int x)
     return x;
 }
 
+// As sunite, returning the root of the united set.
+__device__ __forceinline__ int sunite_root(volatile int *par, int a, int b)
+{
+    for (;;) {
+        a = sfind(par, a);
+        b = sfind(par, b);
+        if (a == b) return a;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS((int *)&par[b], b, a) == b) return a;
+    }
+}
+
 __device__ __forceinline__ void sunite(volatile int *par, int a, int b)
 {
     for (;;) {
@@ -361,9 +377,16 @@ __device__ void tile_label(volatile int *par, const uint32_t (*H)[TWW], const ui
             for (int x = 0; x < 32; ++x) par[base + x] = base + x;
         }
         __syncwarp();
+        // consecutive contacts often share a run above or below: their
+        // finds start at the last union's root (an ancestor of that run's
+        // head), not at the head
+        int prev_a = -1, prev_b = -1, prev_r = 0;
         for (uint32_t b = u; b; b &= b - 1) {
             const int x = __ffs(b) - 1;
-            sunite(par, head_of(heads, base, x), head_of(heads_below, base + PW, x));
+            const int ha = head_of(heads, base, x), hb = head_of(heads_below, base + PW, x);
+            prev_r = sunite_root(par, ha == prev_a ? prev_r : ha, hb == prev_b ? prev_r : hb);
+            prev_a = ha;
+            prev_b = hb;
         }
     }
     __syncthreads();
