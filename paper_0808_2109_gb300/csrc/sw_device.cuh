@@ -1146,22 +1146,36 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_union(const SweepArg
     const Tile t = tile_of(R, blockIdx.x, TH);
     const uint32_t *cross = R.cross + (size_t)t.lt * CROSS_WORDS;
     int na[MC::EPT], nb[MC::EPT];
+    bool prev[MC::EPT];   // the link before it along the edge is bonded too
 #pragma unroll
     for (int q = 0; q < MC::EPT; ++q) {
         const int e = threadIdx.x + q * MC::MT;
         na[q] = -1;
+        prev[q] = false;
         if (e < TH) {
             if (e < t.th && ((cross[e >> 5] >> (e & 31)) & 1u)) {
                 na[q] = t.lt * S + SL::RIGHT + e;
                 nb[q] = t.g_right * S + SL::LEFT + e;
+                prev[q] = e > 0 && ((cross[(e - 1) >> 5] >> ((e - 1) & 31)) & 1u);
             }
         } else if (e < TH + TW) {
             const int x = e - TH;
             if (x < t.tw && ((cross[TWW + (x >> 5)] >> (x & 31)) & 1u)) {
                 na[q] = t.lt * S + SL::BOTTOM + x;
                 nb[q] = t.g_down * S + SL::TOP + x;
+                prev[q] = x > 0 && ((cross[TWW + ((x - 1) >> 5)] >> ((x - 1) & 31)) & 1u);
             }
         }
+    }
+    // A link whose two ends lie in the same two pieces as the bonded link just
+    // before it along the edge joins nothing new (pieces are known by their
+    // keys, which no union changes): skip it.
+#pragma unroll
+    for (int q = 0; q < MC::EPT; ++q) {
+        if (!prev[q]) continue;
+        const uint32_t ka = (uint32_t)R.nkey[na[q]] ^ (uint32_t)R.nkey[na[q] - 1];
+        const uint32_t kb = (uint32_t)R.nkey[nb[q]] ^ (uint32_t)R.nkey[nb[q] - 1];
+        if (((ka | kb) & KEY_MASK) == 0) na[q] = -1;
     }
     const bool wind = W && (R.flags & RF_WIND);
 #pragma unroll
