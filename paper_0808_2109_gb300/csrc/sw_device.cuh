@@ -306,7 +306,7 @@ struct TileCfg {
     // rows: five, 51; 96 rows: three, 56; 128 rows: two, 64).  The kernel is
     // latency-bound in its union-find, so resident warps pay: five 64-row
     // CTAs run 12% faster than four.
-    static constexpr int MINB = TH == 32 ? 10 : TH == 64 ? 5 : TH == 96 ? 3 : 2;
+    static constexpr int MINB = TH == 32 ? 11 : TH == 64 ? 6 : TH == 96 ? 4 : 3;
 };
 
 // Root of x without writing (a forest no thread is changing any more).
@@ -343,8 +343,8 @@ __device__ __forceinline__ int head_of(uint32_t heads, int base, int x)
     return base + 31 - __clz(heads & (0xFFFFFFFFu >> (31 - x)));
 }
 
-// Connected components of the intra-tile bonds (H: right links, with the
-// link leaving the tile's last column cleared; V: down links, zero in the
+// Connected components of the intra-tile bonds (H: right links, whose link
+// leaving the tile's last column is ignored; V: down links, ignored in the
 // tile's last row).  The tile is cut into 32 x 32 sub-tiles, one per warp,
 // and the forest lives on run heads only (a run = maximal chain of right
 // bonds inside one sub-tile row; its head is its leftmost site):
@@ -358,20 +358,24 @@ __device__ __forceinline__ int head_of(uint32_t heads, int base, int x)
 // site.  Forest indices are padded, y * PW + x, which keeps row-major order
 // and puts the rows of a column on distinct shared-memory banks.
 template <int TH>
-__device__ void tile_label(volatile int *par, const uint32_t (*H)[TWW], const uint32_t (*V)[TWW],
-                           int th)
+__device__ void tile_label(volatile int *par, const uint32_t (*Hb)[TWW], const uint32_t (*Vb)[TWW],
+                           int th, int tw)
 {
     constexpr int NT = TileCfg<TH>::NT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sx = warp & (TWW - 1), sy = warp / TWW;
+    // the intra-tile bonds: the tile's last column has no right link inside,
+    // its last row no down link inside
+    auto H = [&](int y, int c) { return Hb[y][c] & valid_mask(c, tw - 1); };
+    auto V = [&](int y, int c) { return y < th - 1 ? Vb[y][c] : 0u; };
 
     // ---- 1. inside each sub-tile, lane = row
     {
         const int y = 32 * sy + lane;
         const bool row_ok = y < th;
-        const uint32_t heads = run_heads(row_ok ? H[y][sx] : 0u);
+        const uint32_t heads = run_heads(row_ok ? H(y, sx) : 0u);
         const uint32_t heads_below = __shfl_down_sync(0xFFFFFFFFu, heads, 1);
-        const uint32_t v = (row_ok && lane < 31) ? V[y][sx] : 0u;
+        const uint32_t v = (row_ok && lane < 31) ? V(y, sx) : 0u;
         const uint32_t u = v & (~(v << 1) | heads | heads_below);
         const int base = y * PW + 32 * sx;
         if (row_ok) {   // every site of the row its own root (only run heads are used)
@@ -402,30 +406,30 @@ __device__ void tile_label(volatile int *par, const uint32_t (*H)[TWW], const ui
             int a, b;
             if (q < NV) {
                 const int bnd = q / TH + 1, y = q % TH;     // link (32 bnd - 1, y) - (32 bnd, y)
-                if (y >= th || !((H[y][bnd - 1] >> 31) & 1u)) continue;
+                if (y >= th || !((H(y, bnd - 1) >> 31) & 1u)) continue;
                 // skip when the row above already joins the same two sites
                 // through down links inside the sub-tiles (united in phase 1;
                 // at a sub-tile row edge those down links are phase-2 links
                 // themselves and could justify each other in a cycle)
-                if ((y & 31) != 0 && ((H[y - 1][bnd - 1] >> 31) & 1u) &&
-                    ((V[y - 1][bnd - 1] >> 31) & 1u) && (V[y - 1][bnd] & 1u))
+                if ((y & 31) != 0 && ((H(y - 1, bnd - 1) >> 31) & 1u) &&
+                    ((V(y - 1, bnd - 1) >> 31) & 1u) && (V(y - 1, bnd) & 1u))
                     continue;
-                a = head_of(run_heads(H[y][bnd - 1]), y * PW + 32 * (bnd - 1), 31);
+                a = head_of(run_heads(H(y, bnd - 1)), y * PW + 32 * (bnd - 1), 31);
                 b = y * PW + 32 * bnd;   // column 0 of a sub-tile row is always a head
             } else {
                 const int r = q - NV;
                 const int bnd = r / TW + 1, x = r % TW;     // link (x, 32 bnd - 1) - (x, 32 bnd)
                 const int y = 32 * bnd - 1;
-                if (y + 1 >= th || !((V[y][x >> 5] >> (x & 31)) & 1u)) continue;
+                if (y + 1 >= th || !((V(y, x >> 5) >> (x & 31)) & 1u)) continue;
                 // skip when the column to the left already joins the same two
                 // sites through right links inside the sub-tiles
-                if ((x & 31) != 0 && ((V[y][(x - 1) >> 5] >> ((x - 1) & 31)) & 1u) &&
-                    ((H[y][(x - 1) >> 5] >> ((x - 1) & 31)) & 1u) &&
-                    ((H[y + 1][(x - 1) >> 5] >> ((x - 1) & 31)) & 1u))
+                if ((x & 31) != 0 && ((V(y, (x - 1) >> 5) >> ((x - 1) & 31)) & 1u) &&
+                    ((H(y, (x - 1) >> 5) >> ((x - 1) & 31)) & 1u) &&
+                    ((H(y + 1, (x - 1) >> 5) >> ((x - 1) & 31)) & 1u))
                     continue;
                 const int c = x >> 5;
-                a = head_of(run_heads(H[y][c]), y * PW + 32 * c, x & 31);
-                b = head_of(run_heads(H[y + 1][c]), (y + 1) * PW + 32 * c, x & 31);
+                a = head_of(run_heads(H(y, c)), y * PW + 32 * c, x & 31);
+                b = head_of(run_heads(H(y + 1, c)), (y + 1) * PW + 32 * c, x & 31);
             }
             sunite(par, a, b);
         }
@@ -501,14 +505,16 @@ __device__ __forceinline__ void block_sum_atomic(long long (&v)[K], unsigned lon
 template <int TH>
 struct TileSmem {
     int par[TH * PW];               // union-find forest over run heads (padded rows)
-    uint32_t sp[TH + 1][TWW + 1];   // spins as bits, row TH = halo row, bit tw = halo column
+    uint32_t sp[TH + 1][TWW];       // spins as bits, row TH = halo row; in a tile narrower
+                                    // than TW, bit tw of a row = the halo column
+    uint32_t spx[TH / 32];          // halo column of a full-width tile: bit y = row y
     uint32_t bh[TH][TWW];           // right-link bonds (bit x: link (x,y)-(x+1,y))
     uint32_t bv[TH][TWW];           // down-link bonds
-    uint32_t ih[TH][TWW];           // intra-tile right bonds
-    uint32_t iv[TH][TWW];           // intra-tile down bonds
-    uint32_t spb[TH][8];            // SPIN-stream blocks covering each row
-    uint32_t finfo[Slots<TH>::S];   // resolved finals of the tile's own nodes
-    long long red[TileCfg<TH>::NW][4];
+    union {                         // never live at the same time:
+        uint32_t finfo[Slots<TH>::S];        // finish half: finals of the tile's own nodes
+        uint32_t spb[TH][TWW];               // start half: SPIN-stream bit of each site
+        long long red[TileCfg<TH>::NW][4];   // the reduction that ends each half
+    } u;
     uint32_t pm[Slots<TH>::S][8];   // PCC: per border piece, columns and rows it occupies
 };
 
@@ -566,6 +572,18 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     const uint32_t uL = (uint32_t)L;
     const uint32_t gbase = (uint32_t)t.y0 * uL + (uint32_t)t.x0;   // global index of local site 0
     uint16_t *code = R.code + (size_t)t.lt * TH * TW;
+    // the intra-tile right bonds of word (y, c): the tile's last column links out
+    auto ih_of = [&](int y, int c) { return sm.bh[y][c] & valid_mask(c, t.tw - 1); };
+    // the spin word right of word (y, c), of which only bit 0 is used: the next
+    // word of the row, or the halo column of a full-width tile
+    auto right_of = [&](int y, int c) { return c + 1 < TWW ? sm.sp[y][c + 1] : sm.spx[y >> 5] >> (y & 31); };
+    // sets the halo-column spin of row y (the spin right of the tile's last column)
+    auto set_halo = [&](int y) {
+        if (t.tw == TW)
+            atomicOr(&sm.spx[y >> 5], 1u << (y & 31));
+        else
+            sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
+    };
 
     if (fin) {
         // ---- finish sweep k-1: resolve every site's cluster and flip it
@@ -579,8 +597,8 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             const int idx = tid + q * NT;
             cv[q] = ((idx * 8) / TW < t.th) ? code4[idx] : make_uint4(0u, 0u, 0u, 0u);
         }
-        for (int s = tid; s < S; s += NT) sm.finfo[s] = R.nfinal[(size_t)t.lt * S + s];
-        for (int y = tid; y < t.th; y += NT) sm.sp[y][TWW] = 0u;
+        for (int s = tid; s < S; s += NT) sm.u.finfo[s] = R.nfinal[(size_t)t.lt * S + s];
+        for (int w = tid; w < TH / 32; w += NT) sm.spx[w] = 0u;
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -593,7 +611,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             for (int e = 0; e < 8; ++e) {
                 const uint32_t u = (wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
                 const uint32_t spin =
-                    (u & CODE_BORDER) ? (sm.finfo[u & 0x3FFu] >> 30) & 1u : (u >> 14) & 1u;
+                    (u & CODE_BORDER) ? (sm.u.finfo[u & 0x3FFu] >> 30) & 1u : (u >> 14) & 1u;
                 bits |= spin << e;
             }
             bits &= (1u << min(8, max(0, t.tw - xb))) - 1u;   // sites past tw are not spins
@@ -605,7 +623,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
                 for (int e = 0; e < 8; ++e) {
                     const uint32_t u = (wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
                     const uint32_t lr = u & CODE_ROOT;
-                    roots[e] = (u & CODE_BORDER) ? sm.finfo[u & 0x3FFu] & ROOT_MASK
+                    roots[e] = (u & CODE_BORDER) ? sm.u.finfo[u & 0x3FFu] & ROOT_MASK
                                                  : gbase + (lr / TW) * uL + (lr % TW);
                 }
                 const int nval = min(8, t.tw - xb);
@@ -626,7 +644,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             }
         }
         // bottom halo row: new spins of the top row of the tile below
-        for (int w = warp; w < TWW + 1; w += NW) {
+        for (int w = warp; w < TWW; w += NW) {
             const int x = 32 * w + lane;
             int spin = 0;
             if (x < t.tw) spin = (node_final(R, (size_t)t.g_down * S + SL::TOP + x) & FINAL_SPIN) ? 1 : 0;
@@ -636,8 +654,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         __syncthreads();
         // right halo column: new spins of the left column of the tile to the right
         for (int y = tid; y < t.th; y += NT) {
-            if (node_final(R, (size_t)t.g_right * S + SL::LEFT + y) & FINAL_SPIN)
-                sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
+            if (node_final(R, (size_t)t.g_right * S + SL::LEFT + y) & FINAL_SPIN) set_halo(y);
         }
         __syncthreads();
         long long bs = 0, mag = 0;
@@ -647,7 +664,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             const uint32_t vr = open_r ? valid_mask(c, t.tw - 1) : vm;   // sites with a right link
             const uint32_t vd = (open_b && y == t.th - 1) ? 0u : vm;      // sites with a down link
             const uint32_t cur = sm.sp[y][c];
-            const uint32_t right = (cur >> 1) | (sm.sp[y][c + 1] << 31);
+            const uint32_t right = (cur >> 1) | (right_of(y, c) << 31);
             const uint32_t down = sm.sp[y + 1][c];
             bs += __popc(vr) - 2 * __popc((cur ^ right) & vr) + __popc(vd) - 2 * __popc((cur ^ down) & vd);
             mag += 2 * __popc(cur & vm) - __popc(vm);
@@ -663,7 +680,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         long long v[4] = {bs, mag, c2, 0};
         DevObs *o = R.obs + jf;
         unsigned long long *const dst[4] = {&o->bond_sum, &o->mag, &o->csize2, nullptr};
-        block_sum_atomic<NT, 4>(v, dst, sm.red);
+        block_sum_atomic<NT, 4>(v, dst, sm.u.red);
         __syncthreads();
     }
 
@@ -674,6 +691,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     const uint64_t thr = (R.flags & RF_PCC) ? *R.thr_dev : R.thr;
     if (!fin) {
         // first sweep of the call: spins (and halos) from global memory
+        for (int w = tid; w < TH / 32; w += NT) sm.spx[w] = 0u;
         for (int w = warp; w < (t.th + 1) * TWW; w += NW) {
             const int y = w >> 2, c = w & 3;
             const int x = 32 * c + lane;
@@ -681,15 +699,12 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             int spin = 0;
             if (x < t.tw) spin = R.spin[gy * uL + (uint32_t)(t.x0 + x)];
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
-            if (lane == 0) {
-                sm.sp[y][c] = word;
-                if (c == TWW - 1) sm.sp[y][TWW] = 0u;
-            }
+            if (lane == 0) sm.sp[y][c] = word;
         }
         __syncthreads();
         for (int y = tid; y < t.th; y += NT) {
             const uint32_t gi = (uint32_t)(t.y0 + y) * uL + (uint32_t)((t.x0 + t.tw) % L);
-            if (R.spin[gi]) sm.sp[y][t.tw >> 5] |= 1u << (t.tw & 31);
+            if (R.spin[gi]) set_halo(y);
         }
         __syncthreads();
     }
@@ -725,16 +740,12 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             const uint32_t vr = open_r ? valid_mask(c, t.tw - 1) : vm;
             const uint32_t vd = (open_b && y == t.th - 1) ? 0u : vm;
             const uint32_t cur = sm.sp[y][c];
-            const uint32_t right = (cur >> 1) | (sm.sp[y][c + 1] << 31);
+            const uint32_t right = (cur >> 1) | (right_of(y, c) << 31);
             const uint32_t down = sm.sp[y + 1][c];
             const uint32_t h = rhc & ~(cur ^ right) & vr;
             const uint32_t v = rvc & ~(cur ^ down) & vd;
             sm.bh[y][c] = h;
             sm.bv[y][c] = v;
-            // intra-tile parts: the last column's right link and the last
-            // row's down link cross the tile edge
-            sm.ih[y][c] = h & valid_mask(c, t.tw - 1);
-            sm.iv[y][c] = (y < t.th - 1) ? v : 0u;
         }
     };
     auto store_row = [&](int y, const uint32_t (&rh)[TWW], const uint32_t (&rv)[TWW]) {
@@ -798,16 +809,27 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             store_row(y, rh, rv);
         }
     }
-    // SPIN-stream blocks covering each row, for the clusters that end inside
-    // the tile (Sec. I step 3: one new random spin per cluster)
-    for (int q = tid; q < 2 * t.th; q += NT) {
-        const int y = q >> 1, b = q & 1;
-        const uint32_t blk = ((gbase + (uint32_t)y * uL) >> 7) + b;
-        const U4 r = philox4x32_10(blk, klo, khi, STREAM_SPIN, R.key0, R.key1);
-        sm.spb[y][4 * b + 0] = r.x;
-        sm.spb[y][4 * b + 1] = r.y;
-        sm.spb[y][4 * b + 2] = r.z;
-        sm.spb[y][4 * b + 3] = r.w;
+    // The SPIN-stream bit of every site of the tile, for the clusters that end
+    // inside it (Sec. I step 3: one new random spin per cluster): bit (g mod
+    // 128) of Philox(g / 128, k, SPIN) for a site of global index g.  A row's
+    // 128 sites span the two blocks from the one holding its first site; one
+    // thread per row draws them and keeps the row's 128 bits.
+    for (int y = tid; y < t.th; y += NT) {
+        const uint32_t g0 = gbase + (uint32_t)y * uL;
+        const uint32_t pos = g0 & 127u;
+        const U4 r0 = philox4x32_10(g0 >> 7, klo, khi, STREAM_SPIN, R.key0, R.key1);
+        U4 r1 = r0;
+        if (pos) r1 = philox4x32_10((g0 >> 7) + 1, klo, khi, STREAM_SPIN, R.key0, R.key1);
+        // the 8 words from the first one the row needs: words pos/32 .. pos/32 + 4
+        uint32_t w[5];
+        switch (pos >> 5) {
+        case 0: w[0] = r0.x; w[1] = r0.y; w[2] = r0.z; w[3] = r0.w; w[4] = r1.x; break;
+        case 1: w[0] = r0.y; w[1] = r0.z; w[2] = r0.w; w[3] = r1.x; w[4] = r1.y; break;
+        case 2: w[0] = r0.z; w[1] = r0.w; w[2] = r1.x; w[3] = r1.y; w[4] = r1.z; break;
+        default: w[0] = r0.w; w[1] = r1.x; w[2] = r1.y; w[3] = r1.z; w[4] = r1.w; break;
+        }
+#pragma unroll
+        for (int c = 0; c < TWW; ++c) sm.u.spb[y][c] = __funnelshift_r(w[c], w[c + 1], pos & 31u);
     }
     __syncthreads();
 
@@ -838,7 +860,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     }
 
     // Step 2 inside the tile (Hoshen-Kopelman's role in Sec. II.A slave step 1)
-    tile_label<TH>(sm.par, sm.ih, sm.iv, t.th);
+    tile_label<TH>(sm.par, sm.bh, sm.bv, t.th, t.tw);
 
     // One node per border site: key = global index of the piece's local root,
     // parent = the piece's first border slot (the representative).
@@ -850,7 +872,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         rs[q] = -1;
         if (s < S && slot_site<TH>(s, t.tw, t.th, site)) {
             const int sy = site / TW, c = (site % TW) >> 5;
-            rs[q] = sroot(sm.par, head_of(run_heads(sm.ih[sy][c]), sy * PW + 32 * c, site & 31));
+            rs[q] = sroot(sm.par, head_of(run_heads(ih_of(sy, c)), sy * PW + 32 * c, site & 31));
         }
     }
     __syncthreads();
@@ -882,7 +904,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     for (int w = tid; w < t.th * TWW; w += NT) {
         const int y = w % t.th, c = w / t.th;   // a warp covers consecutive rows
         const int base = y * PW + 32 * c;
-        for (uint32_t bits = run_heads(sm.ih[y][c]); bits; bits &= bits - 1) {
+        for (uint32_t bits = run_heads(ih_of(y, c)); bits; bits &= bits - 1) {
             const int hx = __ffs(bits) - 1;
             const int hd = base + hx;
             int x = hd, p = sm.par[x];
@@ -896,12 +918,8 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
                 // at roots, so the feature variant keeps root indices.
                 sm.par[hd] = (!(F & FEAT_CSIZE) && (uint32_t)p >= INFO_INTERIOR && p != x) ? p : x;
             } else if (p == hd && 32 * c + hx < t.tw) {
-                // an interior root inside the tile: bit (g mod 128) of block
-                // g / 128 for its global index g; the row's two blocks start
-                // at the one holding the row's first site, so the bit sits
-                // at position (row start mod 128) + x of spb[y]
-                const uint32_t pos = ((gbase + (uint32_t)y * uL) & 127u) + (uint32_t)(32 * c + hx);
-                const uint32_t spin = (sm.spb[y][pos >> 5] >> (pos & 31)) & 1u;
+                // an interior root inside the tile: its site's SPIN-stream bit
+                const uint32_t spin = (sm.u.spb[y][c] >> hx) & 1u;
                 sm.par[hd] = (int)(INFO_INTERIOR | (spin << 14) | (uint32_t)(y * TW + 32 * c + hx));
                 ++ncl_interior;
             }
@@ -918,7 +936,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             const int y = w % t.th, c = w / t.th;
             const int base = y * PW + 32 * c;
             const int vw = min(32, t.tw - 32 * c);   // real sites in this word
-            for (uint32_t bits = run_heads(sm.ih[y][c]); bits;) {
+            for (uint32_t bits = run_heads(ih_of(y, c)); bits;) {
                 const int hx = __ffs(bits) - 1;
                 bits &= bits - 1;
                 if (hx >= vw) break;
@@ -940,7 +958,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         if (y >= t.th) continue;
         uint32_t wv[4] = {0u, 0u, 0u, 0u};
         const int c = xb >> 5;
-        const uint32_t heads = run_heads(sm.ih[y][c]);
+        const uint32_t heads = run_heads(ih_of(y, c));
         const int base = y * PW + 32 * c;
         int slot = -1;            // PCC: border piece of the sites gathered in cols
         uint32_t cols = 0u;
@@ -990,7 +1008,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             const int y = w % t.th, c = w / t.th;
             const int base = y * PW + 32 * c;
             const int vw = min(32, t.tw - 32 * c);
-            for (uint32_t bits = run_heads(sm.ih[y][c]) & valid_mask(0, vw); bits; bits &= bits - 1) {
+            for (uint32_t bits = run_heads(ih_of(y, c)) & valid_mask(0, vw); bits; bits &= bits - 1) {
                 const int v = sm.par[base + __ffs(bits) - 1];
                 if (v < 0) {   // piece size: bits 16-30 (bit 31 is the border flag)
                     R.psize[(size_t)t.lt * S + (v & 0x3FF)] = (int32_t)(((uint32_t)v >> 16) & 0x7FFFu);
@@ -1004,7 +1022,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     long long v4[4] = {nb, ncl_interior, c2, 0};
     DevObs *o = R.obs + j;
     unsigned long long *const dst[4] = {&o->nbonds, &o->nclusters, &o->csize2, nullptr};
-    block_sum_atomic<NT, 4>(v4, dst, sm.red);
+    block_sum_atomic<NT, 4>(v4, dst, sm.u.red);
 }
 
 // ------------------------------------------------ union-find with offsets
