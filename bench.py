@@ -170,15 +170,16 @@ def philox_calls_per_start(L: int) -> int:
     return bond + 2 * L * tiles_x
 
 
-def profile_traffic(kernel_src_sha: str):
-    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
-    or None when that summary was taken on a different kernel source."""
+def profile_traffic(kernel_src_sha: str, tile_h: int):
+    """DRAM bytes per launch of the tile kernel at this tile height from the
+    committed ncu summary, or None when that summary was taken on a different
+    kernel source (or lacks the height)."""
     try:
         txt = open(PROFILE_FILE).read()
     except OSError:
         return None
     m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
-    m_tr = re.search(r"dram bytes per launch:\s*([0-9]+)", txt)
+    m_tr = re.search(rf"dram bytes per launch, tile height {int(tile_h)}:\s*([0-9]+)", txt)
     if not m_sha or not m_tr or m_sha.group(1) != kernel_src_sha:
         return None
     return int(m_tr.group(1))
@@ -277,7 +278,7 @@ def run_gb300(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = alu_peak_tmul(props.multi_processor_count, sm_max)
-    traffic = profile_traffic(kernel_source_sha())
+    traffic = profile_traffic(kernel_source_sha(), tile_h)
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
                 "unit": "T int32 products/s (32x32->64, Philox4x32-10)",
                 "frac": round(achieved / peak, 4),
