@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SW site updates/ns at T_c (L=16384)"
+L2_BYTES = 129 << 20     # GB300 L2
 UNIT = "site-updates/ns"
 WIDE_MULS_PER_PHILOX = 20          # 10 rounds x 2 (32x32->64) products
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_tile_L16384_Tc.md")
@@ -47,6 +48,7 @@ def parse_args():
     ap.add_argument("--workload", default="plain", choices=["plain", "serve"])
     ap.add_argument("--lattice", type=int, default=0, help="profiling only: another L")
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: sweeps per step")
+    ap.add_argument("--temperature", type=float, default=0.0, help="profiling only: another T")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--tile-h", type=int, default=0, choices=[0, 32, 64, 96, 128],
                     help="rows per tile (0: the autotuner's choice for this L and T)")
@@ -92,7 +94,9 @@ def workload_config(w, extra=None):
     cfg = {"workload": f"plain SW, 2D Ising periodic L={w.L}, J=1, T={w.T}, hot start, "
                        f"{w.sweeps} sweeps per step",
            "L": w.L, "T": w.T, "J": 1.0, "sweeps_per_step": w.sweeps,
-           "l2": "inputs larger than L2 (256 MiB spins, 512 MiB site codes per lattice)"}
+           "l2": (f"inputs larger than L2 ({w.L * w.L >> 20} MiB spins, {2 * w.L * w.L >> 20} MiB site "
+                  f"codes per lattice)" if 3 * w.L * w.L > L2_BYTES else
+                  f"state L2-resident ({3 * w.L * w.L >> 10} KiB of spins and site codes)")}
     if extra:
         cfg.update(extra)
     return cfg
@@ -225,8 +229,9 @@ def run_gb300(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
     w = workloads.LARGE
-    if args.lattice or args.sweeps:
-        w = workloads.Plain(args.lattice or w.L, w.T, args.sweeps or w.sweeps, w.seed)
+    profiling = bool(args.lattice or args.sweeps or args.temperature)
+    if profiling:
+        w = workloads.Plain(args.lattice or w.L, args.temperature or w.T, args.sweeps or w.sweeps, w.seed)
     K, W = args.steps, args.warmup
     N = w.L * w.L
     stream = torch.cuda.Stream()
@@ -311,7 +316,7 @@ def run_gb300(args):
     del o
 
     batched = None
-    if not args.no_batch and not (args.lattice or args.sweeps):
+    if not args.no_batch and not profiling:
         batched = run_batch_vs_solo(swgpu, workloads, rank, world, barrier)
 
     out = None
@@ -320,7 +325,8 @@ def run_gb300(args):
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline_oracle(w)
         out = {
-            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC if not profiling else f"SW site updates/ns at T={w.T} (L={w.L})",
+            "value": round(value, 3), "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": round(ms / K, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
