@@ -45,7 +45,7 @@ def parse_args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-solo comparison")
-    ap.add_argument("--workload", default="plain", choices=["plain", "serve"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "serve", "potts"])
     ap.add_argument("--lattice", type=int, default=0, help="profiling only: another L")
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: sweeps per step")
     ap.add_argument("--temperature", type=float, default=0.0, help="profiling only: another T")
@@ -436,6 +436,70 @@ def run_serve(args):
                                    "80% SW T~U[1.8,3.2], 20% PCC", "data": "synthetic"}}
 
 
+# ------------------------------------------------------------- Potts / 3D
+POTTS_BYTES_PER_SITE = 7   # states in and out, the bond byte, the label
+
+
+def run_potts(args):
+    """The q-state Potts / 3D path at four critical points (2D: exact T_c;
+    3D: the published estimates), each lattice larger than L2: W warm-up
+    steps of 10 sweeps, then K steps timed with CUDA events on its stream."""
+    import math
+    import torch
+    from paper_0808_2109_gb300 import _build, swgpu
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    _build.build()
+    cases = [(2, 8192, 2, 1.0 / math.log(1.0 + math.sqrt(2.0))),
+             (2, 8192, 3, 1.0 / math.log(1.0 + math.sqrt(3.0))),
+             (3, 512, 2, 2.2557),     # q=2 is Ising at J/2: 4.5115 / 2
+             (3, 512, 3, 1.8164)]
+    SW = 10
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    rows, upd, ms_tot = [], 0, 0.0
+    for dim, L, q, T in cases:
+        with swgpu.PottsLattice(dim, L, q, T=T, seed=1) as lat:
+            lat.set_stream(stream)
+            for _ in range(args.warmup):
+                lat.sweep(SW)
+            lat.sync()
+            lat.observables()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                lat.sweep(SW)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            assert len(lat.observables()) == args.steps * SW
+            n = L ** dim * SW * args.steps
+            upd += n
+            ms_tot += ms
+            rows.append({"dim": dim, "L": L, "q": q, "T": round(T, 6),
+                         "value": round(n / (ms * 1e6), 3), "ms_per_sweep": round(ms / (SW * args.steps), 4)})
+    clk = clocks.stop()
+    value = upd / (ms_tot * 1e6)
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = value * POTTS_BYTES_PER_SITE   # site-updates/ns x B/site = GB/s
+    return {"metric": "Potts/3D SW site updates/ns (four critical lattices)", "value": round(value, 3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "q-state Potts, hot start, 10 sweeps per step", "cases": rows,
+                       "l2": "every lattice larger than L2 (states, labels and bond bytes >= 400 MB)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(hbm, 1), "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "traffic": None,
+                         "kernel": "all five kernels of a sweep",
+                         "bytes_per_site": POTTS_BYTES_PER_SITE},
+            "clocks": clk, "impl": "gb300"}
+
+
 # ---------------------------------------------------------- reference arm
 def run_reference(args):
     """The CPU oracle, single-threaded, one sweep of an L=4096 lattice of the
@@ -476,6 +540,8 @@ def main():
         out = run_reference(args)
     elif args.workload == "serve":
         out = run_serve(args)
+    elif args.workload == "potts":
+        out = run_potts(args)
     else:
         out = run_gb300(args)
     if out is not None:

@@ -3,11 +3,20 @@
 // "equal spins" read as "equal states", on the d-dimensional lattice the
 // paper states its method for (Sec. II).
 //
-// A site-level path, one thread per site: bonds, unions in a global
-// union-find (the smaller index wins, so roots are cluster minima), a
-// flattening pass, the new states, and the sums.  The tiled 2D Ising kernels
-// keep spins as single bits and do not carry over to q states or a third
-// dimension; this path trades their speed for generality.
+// Per sweep, five kernels over bricks of sites (32 x 32 in 2D, 8 x 8 x 8 in
+// 3D; one thread per site):
+//   1. k_potts_local: the brick's states (with a halo on the + side) in shared
+//      memory, its bonds, and a shared-memory union-find over the bonds inside
+//      the brick; every site's label becomes its piece's minimum site;
+//   2. k_potts_cross: the bonds that leave a brick unite pieces in a global
+//      union-find over those labels (the smaller index wins, so roots are
+//      cluster minima);
+//   3. k_potts_flatten: every label becomes its cluster's root, and piece
+//      sizes move to the roots;
+//   4. k_potts_assign: the new states and the cluster count;
+//   5. k_potts_measure: the sums.
+// The tiled 2D Ising kernels keep spins as single bits and do not carry over
+// to q states or a third dimension.
 //
 // Conventions (both sides implement them; the CPU oracle is the reference):
 //   - N = L^d sites, i = x + L*y (+ L*L*z); site i owns link dir = 0 (+x),
@@ -40,17 +49,14 @@ __device__ __forceinline__ uint8_t potts_state(uint32_t w, int q)
     return (uint8_t)(((uint64_t)w * (uint32_t)q) >> 32);
 }
 
-__device__ __forceinline__ int64_t nd_neighbour(const PottsDev &p, int64_t i, int dir)
+// Neighbour of site i (N <= 2^30, so 32-bit indices) along +dir, wrapping;
+// (x, y, z) are the site's coordinates.
+__device__ __forceinline__ uint32_t nd_neighbour(uint32_t uL, uint32_t i, uint32_t x, uint32_t y, uint32_t z,
+                                                 int dir)
 {
-    const int64_t L = p.L;
-    int64_t x = i % L, y = (i / L) % L, z = i / (L * L);
-    if (dir == 0)
-        x = x + 1 == L ? 0 : x + 1;
-    else if (dir == 1)
-        y = y + 1 == L ? 0 : y + 1;
-    else
-        z = z + 1 == L ? 0 : z + 1;
-    return p.dim == 2 ? y * L + x : (z * L + y) * L + x;
+    if (dir == 0) return i - x + (x + 1 == uL ? 0u : x + 1u);
+    if (dir == 1) return y + 1 == uL ? i - y * uL : i + uL;
+    return z + 1 == uL ? i - z * uL * uL : i + uL * uL;
 }
 
 __device__ __forceinline__ int pfind(int32_t *lab, int x)
@@ -89,87 +95,198 @@ __global__ void k_potts_hot_start(const PottsDev p)
     p.spin[i] = potts_state(u4_word(r, (int)(i & 3)), p.q);
 }
 
-// Every site its own cluster; cluster sizes zeroed.
-__global__ void k_potts_reset(const PottsDev p)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.N) return;
-    p.label[i] = (int32_t)i;
-    if (p.size) p.size[i] = 0;
-}
+// Sites of a brick, one thread each, and its shared states with a halo of
+// one site on the + side of every axis.
+template <int DIM>
+struct Brick {
+    static constexpr int BX = DIM == 2 ? 32 : 8, BY = DIM == 2 ? 32 : 8, BZ = DIM == 2 ? 1 : 8;
+    static constexpr int NT = BX * BY * BZ;
+    static constexpr int HX = BX + 1, HY = BY + 1, HZ = DIM == 2 ? 1 : BZ + 1;
+};
 
-// Bonds of site i's own links (Sec. I step 1) and their unions (step 2).
-__global__ void k_potts_bonds(const PottsDev p, uint64_t k)
+// Bonds of every site's own links (Sec. I step 1); unions of the bonds inside
+// the brick (step 2) in shared memory, larger root under smaller (local order
+// is global order inside a brick, so a piece's root is its minimum site).
+// Every site's label: its piece's minimum site; with cluster sizes, each piece
+// root's size holds the piece's site count and every other size is zero.
+template <int DIM>
+__global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p, uint64_t k)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.N) return;
-    const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
-    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
-    const uint8_t s = p.spin[i];
-    const int64_t l0 = (int64_t)p.dim * i;
-    // the site's links fall in one or two Philox blocks
-    const int64_t m0 = l0 >> 2, m1 = (l0 + p.dim - 1) >> 2;
-    const U4 r0 = philox4x32_10((uint32_t)m0, klo, khi, STREAM_BOND, k0, k1);
-    U4 r1 = r0;
-    if (m1 != m0) r1 = philox4x32_10((uint32_t)m1, klo, khi, STREAM_BOND, k0, k1);
-    uint8_t b = 0;
-    for (int dir = 0; dir < p.dim; ++dir) {
-        const int64_t l = l0 + dir;
-        const uint32_t u = u4_word((l >> 2) == m0 ? r0 : r1, (int)(l & 3));
-        const int64_t j = nd_neighbour(p, i, dir);
-        if (p.spin[j] == s && (uint64_t)u < p.thr) {
-            b |= (uint8_t)(1u << dir);
-            punite(p.label, (int)i, (int)j);
-        }
+    using B = Brick<DIM>;
+    __shared__ uint8_t st[B::HZ][B::HY][B::HX];
+    __shared__ int par[B::NT];
+    __shared__ int cnt[B::NT];
+    const int L = p.L;
+    const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
+    const uint32_t uL = (uint32_t)L;
+    // past the lattice's last site the halo wraps (a lattice narrower than a
+    // brick wraps more than once)
+    auto wrap = [L](int g) { return (uint32_t)(g < L ? g : g % L); };
+    for (int q = threadIdx.x; q < B::HX * B::HY * B::HZ; q += B::NT) {
+        const int hx = q % B::HX, hy = (q / B::HX) % B::HY, hz = q / (B::HX * B::HY);
+        const uint32_t gx = wrap(x0 + hx), gy = wrap(y0 + hy), gz = DIM == 3 ? wrap(z0 + hz) : 0u;
+        st[hz][hy][hx] = p.spin[gx + uL * (gy + uL * gz)];
     }
-    p.bond[i] = b;
+    const int t = threadIdx.x;
+    const int lx = t % B::BX, ly = (t / B::BX) % B::BY, lz = t / (B::BX * B::BY);
+    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+    const bool valid = gx < L && gy < L && (DIM == 2 || gz < L);
+    const uint32_t i = (uint32_t)gx + uL * ((uint32_t)gy + uL * (uint32_t)gz);   // N <= 2^30
+    par[t] = t;
+    if (p.size) cnt[t] = 0;
+    __syncthreads();
+    if (valid) {
+        const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
+        const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+        const uint8_t s = st[lz][ly][lx];
+        const uint32_t l0 = (uint32_t)DIM * i;   // < 3 * 2^30
+        // the site's links fall in one or two Philox blocks
+        const uint32_t m0 = l0 >> 2, m1 = (l0 + DIM - 1) >> 2;
+        const U4 r0 = philox4x32_10(m0, klo, khi, STREAM_BOND, k0, k1);
+        U4 r1 = r0;
+        if (m1 != m0) r1 = philox4x32_10(m1, klo, khi, STREAM_BOND, k0, k1);
+        uint8_t bits = 0;
+#pragma unroll
+        for (int dir = 0; dir < DIM; ++dir) {
+            const uint32_t l = l0 + dir;
+            const uint32_t u = u4_word((l >> 2) == m0 ? r0 : r1, (int)(l & 3));
+            const uint8_t ns = dir == 0 ? st[lz][ly][lx + 1] : dir == 1 ? st[lz][ly + 1][lx] : st[lz + 1][ly][lx];
+            if (ns == s && (uint64_t)u < p.thr) bits |= (uint8_t)(1u << dir);
+        }
+        p.bond[i] = bits;
+        // bonds whose far end is in the brick (not across the lattice's edge)
+        if ((bits & 1) && lx + 1 < B::BX && gx + 1 < L) sunite(par, t, t + 1);
+        if ((bits & 2) && ly + 1 < B::BY && gy + 1 < L) sunite(par, t, t + B::BX);
+        if (DIM == 3 && (bits & 4) && lz + 1 < B::BZ && gz + 1 < L) sunite(par, t, t + B::BX * B::BY);
+    }
+    __syncthreads();
+    if (valid) {
+        const int r = sroot(par, t);
+        const int rx = r % B::BX, ry = (r / B::BX) % B::BY, rz = r / (B::BX * B::BY);
+        p.label[i] = (int32_t)((uint32_t)(x0 + rx) + uL * ((uint32_t)(y0 + ry) + uL * (uint32_t)(z0 + rz)));
+        if (p.size) atomicAdd(&cnt[r], 1);
+    }
+    if (p.size) {
+        __syncthreads();
+        if (valid) p.size[i] = par[t] == t ? cnt[t] : 0;
+    }
 }
 
-// Every site's label becomes its root: the cluster minimum.
+// Bonds that leave their brick (Sec. I step 2 across bricks): unite the two
+// ends' pieces in the global forest of labels.  One block per brick, one
+// thread per site of its + faces (the brick's last valid column, row and
+// layer, which also hold the lattice's wrapping links).
+template <int DIM>
+struct Faces {
+    static constexpr int FS = DIM == 2 ? 32 : 64;   // sites of one face
+    static constexpr int NT = DIM * FS;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(Faces<DIM>::NT) k_potts_cross(const PottsDev p)
+{
+    using B = Brick<DIM>;
+    constexpr int FS = Faces<DIM>::FS;
+    const int L = p.L;
+    const uint32_t uL = (uint32_t)L;
+    const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
+    const int f = threadIdx.x / FS, r = threadIdx.x % FS;   // f: the face's axis
+    const int a = DIM == 2 ? r : r % 8, b = DIM == 2 ? 0 : r / 8;
+    int gx, gy, gz;
+    if (f == 0) {
+        gx = min(x0 + B::BX, L) - 1;
+        gy = y0 + a;
+        gz = z0 + b;
+    } else if (f == 1) {
+        gx = x0 + a;
+        gy = min(y0 + B::BY, L) - 1;
+        gz = z0 + b;
+    } else {
+        gx = x0 + a;
+        gy = y0 + b;
+        gz = min(z0 + B::BZ, L) - 1;
+    }
+    if (gx >= L || gy >= L || (DIM == 3 && gz >= L)) return;
+    const uint32_t i = (uint32_t)gx + uL * ((uint32_t)gy + uL * (uint32_t)gz);
+    if (!((p.bond[i] >> f) & 1u)) return;
+    uint32_t j;
+    if (f == 0)
+        j = i - (uint32_t)gx + (gx + 1 == L ? 0u : (uint32_t)gx + 1u);
+    else if (f == 1)
+        j = gy + 1 == L ? i - (uint32_t)gy * uL : i + uL;
+    else
+        j = gz + 1 == L ? i - (uint32_t)gz * uL * uL : i + uL * uL;
+    punite(p.label, (int)i, (int)j);
+}
+
+// Every site's label becomes its root: the cluster minimum (every write
+// moves a label to an ancestor, so concurrent walks stay on their paths).  A
+// piece root that is not a cluster root hands its size to the cluster root.
 __global__ void k_potts_flatten(const PottsDev p)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.N) return;
-    int x = (int)i, nx = gload(p.label + x);
+    const int first = gload(p.label + i);   // the piece's root, or an ancestor of it
+    int x = first, nx = gload(p.label + x);
     while (nx != x) {
         x = nx;
         nx = gload(p.label + x);
     }
+    // the other sites of the piece then stop one step later
+    if (x != first) *(volatile int32_t *)(p.label + first) = x;
+    if (p.size && x != (int)i) {
+        const int s = p.size[i];
+        if (s > 0) {
+            atomicAdd(p.size + x, s);
+            p.size[i] = 0;
+        }
+    }
     p.label[i] = x;
-    if (p.size) atomicAdd(p.size + x, 1);
 }
+
+// The per-site passes below stride over the lattice with a bounded grid, so
+// each block adds its sums to the observables once.
+constexpr unsigned MAX_BLOCKS = 4096;
 
 // New states (Sec. I step 3) and the cluster count.
 __global__ void k_potts_assign(const PottsDev p, uint64_t k, DevObs *obs)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int root = 0;
-    if (i < p.N) {
+    int roots = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = p.label[i];
         const U4 w = philox4x32_10((uint32_t)(r >> 2), (uint32_t)k, (uint32_t)(k >> 32), STREAM_QSPIN,
                                    (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
         p.spin[i] = potts_state(u4_word(w, (int)(r & 3)), p.q);
-        root = r == i;
+        roots += r == i;
     }
-    const int n = __syncthreads_count(root);
-    if (threadIdx.x == 0 && n) atomicAdd(&obs->nclusters, (unsigned long long)n);
-    if (i == 0) obs->threshold = p.thr;
+    roots = __reduce_add_sync(0xFFFFFFFFu, roots);
+    __shared__ int red[PT / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = roots;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long n = 0;
+        for (int w = 0; w < PT / 32; ++w) n += red[w];
+        if (n) atomicAdd(&obs->nclusters, (unsigned long long)n);
+        if (blockIdx.x == 0) obs->threshold = p.thr;
+    }
 }
 
 // Sums of the new states: bond_sum, mag, the bond count and sum |C|^2.
 __global__ void k_potts_measure(const PottsDev p, DevObs *obs)
 {
     __shared__ long long red[PT / 32][4];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     long long v[4] = {0, 0, 0, 0};
-    if (i < p.N) {
+    const uint32_t uL = (uint32_t)p.L;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ui = (uint32_t)i;
+        const uint32_t x = ui % uL, y = (ui / uL) % uL, z = ui / (uL * uL);
         const uint8_t s = p.spin[i];
-        for (int dir = 0; dir < p.dim; ++dir) v[0] += p.spin[nd_neighbour(p, i, dir)] == s ? 1 : -1;
-        v[1] = s == 0 ? p.q - 1 : -1;
-        v[2] = __popc((uint32_t)p.bond[i]);
+        for (int dir = 0; dir < p.dim; ++dir) v[0] += p.spin[nd_neighbour(uL, ui, x, y, z, dir)] == s ? 1 : -1;
+        v[1] += s == 0 ? p.q - 1 : -1;
+        v[2] += __popc((uint32_t)p.bond[i]);
         if (p.size) {
             const long long c = p.size[i];
-            v[3] = c * c;
+            v[3] += c * c;
         }
     }
     unsigned long long *const dst[4] = {&obs->bond_sum, &obs->mag, &obs->nbonds, &obs->csize2};
@@ -200,11 +317,24 @@ cudaError_t potts_enqueue_hot_start(const PottsDev &p, cudaStream_t st)
 cudaError_t potts_enqueue_sweep(const PottsDev &p, uint64_t sweep, DevObs *obs, cudaStream_t st)
 {
     const unsigned nb = blocks_of(p.N);
-    k_potts_reset<<<nb, PT, 0, st>>>(p);
-    k_potts_bonds<<<nb, PT, 0, st>>>(p, sweep);
+    // one block per brick (2D: L <= 2^15, so at most 1024 bricks along an
+    // axis; 3D: L <= 2^10, at most 128)
+    if (p.dim == 2) {
+        using B = Brick<2>;
+        const dim3 g((unsigned)((p.L + B::BX - 1) / B::BX), (unsigned)((p.L + B::BY - 1) / B::BY), 1u);
+        k_potts_local<2><<<g, B::NT, 0, st>>>(p, sweep);
+        k_potts_cross<2><<<g, Faces<2>::NT, 0, st>>>(p);
+    } else {
+        using B = Brick<3>;
+        const unsigned nb3 = (unsigned)((p.L + B::BX - 1) / B::BX);
+        const dim3 g(nb3, nb3, nb3);
+        k_potts_local<3><<<g, B::NT, 0, st>>>(p, sweep);
+        k_potts_cross<3><<<g, Faces<3>::NT, 0, st>>>(p);
+    }
     k_potts_flatten<<<nb, PT, 0, st>>>(p);
-    k_potts_assign<<<nb, PT, 0, st>>>(p, sweep, obs);
-    k_potts_measure<<<nb, PT, 0, st>>>(p, obs);
+    const unsigned ns = std::min(nb, MAX_BLOCKS);
+    k_potts_assign<<<ns, PT, 0, st>>>(p, sweep, obs);
+    k_potts_measure<<<ns, PT, 0, st>>>(p, obs);
     return cudaGetLastError();
 }
 

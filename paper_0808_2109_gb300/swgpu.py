@@ -518,6 +518,9 @@ class PottsLattice:
     def load(self, data: bytes):
         sw_load(self.h, data)
 
+    def set_stream(self, stream):
+        sw_set_stream(self.h, stream)
+
     def sync(self):
         sw_sync(self.h)
 
