@@ -49,16 +49,6 @@ __device__ __forceinline__ uint8_t potts_state(uint32_t w, int q)
     return (uint8_t)(((uint64_t)w * (uint32_t)q) >> 32);
 }
 
-// Neighbour of site i (N <= 2^30, so 32-bit indices) along +dir, wrapping;
-// (x, y, z) are the site's coordinates.
-__device__ __forceinline__ uint32_t nd_neighbour(uint32_t uL, uint32_t i, uint32_t x, uint32_t y, uint32_t z,
-                                                 int dir)
-{
-    if (dir == 0) return i - x + (x + 1 == uL ? 0u : x + 1u);
-    if (dir == 1) return y + 1 == uL ? i - y * uL : i + uL;
-    return z + 1 == uL ? i - z * uL * uL : i + uL * uL;
-}
-
 __device__ __forceinline__ int pfind(int32_t *lab, int x)
 {
     int p = gload(lab + x);
@@ -116,6 +106,7 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
     __shared__ uint8_t st[B::HZ][B::HY][B::HX];
     __shared__ int par[B::NT];
     __shared__ int cnt[B::NT];
+    __shared__ uint32_t uw[DIM * B::NT];   // the BOND words of the brick's links
     const int L = p.L;
     const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
     const uint32_t uL = (uint32_t)L;
@@ -134,22 +125,35 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
     const uint32_t i = (uint32_t)gx + uL * ((uint32_t)gy + uL * (uint32_t)gz);   // N <= 2^30
     par[t] = t;
     if (p.size) cnt[t] = 0;
+    const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
+    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    {
+        // a brick row's BX sites own DIM * BX consecutive links, which span
+        // RB - 1 or RB Philox blocks; each block is drawn once, by one thread
+        // (words of sites past the lattice's edge are drawn but never read)
+        constexpr int RL = DIM * B::BX, RB = RL / 4 + 1, NR = B::BY * B::BZ;
+        for (int q = t; q < NR * RB; q += B::NT) {
+            const int row = q / RB, jb = q % RB;
+            const int ry = row % B::BY, rz = row / B::BY;
+            if (y0 + ry >= L || (DIM == 3 && z0 + rz >= L)) continue;
+            const uint32_t i0 = (uint32_t)x0 + uL * ((uint32_t)(y0 + ry) + uL * (uint32_t)(z0 + rz));
+            const uint32_t la = (uint32_t)DIM * i0, ma = la >> 2, mb = (la + RL - 1) >> 2;
+            if ((uint32_t)jb > mb - ma) continue;
+            const U4 r = philox4x32_10(ma + (uint32_t)jb, klo, khi, STREAM_BOND, k0, k1);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t l = 4u * (ma + (uint32_t)jb) + (uint32_t)w;
+                if (l >= la && l < la + RL) uw[RL * row + (l - la)] = u4_word(r, w);
+            }
+        }
+    }
     __syncthreads();
     if (valid) {
-        const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
-        const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
         const uint8_t s = st[lz][ly][lx];
-        const uint32_t l0 = (uint32_t)DIM * i;   // < 3 * 2^30
-        // the site's links fall in one or two Philox blocks
-        const uint32_t m0 = l0 >> 2, m1 = (l0 + DIM - 1) >> 2;
-        const U4 r0 = philox4x32_10(m0, klo, khi, STREAM_BOND, k0, k1);
-        U4 r1 = r0;
-        if (m1 != m0) r1 = philox4x32_10(m1, klo, khi, STREAM_BOND, k0, k1);
         uint8_t bits = 0;
 #pragma unroll
         for (int dir = 0; dir < DIM; ++dir) {
-            const uint32_t l = l0 + dir;
-            const uint32_t u = u4_word((l >> 2) == m0 ? r0 : r1, (int)(l & 3));
+            const uint32_t u = uw[DIM * t + dir];   // link DIM * i + dir
             const uint8_t ns = dir == 0 ? st[lz][ly][lx + 1] : dir == 1 ? st[lz][ly + 1][lx] : st[lz + 1][ly][lx];
             if (ns == s && (uint64_t)u < p.thr) bits |= (uint8_t)(1u << dir);
         }
@@ -271,22 +275,35 @@ __global__ void k_potts_assign(const PottsDev p, uint64_t k, DevObs *obs)
     }
 }
 
-// Sums of the new states: bond_sum, mag, the bond count and sum |C|^2.
+// Sums of the new states: bond_sum, mag, the bond count and sum |C|^2.  A
+// warp takes one lattice row (L sites along x) at a time, so neighbours are
+// found without dividing site indices.
 __global__ void k_potts_measure(const PottsDev p, DevObs *obs)
 {
     __shared__ long long red[PT / 32][4];
     long long v[4] = {0, 0, 0, 0};
     const uint32_t uL = (uint32_t)p.L;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t ui = (uint32_t)i;
-        const uint32_t x = ui % uL, y = (ui / uL) % uL, z = ui / (uL * uL);
-        const uint8_t s = p.spin[i];
-        for (int dir = 0; dir < p.dim; ++dir) v[0] += p.spin[nd_neighbour(uL, ui, x, y, z, dir)] == s ? 1 : -1;
-        v[1] += s == 0 ? p.q - 1 : -1;
-        v[2] += __popc((uint32_t)p.bond[i]);
-        if (p.size) {
-            const long long c = p.size[i];
-            v[3] += c * c;
+    const uint32_t rows = (uint32_t)(p.N / p.L);   // row R = y + L z
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t R = w0; R < rows; R += nw) {
+        const uint32_t y = R % uL, z = R / uL;
+        const uint32_t Ry = y + 1 == uL ? R - y : R + 1;                     // row at y + 1
+        const uint32_t Rz = p.dim == 3 ? (z + 1 == uL ? R - z * uL : R + uL) : 0u;   // row at z + 1
+        const uint8_t *row = p.spin + (size_t)R * uL;
+        const uint8_t *row_y = p.spin + (size_t)Ry * uL;
+        const uint8_t *row_z = p.spin + (size_t)Rz * uL;
+        for (uint32_t x = lane; x < uL; x += 32) {
+            const uint8_t s = row[x];
+            v[0] += (row[x + 1 == uL ? 0u : x + 1] == s ? 1 : -1) + (row_y[x] == s ? 1 : -1);
+            if (p.dim == 3) v[0] += row_z[x] == s ? 1 : -1;
+            v[1] += s == 0 ? p.q - 1 : -1;
+            const size_t i = (size_t)R * uL + x;
+            v[2] += __popc((uint32_t)p.bond[i]);
+            if (p.size) {
+                const long long c = p.size[i];
+                v[3] += c * c;
+            }
         }
     }
     unsigned long long *const dst[4] = {&obs->bond_sum, &obs->mag, &obs->nbonds, &obs->csize2};
