@@ -3,18 +3,18 @@
 // "equal spins" read as "equal states", on the d-dimensional lattice the
 // paper states its method for (Sec. II).
 //
-// Per sweep, five kernels over bricks of sites (32 x 32 in 2D, 8 x 8 x 8 in
-// 3D; one thread per site):
+// Per sweep, four kernels, the first two over bricks of sites (32 x 32 in 2D,
+// 8 x 8 x 8 in 3D):
 //   1. k_potts_local: the brick's states (with a halo on the + side) in shared
 //      memory, its bonds, and a shared-memory union-find over the bonds inside
 //      the brick; every site's label becomes its piece's minimum site;
 //   2. k_potts_cross: the bonds that leave a brick unite pieces in a global
 //      union-find over those labels (the smaller index wins, so roots are
 //      cluster minima);
-//   3. k_potts_flatten: every label becomes its cluster's root, and piece
-//      sizes move to the roots;
-//   4. k_potts_assign: the new states and the cluster count;
-//   5. k_potts_measure: the sums.
+//   3. k_potts_resolve: every label becomes its cluster's root, piece sizes
+//      move to the roots, every site takes its cluster's new state, and the
+//      clusters are counted;
+//   4. k_potts_measure: the sums.
 // The tiled 2D Ising kernels keep spins as single bits and do not carry over
 // to q states or a third dimension.
 //
@@ -223,45 +223,39 @@ __global__ void __launch_bounds__(Faces<DIM>::NT) k_potts_cross(const PottsDev p
     punite(p.label, (int)i, (int)j);
 }
 
-// Every site's label becomes its root: the cluster minimum (every write
-// moves a label to an ancestor, so concurrent walks stay on their paths).  A
-// piece root that is not a cluster root hands its size to the cluster root.
-__global__ void k_potts_flatten(const PottsDev p)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.N) return;
-    const int first = gload(p.label + i);   // the piece's root, or an ancestor of it
-    int x = first, nx = gload(p.label + x);
-    while (nx != x) {
-        x = nx;
-        nx = gload(p.label + x);
-    }
-    // the other sites of the piece then stop one step later
-    if (x != first) *(volatile int32_t *)(p.label + first) = x;
-    if (p.size && x != (int)i) {
-        const int s = p.size[i];
-        if (s > 0) {
-            atomicAdd(p.size + x, s);
-            p.size[i] = 0;
-        }
-    }
-    p.label[i] = x;
-}
-
 // The per-site passes below stride over the lattice with a bounded grid, so
 // each block adds its sums to the observables once.
 constexpr unsigned MAX_BLOCKS = 4096;
 
-// New states (Sec. I step 3) and the cluster count.
-__global__ void k_potts_assign(const PottsDev p, uint64_t k, DevObs *obs)
+// Every site's label becomes its root, the cluster minimum (every write moves
+// a label to an ancestor, so concurrent walks stay on their paths), and the
+// site takes its cluster's new state (Sec. I step 3); cluster roots are
+// counted.  A piece root that is not a cluster root hands its size to the
+// cluster root.
+__global__ void k_potts_resolve(const PottsDev p, uint64_t k, DevObs *obs)
 {
     int roots = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = p.label[i];
-        const U4 w = philox4x32_10((uint32_t)(r >> 2), (uint32_t)k, (uint32_t)(k >> 32), STREAM_QSPIN,
+        const int first = gload(p.label + i);   // the piece's root, or an ancestor of it
+        int x = first, nx = gload(p.label + x);
+        while (nx != x) {
+            x = nx;
+            nx = gload(p.label + x);
+        }
+        // the other sites of the piece then stop one step later
+        if (x != first) *(volatile int32_t *)(p.label + first) = x;
+        if (p.size && x != (int)i) {
+            const int s = p.size[i];
+            if (s > 0) {
+                atomicAdd(p.size + x, s);
+                p.size[i] = 0;
+            }
+        }
+        p.label[i] = x;
+        const U4 w = philox4x32_10((uint32_t)x >> 2, (uint32_t)k, (uint32_t)(k >> 32), STREAM_QSPIN,
                                    (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-        p.spin[i] = potts_state(u4_word(w, (int)(r & 3)), p.q);
-        roots += r == i;
+        p.spin[i] = potts_state(u4_word(w, x & 3), p.q);
+        roots += x == (int)i;
     }
     roots = __reduce_add_sync(0xFFFFFFFFu, roots);
     __shared__ int red[PT / 32];
@@ -348,9 +342,8 @@ cudaError_t potts_enqueue_sweep(const PottsDev &p, uint64_t sweep, DevObs *obs, 
         k_potts_local<3><<<g, B::NT, 0, st>>>(p, sweep);
         k_potts_cross<3><<<g, Faces<3>::NT, 0, st>>>(p);
     }
-    k_potts_flatten<<<nb, PT, 0, st>>>(p);
     const unsigned ns = std::min(nb, MAX_BLOCKS);
-    k_potts_assign<<<ns, PT, 0, st>>>(p, sweep, obs);
+    k_potts_resolve<<<ns, PT, 0, st>>>(p, sweep, obs);
     k_potts_measure<<<ns, PT, 0, st>>>(p, obs);
     return cudaGetLastError();
 }
