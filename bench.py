@@ -34,7 +34,7 @@ L2_BYTES = 129 << 20     # GB300 L2
 UNIT = "site-updates/ns"
 WIDE_MULS_PER_PHILOX = 20          # 10 rounds x 2 (32x32->64) products
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_tile_L16384_Tc.md")
-MERGE_JUMPS = 3                    # pointer-jumping launches per sweep in the merge
+LAUNCHES_PER_SWEEP = 4             # tile kernel, merge union, pointer jumping, resolve
 
 
 def parse_args():
@@ -334,7 +334,7 @@ def run_gb300(args):
                                           "seeds": f"{w.seed}..{w.seed + world - 1}",
                                           "tile_h": tile_h}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
-            "gpu_launches": K * ((3 + MERGE_JUMPS) * w.sweeps + 1),
+            "gpu_launches": K * (LAUNCHES_PER_SWEEP * w.sweeps + 1),
             "clocks": clk, "impl": "gb300",
         }
     lat.close()

@@ -1233,10 +1233,14 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_wind_init(const SweepArgs 
     }
 }
 
-// One round of pointer jumping over the representatives (every parent
-// replaced by its grandparent): a few rounds between the unions and the
-// compression cut the depth of the chains that unions across many tiles
-// leave behind.  Other slots only alias their piece's representative.
+// Pointer jumping over the representatives (every parent replaced by its
+// grandparent, MERGE_JUMP_ROUNDS times) between the unions and the
+// compression: it cuts the depth of the chains that unions across many tiles
+// leave behind.  The rounds run in one launch, so a round may read a parent
+// that its own thread has already moved up; every value read is still an
+// ancestor, and the resolve kernel walks to the root whatever depth is left.
+// Other slots only alias their piece's representative.
+constexpr int MERGE_JUMP_ROUNDS = 3;
 template <int TH, bool W>
 __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs a)
 {
@@ -1247,18 +1251,20 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs
     const Replica &R = *Rp;
     const int base = (blockIdx.x - R.tile_base) * MC::S;   // the lattice's own nodes
     if (W && (R.flags & RF_WIND)) {
-        unsigned long long v[MC::NPT], w[MC::NPT];
+        for (int r = 0; r < MERGE_JUMP_ROUNDS; ++r) {
+            unsigned long long v[MC::NPT], w[MC::NPT];
 #pragma unroll
-        for (int q = 0; q < MC::NPT; ++q)
-            v[q] = ((uint32_t)R.nkey[base + threadIdx.x + q * MC::MT] & KEY_REP)
-                       ? wload(R.nlink + base + threadIdx.x + q * MC::MT) : ~0ull;
+            for (int q = 0; q < MC::NPT; ++q)
+                v[q] = ((uint32_t)R.nkey[base + threadIdx.x + q * MC::MT] & KEY_REP)
+                           ? wload(R.nlink + base + threadIdx.x + q * MC::MT) : ~0ull;
 #pragma unroll
-        for (int q = 0; q < MC::NPT; ++q) w[q] = v[q] != ~0ull ? wload(R.nlink + (uint32_t)v[q]) : ~0ull;
+            for (int q = 0; q < MC::NPT; ++q) w[q] = v[q] != ~0ull ? wload(R.nlink + (uint32_t)v[q]) : ~0ull;
 #pragma unroll
-        for (int q = 0; q < MC::NPT; ++q)
-            if (v[q] != ~0ull && (uint32_t)w[q] != (uint32_t)v[q])
-                *(volatile unsigned long long *)(R.nlink + base + threadIdx.x + q * MC::MT) =
-                    wind_link((int)(uint32_t)w[q], wind_add((uint32_t)(v[q] >> 32), (uint32_t)(w[q] >> 32)));
+            for (int q = 0; q < MC::NPT; ++q)
+                if (v[q] != ~0ull && (uint32_t)w[q] != (uint32_t)v[q])
+                    *(volatile unsigned long long *)(R.nlink + base + threadIdx.x + q * MC::MT) =
+                        wind_link((int)(uint32_t)w[q], wind_add((uint32_t)(v[q] >> 32), (uint32_t)(w[q] >> 32)));
+        }
         return;
     }
     uint32_t key[MC::NPT];
@@ -1267,11 +1273,15 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs
     for (int q = 0; q < MC::NPT; ++q) key[q] = (uint32_t)R.nkey[base + threadIdx.x + q * MC::MT];
 #pragma unroll
     for (int q = 0; q < MC::NPT; ++q) p[q] = (key[q] & KEY_REP) ? gload(R.npar + base + threadIdx.x + q * MC::MT) : -1;
+    for (int r = 0; r < MERGE_JUMP_ROUNDS; ++r) {
 #pragma unroll
-    for (int q = 0; q < MC::NPT; ++q) gp[q] = p[q] >= 0 ? gload(R.npar + p[q]) : -1;
+        for (int q = 0; q < MC::NPT; ++q) gp[q] = p[q] >= 0 ? gload(R.npar + p[q]) : -1;
 #pragma unroll
-    for (int q = 0; q < MC::NPT; ++q)
-        if (gp[q] != p[q]) *(volatile int32_t *)(R.npar + base + threadIdx.x + q * MC::MT) = gp[q];
+        for (int q = 0; q < MC::NPT; ++q) {
+            if (gp[q] != p[q]) *(volatile int32_t *)(R.npar + base + threadIdx.x + q * MC::MT) = gp[q];
+            p[q] = gp[q];
+        }
+    }
 }
 
 // Resolve every node once the unions are done: each representative walks to

@@ -63,7 +63,7 @@ void launch_merge_w(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
     const unsigned tiles = (unsigned)a.n_tiles;
     if (W) k_wind_init<TH><<<tiles, MT, 0, st>>>(a);
     k_merge_union<TH, W><<<tiles, MT, 0, st>>>(a);
-    for (int r = 0; r < MERGE_JUMPS; ++r) k_merge_jump<TH, W><<<tiles, MT, 0, st>>>(a);
+    k_merge_jump<TH, W><<<tiles, MT, 0, st>>>(a);
     k_merge_resolve<TH, W><<<tiles, MT, 0, st>>>(a);
     if (pcc) {   // reads the compressed forest; the spins do not depend on it
         k_pcc_candidates<TH><<<bu, MERGE_THREADS, 0, st>>>(a);

@@ -10,7 +10,6 @@
 namespace swg {
 
 constexpr int MERGE_THREADS = 256;
-constexpr int MERGE_JUMPS = 3;     // pointer-jumping rounds between unions and compression
 
 // Defined once, in sw_engine.cu: every kernel template is instantiated in
 // that translation unit only, so each kernel has a single module copy (and
