@@ -242,6 +242,27 @@ int sw_save(sw_ctx *ctx, void *host_buf, uint64_t bytes);
  * and sw_get_bonds answer SW_ERR_STATE until the next sweep. */
 int sw_load(sw_ctx *ctx, const void *host_buf, uint64_t bytes);
 
+/* Integer ceiling of the bond step (measurement support).  Sec. II's cost
+ * model charges every sweep a per-site bond-activating time tau_site; here
+ * that work is Philox4x32-10 draws, so their rate bounds the sweep.  Draws
+ * the BOND-stream blocks with counters 0 .. nblocks-1 (sweep 0, key = seed)
+ * on a grid that fills the GPU, four blocks in flight per thread, and xors
+ * every word into *out_dev (a caller-owned 4-byte-aligned device word; the
+ * call does not clear it).  Asynchronous on `stream` (a cudaStream_t, NULL:
+ * the legacy default stream); time it with events on that stream to get
+ * blocks per second.  0 <= nblocks <= 2^32, else SW_ERR_ARG; a NULL or
+ * misaligned out_dev: SW_ERR_ARG. */
+int sw_bench_philox(int64_t nblocks, uint64_t seed, uint32_t *out_dev, void *stream);
+
+/* L2 copy ceiling (measurement support for the lattices whose state fits
+ * the L2 cache, Sec. II.C's smaller L).  reps passes of dst = src ^ pass over
+ * `bytes` bytes of caller-owned device memory, loads and stores cached in L2
+ * only; with src and dst together smaller than L2, every pass after the
+ * first runs out of L2.  Time it with events on `stream`: 2 * bytes * reps /
+ * time is the copy bandwidth.  Both buffers 16-byte aligned, not
+ * overlapping, bytes > 0 and a multiple of 16, reps >= 1; else SW_ERR_ARG. */
+int sw_bench_l2(const void *src_dev, void *dst_dev, int64_t bytes, int32_t reps, void *stream);
+
 /* Fault injection for tests (host side; the paper has no counterpart): of
  * the library's next device allocations, the first `skip` proceed and the n
  * after them report out-of-memory without allocating, so callers see
@@ -322,30 +343,38 @@ int sw_batch_wait_all(sw_server *srv, double timeout_s);
 int sw_server_get_stats(sw_server *srv, sw_server_stats *out);
 
 /* ------------------------------------------------- sweep without allocation
- * The paper has no counterpart to this call: it exists for callers that must
- * not allocate device memory -- code running inside someone else's CUDA graph
- * capture, inside an allocator or framework that owns all device memory, or
- * in a latency-bound loop where cudaMalloc's implicit synchronisation is not
- * acceptable.  It runs ONE Swendsen-Wang sweep k of an L x L lattice on
- * caller-owned DEVICE buffers, and all its scratch memory sits in one
- * fixed-size array inside the library (about 3 MiB per GPU, reserved on
- * every GPU that loads the library until the process exits), so it calls no
- * cudaMalloc or cudaFree.
+ * The paper has no counterpart to this call.  It exists for callers that may
+ * not, or cannot, allocate device memory: a framework or memory pool that
+ * owns all device memory and forbids foreign cudaMalloc, code running from an
+ * allocator hook or a host callback, or a real-time loop where cudaMalloc's
+ * implicit device synchronisation and latency are not acceptable.  It runs
+ * ONE Swendsen-Wang sweep k of an L x L lattice on caller-owned DEVICE
+ * buffers, and all its scratch memory sits in one fixed-size array inside
+ * the library (2,755,328 bytes = 2.63 MiB, reserved on every GPU that loads
+ * the library until the process exits), so it calls no cudaMalloc or
+ * cudaFree.
  *   spin_in   L*L spins (0/1) before the sweep
- *   spin_out  L*L spins after the sweep (may equal spin_in)
- *   labels_out L*L labels of the sweep (cluster roots, minimum site index)
- *   obs_out   one sw_obs of the sweep (the call zeroes it first)
+ *   spin_out  L*L spins after the sweep; equal to spin_in, or not
+ *             overlapping it at all; 8-byte aligned
+ *   labels_out L*L labels of the sweep (cluster roots, minimum site index);
+ *             16-byte aligned
+ *   obs_out   one sw_obs of the sweep (the call zeroes it first); 8-byte
+ *             aligned
  *   threshold the bond threshold t in [0, 2^32] (see sw_threshold)
  *   seed, sweep  the Philox key and the sweep index k of the sweep
  *   stream    a cudaStream_t (NULL: the legacy default stream); the call is
  *             asynchronous on it
- * Results equal sw_sweep on a lattice with the same spins, seed, threshold
- * and sweep index.  L above SW_STATIC_MAX_L (or below 2), a threshold above
- * 2^32 or a NULL buffer: SW_ERR_ARG.  The one array is shared by every call:
- * calls that overlap on the GPU (other streams, other threads) race; run them
- * one after another.  The first call on a device sets the array up (looks up
- * its device address, raises a kernel's shared-memory limit): make it before
- * any stream capture starts. */
+ * Buffers from cudaMalloc (256-byte aligned) meet every alignment above; a
+ * view at an offset into one may not.  Results equal sw_sweep on a lattice
+ * with the same spins, seed, threshold and sweep index.  Errors, all
+ * returned before anything is enqueued: SW_ERR_ARG for L above
+ * SW_STATIC_MAX_L (or below 2), a threshold above 2^32, a NULL buffer, a
+ * misaligned buffer, or spin buffers that overlap without being equal.  The
+ * one array is shared by every call: calls that overlap on the GPU (other
+ * streams, other threads) race; run them one after another.  The first call
+ * on a device sets the array up for that device (looks up its device address
+ * and raises a kernel's shared-memory limit while the device is current):
+ * make it before any stream capture starts. */
 #define SW_STATIC_MAX_L 1024
 int sw_sweep_static(const uint8_t *spin_in, uint8_t *spin_out, int32_t *labels_out, sw_obs *obs_out,
                     int32_t L, uint64_t threshold, uint64_t seed, uint64_t sweep, void *stream);

@@ -35,7 +35,10 @@ constexpr int CROSS_WORDS = 8;    // per tile: 4 words right-edge bits, 4 words 
 // 30-bit global roots: the GPU path supports N = L*L <= 2^30.
 constexpr uint32_t ROOT_MASK = 0x3FFFFFFFu;
 constexpr uint32_t FINAL_SPIN = 0x40000000u;
-constexpr uint32_t KEY_NONE = 0x3FFFFFFFu;   // an edge slot past the tile's sites
+// A node key is a 30-bit site index (bits 0-29) plus KEY_REP; an edge slot
+// past the tile's sites holds KEY_NONE, outside that range, so it differs
+// from every real key up to site 2^30 - 1 (the corner of an L = 32768 lattice).
+constexpr uint32_t KEY_NONE = 0x80000000u;
 constexpr uint32_t KEY_REP = 0x40000000u;    // the node represents its piece
 constexpr uint32_t KEY_MASK = 0x3FFFFFFFu;
 
@@ -1555,6 +1558,48 @@ static __global__ void k_job_init(uint8_t *spin, int64_t N, uint32_t key0, uint3
     }
     if (i < n_obs) obs[i] = 0ull;
     if (i == 0) *thr_dev = thr;
+}
+
+// Integer ceiling of the bond step: nblocks BOND-stream Philox blocks
+// (counters 0 .. nblocks-1 of sweep 0), four in flight per thread as in the
+// tile kernel's bond draws, all words xored together and into *out so that
+// no draw can be dropped.  A grid-stride loop over a grid that fills the SMs.
+static __global__ void __launch_bounds__(256) k_philox_rate(int64_t nblocks, uint32_t key0, uint32_t key1,
+                                                            uint32_t *out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0u;
+    for (; i + 3 * stride < nblocks; i += 4 * stride) {
+        const U4 r0 = philox4x32_10((uint32_t)i, 0u, 0u, STREAM_BOND, key0, key1);
+        const U4 r1 = philox4x32_10((uint32_t)(i + stride), 0u, 0u, STREAM_BOND, key0, key1);
+        const U4 r2 = philox4x32_10((uint32_t)(i + 2 * stride), 0u, 0u, STREAM_BOND, key0, key1);
+        const U4 r3 = philox4x32_10((uint32_t)(i + 3 * stride), 0u, 0u, STREAM_BOND, key0, key1);
+        acc ^= r0.x ^ r0.y ^ r0.z ^ r0.w ^ r1.x ^ r1.y ^ r1.z ^ r1.w;
+        acc ^= r2.x ^ r2.y ^ r2.z ^ r2.w ^ r3.x ^ r3.y ^ r3.z ^ r3.w;
+    }
+    for (; i < nblocks; i += stride) {
+        const U4 r = philox4x32_10((uint32_t)i, 0u, 0u, STREAM_BOND, key0, key1);
+        acc ^= r.x ^ r.y ^ r.z ^ r.w;
+    }
+    acc = __reduce_xor_sync(0xFFFFFFFFu, acc);
+    if ((threadIdx.x & 31) == 0) atomicXor(out, acc);
+}
+
+// L2 copy ceiling: reps passes of dst[i] = src[i] ^ pass over n 16-byte
+// words, loads and stores cached in L2 only (ld/st .cg), so a working set
+// that fits L2 is read and written there after the first pass.
+static __global__ void __launch_bounds__(256) k_l2_rate(const uint4 *src, uint4 *dst, int64_t n, int32_t reps)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int32_t r = 0; r < reps; ++r) {
+        for (int64_t i = i0; i < n; i += stride) {
+            uint4 v = __ldcg(src + i);
+            v.x ^= (uint32_t)r;
+            __stcg(dst + i, v);
+        }
+    }
 }
 
 // Sets *bad if any of the n bytes is not 0 or 1.

@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -24,17 +25,25 @@ using namespace swg;
 // ---- the kernel launches (declared in sw_launch.cuh)
 namespace swg {
 
+// Raises the tile kernels' dynamic shared-memory limit.  The attribute is
+// per device, so it is set once for every device, while that device is
+// current; one mutex guards the record for all callers.
+constexpr int PREP_MAX_DEVICES = 64;
 template <int TH>
 cudaError_t tile_prepare()
 {
-    static bool done = false;
-    static cudaError_t err = cudaSuccess;
-    if (!done) {
-        const void *fn[2] = {(const void *)k_tile<TH, 0>, (const void *)k_tile<TH, FEAT_TILE>};
-        for (int f = 0; f < 2 && err == cudaSuccess; ++f)
-            err = cudaFuncSetAttribute(fn[f], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<TH>(true));
-        done = true;
-    }
+    static std::mutex mu;
+    static bool done[PREP_MAX_DEVICES] = {};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= PREP_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    const void *fn[2] = {(const void *)k_tile<TH, 0>, (const void *)k_tile<TH, FEAT_TILE>};
+    for (int f = 0; f < 2 && err == cudaSuccess; ++f)
+        err = cudaFuncSetAttribute(fn[f], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<TH>(true));
+    if (err == cudaSuccess) done[dev] = true;
     return err;
 }
 
@@ -955,6 +964,40 @@ int sw_load(sw_ctx *ctx, const void *host_buf, uint64_t bytes)
         SW_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     ctx->swept = false;   // labels and bonds come back with the next sweep
+    return SW_OK;
+}
+
+int sw_bench_philox(int64_t nblocks, uint64_t seed, uint32_t *out_dev, void *stream)
+{
+    if (!out_dev || nblocks < 0 || nblocks > ((int64_t)1 << 32)) return SW_ERR_ARG;
+    if ((uintptr_t)out_dev & 3u) return SW_ERR_ARG;
+    cudaGetLastError();
+    int dev = 0, sms = 0;
+    SW_CUDA(cudaGetDevice(&dev));
+    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t want = (nblocks + 255) / 256;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+    k_philox_rate<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(nblocks, (uint32_t)seed,
+                                                                       (uint32_t)(seed >> 32), out_dev);
+    SW_CUDA(cudaGetLastError());
+    return SW_OK;
+}
+
+int sw_bench_l2(const void *src_dev, void *dst_dev, int64_t bytes, int32_t reps, void *stream)
+{
+    if (!src_dev || !dst_dev || bytes <= 0 || (bytes & 15) || reps < 1) return SW_ERR_ARG;
+    if (((uintptr_t)src_dev & 15u) || ((uintptr_t)dst_dev & 15u)) return SW_ERR_ARG;
+    const uintptr_t a0 = (uintptr_t)src_dev, b0 = (uintptr_t)dst_dev, nb = (uintptr_t)bytes;
+    if (a0 < b0 + nb && b0 < a0 + nb) return SW_ERR_ARG;
+    cudaGetLastError();
+    int dev = 0, sms = 0;
+    SW_CUDA(cudaGetDevice(&dev));
+    SW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t n = bytes / 16;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8));
+    k_l2_rate<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const uint4 *>(src_dev),
+                                                                   static_cast<uint4 *>(dst_dev), n, reps);
+    SW_CUDA(cudaGetLastError());
     return SW_OK;
 }
 

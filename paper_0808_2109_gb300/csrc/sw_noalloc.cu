@@ -2,12 +2,11 @@
 // device buffers, with every piece of scratch memory in a fixed array that
 // is part of the loaded library, so the call allocates nothing.
 //
-// Who needs this: code that runs where device allocation is not allowed or
-// not safe -- inside a region being captured into a CUDA graph by someone
-// else, from a callback or a custom allocator hook, under a framework that
-// owns all device memory and forbids foreign cudaMalloc, or in a real-time
-// loop where cudaMalloc's implicit synchronisation and latency are not
-// acceptable.
+// Who needs this: callers that may not, or cannot, call cudaMalloc -- a
+// framework or memory pool that owns all device memory and forbids foreign
+// allocations, code running from an allocator hook or a host callback, or a
+// real-time loop where cudaMalloc's implicit device synchronisation and
+// latency are not acceptable.
 //
 // Every other buffer the sweep touches (site codes, bond bits, border
 // nodes) is fully rewritten by each sweep before it is read, so only the
@@ -16,14 +15,17 @@
 //
 // Costs and rules:
 //   - SW_STATIC_MAX_L x SW_STATIC_MAX_L is the largest lattice; the array
-//     (about 3 MiB) stays reserved on every GPU that loads the library until
-//     the process exits.
+//     (SCRATCH_BYTES below: 2,755,328 bytes, 2.63 MiB) stays reserved on
+//     every GPU that loads the library until the process exits.
 //   - All calls share the one array: two calls that overlap on the GPU (on
 //     different streams, or from different threads) race and corrupt each
 //     other.  Serialise them.
 //   - The first call on a device looks the array's device address up
-//     (cudaGetSymbolAddress) and raises the tile kernel's shared-memory limit;
-//     make that first call before any stream capture begins.
+//     (cudaGetSymbolAddress) and raises the tile kernel's shared-memory limit
+//     on that device; make that first call before any stream capture begins.
+//   - The kernels store spins 8 bytes, labels 16 bytes and observables 8
+//     bytes at a time: spin_out must be 8-byte, labels_out 16-byte and
+//     obs_out 8-byte aligned (buffers from cudaMalloc are 256-byte aligned).
 #include "swgpu.h"
 #include "sw_device.cuh"
 #include "sw_internal.h"
@@ -53,6 +55,7 @@ constexpr size_t OFF_NPAR = OFF_CROSS + al((size_t)MAX_TILES_STATIC * CROSS_WORD
 constexpr size_t OFF_NKEY = OFF_NPAR + al((size_t)MAX_TILES_STATIC * S_STATIC * sizeof(int32_t));
 constexpr size_t OFF_NFINAL = OFF_NKEY + al((size_t)MAX_TILES_STATIC * S_STATIC * sizeof(int32_t));
 constexpr size_t SCRATCH_BYTES = OFF_NFINAL + al((size_t)MAX_TILES_STATIC * S_STATIC * sizeof(uint32_t));
+static_assert(SCRATCH_BYTES == 2755328, "the size quoted in the comments and the header");
 
 // The scratch memory itself: file scope, fixed size, no allocation.
 static __device__ __align__(256) unsigned char g_static_scratch[SCRATCH_BYTES];
@@ -100,6 +103,14 @@ extern "C" int sw_sweep_static(const uint8_t *spin_in, uint8_t *spin_out, int32_
     if (!spin_in || !spin_out || !labels_out || !obs_out) return SW_ERR_ARG;
     if (L < 2 || L > SW_STATIC_MAX_L) return SW_ERR_ARG;
     if (threshold > ((uint64_t)1 << 32)) return SW_ERR_ARG;
+    // the widths of the kernels' stores (a misaligned one would fault on the GPU)
+    if (((uintptr_t)spin_out & 7u) || ((uintptr_t)labels_out & 15u) || ((uintptr_t)obs_out & 7u))
+        return SW_ERR_ARG;
+    // spin_in is copied to spin_out first: the two must be the same buffer
+    // or not overlap at all
+    const uintptr_t n_bytes = (uintptr_t)L * (uintptr_t)L;
+    const uintptr_t a0 = (uintptr_t)spin_in, b0 = (uintptr_t)spin_out;
+    if (a0 != b0 && a0 < b0 + n_bytes && b0 < a0 + n_bytes) return SW_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SW_ERR_CUDA;
     unsigned char *scratch = nullptr;

@@ -164,6 +164,8 @@ SIGNATURES = {
     "sw_server_get_stats": ([_P, _P], ctypes.c_int),
     "sw_autotune": ([_i32, _dbl, _P], ctypes.c_int),
     "sw_sweep_static": ([_P, _P, _P, _P, _i32, _u64, _u64, _u64, _P], ctypes.c_int),
+    "sw_bench_philox": ([_i64, _u64, _P, _P], ctypes.c_int),
+    "sw_bench_l2": ([_P, _P, _i64, _i32, _P], ctypes.c_int),
 }
 
 
@@ -371,6 +373,23 @@ def sw_sweep_static(spin_in: int, spin_out: int, labels_out: int, obs_out: int, 
                                  ctypes.c_void_p(labels_out), ctypes.c_void_p(obs_out), L,
                                  threshold, seed, sweep, ctypes.c_void_p(raw) if raw else None),
            "sw_sweep_static")
+
+
+def sw_bench_philox(nblocks: int, seed: int, out_dev: int, stream=None) -> None:
+    """Draw nblocks BOND-stream Philox blocks on the device, xored into the
+    device word at out_dev (e.g. ``tensor.data_ptr()``); asynchronous on
+    stream.  Times the integer ceiling of the bond step."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().sw_bench_philox(nblocks, seed, ctypes.c_void_p(out_dev), ctypes.c_void_p(raw) if raw else None),
+           "sw_bench_philox")
+
+
+def sw_bench_l2(src_dev: int, dst_dev: int, nbytes: int, reps: int, stream=None) -> None:
+    """reps passes of dst = src ^ pass over nbytes of device memory, cached in
+    L2 only; asynchronous on stream.  Times the L2 copy ceiling."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().sw_bench_l2(ctypes.c_void_p(src_dev), ctypes.c_void_p(dst_dev), nbytes, reps,
+                             ctypes.c_void_p(raw) if raw else None), "sw_bench_l2")
 
 
 def sw_autotune(L: int, T: float) -> int:

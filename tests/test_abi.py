@@ -70,3 +70,26 @@ def test_product_path_does_not_import_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "sw_oracle" not in src, f
+
+
+def test_static_sweep_rejects_misaligned_or_overlapping_buffers(cuda_lib):
+    """sw_sweep_static checks its caller-owned buffers on the host before it
+    enqueues anything: the kernels store spins 8, labels 16 and observables
+    8 bytes at a time, and the input spins are copied to the output first.
+    The addresses below are never dereferenced (the call returns first), so
+    this runs without a GPU."""
+    from paper_0808_2109_gb300 import swgpu
+    L, thr = 64, 1 << 31
+    base = 1 << 20        # 256-byte aligned stand-in addresses
+    spin_in, spin_out, labels, obs = base, base + 0x10000, base + 0x20000, base + 0x40000
+    bad = [
+        (spin_in, spin_out + 4, labels, obs),      # spins out not 8-byte aligned
+        (spin_in, spin_out, labels + 8, obs),      # labels not 16-byte aligned
+        (spin_in, spin_out, labels, obs + 4),      # observables not 8-byte aligned
+        (spin_in, spin_in + 64, labels, obs),      # spin buffers overlap, not equal
+        (spin_in + 64, spin_in, labels, obs),
+    ]
+    for args in bad:
+        with pytest.raises(swgpu.SwError) as e:
+            swgpu.sw_sweep_static(*args, L, thr, 1, 0)
+        assert e.value.code == swgpu.SW_ERR_ARG, args

@@ -114,51 +114,50 @@ def test_L16384_first_sweep_bit_exact(sw, orc):
         np.testing.assert_array_equal(lat.bonds(), ref.bond)
 
 
-def _check_sweep_properties(orc, L, seed, k, thr, spins, labels, bonds, o):
-    """Properties of any correct sweep k, at any size: labels are min roots,
-    bonded links join sites of one cluster, every bonded link drew u < t,
-    each cluster has one spin, and the observables match the fields."""
-    N = L * L
-    i = np.arange(N, dtype=np.int64)
-    assert (labels <= i).all()
-    assert (labels[labels] == labels).all()
-    x, y = i % L, i // L
-    right = y * L + (x + 1) % L
-    down = ((y + 1) % L) * L + x
-    br = (bonds & 1).astype(bool)
-    bd = (bonds & 2).astype(bool)
-    assert (labels[br] == labels[right[br]]).all()
-    assert (labels[bd] == labels[down[bd]]).all()
-    assert (spins == spins[labels]).all()
-    sig = 2 * spins.astype(np.int64) - 1
-    assert int(o["mag"]) == int(sig.sum())
-    assert int(o["bond_sum"]) == int((sig * sig[right]).sum() + (sig * sig[down]).sum())
-    assert int(o["nclusters"]) == int((labels == i).sum())
-    assert int(o["nbonds"]) == int(br.sum() + bd.sum())
-    # sampled bonded links: their Philox word is below the threshold
-    rng = np.random.default_rng(k)
-    idx = np.flatnonzero(br)
-    samp = rng.choice(idx, size=min(20000, idx.size), replace=False)
-    l = 2 * samp
-    ctr = np.zeros((samp.size, 4), dtype=np.uint32)
-    ctr[:, 0] = l // 4
-    ctr[:, 1] = k & 0xFFFFFFFF
-    ctr[:, 2] = k >> 32
-    ctr[:, 3] = orc.STREAM_BOND
-    w = orc.philox(ctr, [seed & 0xFFFFFFFF, seed >> 32])
-    u = w[np.arange(samp.size), l % 4].astype(np.uint64)
-    assert (u < np.uint64(thr)).all()
+def _check_last_sweep_with_oracle(orc, L, seed, k, thr, prev_spins, spins, labels, bonds, o):
+    """The oracle as checker of sweep k, step by step on the GPU's own
+    intermediates (Sec. I steps 1-4): the bonds it draws on the spins before
+    the sweep, the clusters of the GPU's bonds, the flip of the GPU's labels,
+    and the observables of the GPU's spins.  Each is compared bit for bit, so
+    a labelling that over-merges or misses a bond, or a spin that is not its
+    root's SPIN bit, fails here at any size."""
+    want_bonds, nb = orc.bonds(L, seed, k, thr, prev_spins)
+    np.testing.assert_array_equal(bonds, want_bonds, err_msg="bonds of the last sweep")
+    want_labels, nc = orc.label(L, bonds)
+    np.testing.assert_array_equal(labels, want_labels, err_msg="clusters of the GPU's bonds")
+    np.testing.assert_array_equal(spins, orc.assign(L, seed, k, labels), err_msg="flip of the GPU's labels")
+    bs, mag = orc.measure(L, spins)
+    assert (int(o["bond_sum"]), int(o["mag"]), int(o["nclusters"]), int(o["nbonds"])) == (bs, mag, nc, nb)
 
 
 @pytest.mark.parametrize("L,T,n", [(4096, 2.0, 200), (4096, 2.269185, 200), (4096, 3.0, 200),
                                    (16384, 2.269185, 50)])
-def test_full_workloads_properties(sw, orc, L, T, n):
-    """The full configured runs (200 sweeps at L=4096, 50 at L=16384): the
-    last sweep satisfies every property the method fixes."""
+def test_full_workloads_last_sweep_by_oracle(sw, orc, L, T, n):
+    """The full configured runs (200 sweeps at L=4096, 50 at L=16384) in the
+    benchmark's launch configuration (autotuned tile height): the last sweep
+    is recomputed by the oracle from the spins before it."""
     thr = orc.threshold_T(1.0, T)
-    with sw.Lattice(L, T=T, seed=1) as lat:
-        lat.sweep(n)
+    with sw.Lattice(L, T=T, seed=1, tile_h=sw.sw_autotune(L, T)) as lat:
+        lat.sweep(n - 1)
+        prev = lat.spins()
+        lat.sweep(1)
         obs = lat.observables()
         assert len(obs) == n and (obs["threshold"] == thr).all()
-        _check_sweep_properties(orc, L, 1, n - 1, thr, lat.spins(), lat.labels(), lat.bonds(),
-                                obs[-1])
+        _check_last_sweep_with_oracle(orc, L, 1, n - 1, thr, prev, lat.spins(), lat.labels(), lat.bonds(),
+                                      obs[-1])
+
+
+def test_L32768_first_sweep_bit_exact(sw, orc):
+    """The largest lattice the GPU path admits: N = 2^30 sites, so the corner
+    site's index 2^30 - 1 is the largest 30-bit root and key.  The first sweep
+    from the hot start equals the oracle's."""
+    L, T = 32768, 2.269185
+    ref = orc.sw_chain(L, 1.0, T, 1)
+    ref_obs = ref.run(1)
+    with sw.Lattice(L, T=T, seed=1) as lat:
+        lat.sweep(1)
+        assert_obs_equal(lat.observables(), ref_obs)
+        np.testing.assert_array_equal(lat.spins(), ref.spin)
+        np.testing.assert_array_equal(lat.labels(), ref.label)
+        np.testing.assert_array_equal(lat.bonds(), ref.bond)
+

@@ -1,6 +1,7 @@
 """sw_sweep_static: one sweep with no device allocation (for callers that
-must not allocate, e.g. inside another component's graph capture or under a
-framework that owns all device memory), checked against sw_sweep.
+may not call cudaMalloc, e.g. under a framework or memory pool that owns all
+device memory, or in a loop where cudaMalloc's implicit synchronisation is not
+acceptable), checked against sw_sweep.
 
 Two calls in a row -- the second in place on the first one's output -- must
 give exactly the spins, labels and observables of two sweeps of a lattice
