@@ -4,9 +4,13 @@
 Workload: plain SW on the 2D periodic Ising lattice, L = 16384 (268M sites),
 J = 1, T = 2.269185 (critical), hot start; one step = 50 sweeps, the
 configured run length of that lattice.  Metric: site updates per ns over the
-whole job (all ranks), with the lattice resident on the device.
+whole job (all ranks), with the lattice resident on the device, beside the
+achieved HBM GB/s of the dominant kernel.  The same line carries the batched
+512-replica mix (against the same replicas run one at a time) and the served
+Poisson trace (p50/p99 latency beside throughput).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+  python bench.py --workload configs   # every configured run, oracle timed beside it
 
 N > 1 runs under torchrun, one independent lattice per GPU (replicas: the
 single-lattice path has no exchange step), timed between barriers, max over
@@ -32,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "SW site updates/ns at T_c (L=16384)"
 L2_BYTES = 129 << 20     # GB300 L2
 UNIT = "site-updates/ns"
-WIDE_MULS_PER_PHILOX = 20          # 10 rounds x 2 (32x32->64) products
+ALG_BYTES_PER_SITE = 10            # old spin in, label out, label in, new spin out
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_tile_L16384_Tc.md")
 LAUNCHES_PER_SWEEP = 4             # tile kernel, merge union, pointer jumping, resolve
 
@@ -45,7 +49,9 @@ def parse_args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-solo comparison")
-    ap.add_argument("--workload", default="plain", choices=["plain", "serve", "potts"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "serve", "potts", "configs", "batch64"])
+    ap.add_argument("--no-serve", action="store_true", help="skip the served trace")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="--workload serve: arrivals per second")
     ap.add_argument("--lattice", type=int, default=0, help="profiling only: another L")
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: sweeps per step")
     ap.add_argument("--temperature", type=float, default=0.0, help="profiling only: another T")
@@ -156,13 +162,6 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- roofline
-def alu_peak_tmul(sm_count: int, sm_max_mhz: float) -> float:
-    """Integer multiply ceiling in T (32x32->64 products)/s: the FMA pipe
-    issues 16 lanes of IMAD per SM sub-partition per clock (64 per SM) and a
-    full 64-bit product takes two of them."""
-    return sm_count * 64 / 2 * sm_max_mhz * 1e6 / 1e12
-
-
 def philox_calls_per_start(L: int) -> int:
     """Philox blocks the tile kernel draws to start one sweep: per 128-wide
     tile row, 64 BOND blocks (one per two sites; 128 on rows that begin on an
@@ -203,6 +202,47 @@ def measured_peaks():
         return {}
 
 
+def hbm_peak_gbs():
+    """The measured HBM copy bandwidth (driver-written), else the fallback."""
+    pk = measured_peaks()
+    if "hbm_gbs" in pk:
+        return float(pk["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs: STREAM-style copy)"
+    return 6800.0, "of fallback (6.8 TB/s, an earlier GB300 copy measurement)"
+
+
+def time_on_stream(torch, stream, fn, reps: int, warm: int = 2) -> float:
+    """Average ms of fn() over reps calls, CUDA events on stream."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_philox_peak(torch, swgpu, stream) -> float:
+    """Philox4x32-10 blocks/s of the library's probe (sw_bench_philox): 2^32
+    BOND blocks per launch on a grid that fills the GPU."""
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    n = (1 << 32)
+    ms = time_on_stream(torch, stream, lambda: swgpu.sw_bench_philox(n, 1, out.data_ptr(), stream), 5)
+    return n / (ms * 1e-3)
+
+
+def measure_l2_peak(torch, swgpu, stream, nbytes: int = 16 << 20, reps: int = 400) -> float:
+    """L2 copy bandwidth (GB/s, read + write) of the library's probe
+    (sw_bench_l2) on two 16 MiB buffers: 32 MiB in all, resident in L2."""
+    src = torch.ones(nbytes // 4, dtype=torch.int32, device="cuda")
+    dst = torch.empty_like(src)
+    ms = time_on_stream(torch, stream,
+                        lambda: swgpu.sw_bench_l2(src.data_ptr(), dst.data_ptr(), nbytes, reps, stream), 3)
+    return 2.0 * nbytes * reps / (ms * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------ cpu baseline
 def cpu_baseline_oracle(w):
     """The oracle as it stands, single-threaded, on one sweep of the lattice."""
@@ -216,6 +256,53 @@ def cpu_baseline_oracle(w):
             "sample": f"1 sweep of the L={w.L} lattice from the hot start ({dt:.1f} s)"}
 
 
+def _oracle_replicas(args):
+    """Worker: run each (L, T, seed, sweeps) replica with the oracle; returns
+    the site updates done (runs in a spawned process)."""
+    import oracle
+    n = 0
+    for L, T, seed, sweeps in args:
+        oracle.sw_chain(L, 1.0, T, seed).run(sweeps)
+        n += L * L * sweeps
+    return n
+
+
+def cpu_baseline_batch(pool, jobs, sample_replicas: int = 64, sweeps: int = 20):
+    """The oracle on a bounded sample of the batch mix: the first
+    `sample_replicas` replicas of the manifest, `sweeps` sweeps each, on one
+    core and on all host cores (one replica per process at a time, a pool
+    started before the first GPU call)."""
+    import oracle
+    oracle.build()
+    sample = [(j.L, j.T, j.seed, sweeps) for j in jobs[:sample_replicas]]
+    t0 = time.perf_counter()
+    n1 = _oracle_replicas(sample)
+    t1 = time.perf_counter() - t0
+    out = {"value": round(n1 / (t1 * 1e9), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{len(sample)} replicas of the mix (first of the manifest), {sweeps} sweeps each, "
+                     f"one core ({t1:.1f} s)"}
+    if pool is not None:
+        ncores = pool._processes
+        pool.map(_oracle_replicas, [[]] * ncores)          # workers up before timing
+        t0 = time.perf_counter()
+        nall = sum(pool.map(_oracle_replicas, [[a] for a in sample], chunksize=1))
+        tall = time.perf_counter() - t0
+        out["all_cores"] = {"value": round(nall / (tall * 1e9), 6), "unit": UNIT, "cores": ncores,
+                            "kind": "oracle", "sample": f"the same {len(sample)} replicas, one per process "
+                                                         f"({tall:.1f} s)"}
+    return out
+
+
+def start_oracle_pool():
+    """A spawn pool of one process per host core, for the all-cores oracle
+    baseline (started before any GPU call)."""
+    import multiprocessing as mp
+    try:
+        return mp.get_context("spawn").Pool(os.cpu_count() or 1)
+    except OSError:
+        return None
+
+
 # --------------------------------------------------------------- our arm
 def run_gb300(args):
     import numpy as np
@@ -223,13 +310,16 @@ def run_gb300(args):
     from paper_0808_2109_gb300 import _build, swgpu, workloads
 
     rank, world, local = dist_env()
+    profiling = bool(args.lattice or args.sweeps or args.temperature)
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_batch and not profiling:
+        pool = start_oracle_pool()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
     w = workloads.LARGE
-    profiling = bool(args.lattice or args.sweeps or args.temperature)
     if profiling:
         w = workloads.Plain(args.lattice or w.L, args.temperature or w.T, args.sweeps or w.sweeps, w.seed)
     K, W = args.steps, args.warmup
@@ -275,25 +365,7 @@ def run_gb300(args):
     st = lat.profile_read()
     lat.profile(False)
     lat.observables()
-    tile_avg_ms = st["tile_ms"] / st["tile_launches"]
-    starts = prof_steps * w.sweeps
-    muls = starts * philox_calls_per_start(w.L) * WIDE_MULS_PER_PHILOX
-    achieved = muls / (st["tile_ms"] * 1e-3) / 1e12
-    props = torch.cuda.get_device_properties(local)
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = alu_peak_tmul(props.multi_processor_count, sm_max)
-    traffic = profile_traffic(kernel_source_sha(), tile_h)
-    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
-                "unit": "T int32 products/s (32x32->64, Philox4x32-10)",
-                "frac": round(achieved / peak, 4),
-                "traffic": (round(traffic * st["tile_launches"] / max(st["tile_launches"], 1))
-                            if traffic is not None else None),
-                "kernel": f"k_tile<{tile_h}> (fused finish/start of a sweep)",
-                "tile_kernel_avg_ms": round(tile_avg_ms, 4),
-                "merge_group_avg_ms": round(st["merge_ms"] / max(st["merge_groups"], 1), 4),
-                "peak_source": f"derived: {props.multi_processor_count} SMs x 64 IMAD lanes/clk / 2 "
-                               f"per 64-bit product x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"}
+    roofline = tile_roofline(torch, swgpu, stream, w, tile_h, st, ms / (K * w.sweeps))
 
     # ---- end to end through the public API with pinned host buffers
     e2e_steps = max(1, min(K, 5))
@@ -314,10 +386,14 @@ def run_gb300(args):
            "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + w.sweeps * swgpu.OBS_DTYPE.itemsize,
            "steps": e2e_steps}
     del o
+    lat.close()
 
     batched = None
     if not args.no_batch and not profiling:
-        batched = run_batch_vs_solo(swgpu, workloads, rank, world, barrier)
+        batched = run_batch_vs_solo(swgpu, workloads, rank, world, barrier, pool)
+    served = None
+    if not args.no_serve and not profiling and rank == 0 and world == 1:
+        served = run_served(swgpu, workloads, local, args.serve_seconds)
 
     out = None
     if rank == 0:
@@ -331,24 +407,72 @@ def run_gb300(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
             "config": workload_config(w, {"parallelism": f"replicas x{world}",
-                                          "seeds": f"{w.seed}..{w.seed + world - 1}",
-                                          "tile_h": tile_h}),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+                                          "seeds": f"{w.seed}..{w.seed + world - 1}"}),
+            "tile_h": tile_h, "hbm_gbs_achieved": roofline["achieved"],
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "served": served,
             "gpu_launches": K * (LAUNCHES_PER_SWEEP * w.sweeps + 1),
             "clocks": clk, "impl": "gb300",
         }
-    lat.close()
+    if pool is not None:
+        pool.terminate()
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
 
 
+def tile_roofline(torch, swgpu, stream, w, tile_h, st, ms_per_sweep):
+    """Both ceilings of the dominant kernel (the tile kernel), each measured
+    in this run: HBM (the algorithmic 10 B/site of a sweep against the
+    measured copy bandwidth; the DRAM bytes ncu counted per launch beside it)
+    and the integer pipe (the Philox blocks a launch draws against the
+    library's Philox probe).  Neither is what binds the kernel: it issues
+    instructions on about two thirds of its cycles and waits on dependent
+    shared-memory loads and barriers in the union-find (the ncu summaries in
+    profiles/)."""
+    N = w.L * w.L
+    tile_s = st["tile_ms"] / st["tile_launches"] * 1e-3
+    peak, peak_src = hbm_peak_gbs()
+    achieved = ALG_BYTES_PER_SITE * N / tile_s / 1e9
+    traffic = profile_traffic(kernel_source_sha(), tile_h)
+    blocks = philox_calls_per_start(w.L)
+    philox_peak = measure_philox_peak(torch, swgpu, stream)
+    l2_peak = measure_l2_peak(torch, swgpu, stream)
+    alu_achieved = blocks / tile_s
+    sweep_gbs = ALG_BYTES_PER_SITE * N / (ms_per_sweep * 1e-3) / 1e9
+    return {
+        "bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+        "frac": round(achieved / peak, 4),
+        "traffic": traffic,
+        "peak_source": peak_src,
+        "kernel": f"k_tile<{tile_h}> (fused finish/start of a sweep)",
+        "bytes_per_site_algorithmic": ALG_BYTES_PER_SITE,
+        "units_per_launch": N,
+        "tile_kernel_avg_ms": round(tile_s * 1e3, 4),
+        "merge_group_avg_ms": round(st["merge_ms"] / max(st["merge_groups"], 1), 4),
+        "dram_gbs_measured": round(traffic / tile_s / 1e9, 1) if traffic is not None else None,
+        "frac_dram_measured": round(traffic / tile_s / 1e9 / peak, 4) if traffic is not None else None,
+        "sweep_frac_hbm": round(sweep_gbs / peak, 4),
+        "alu": {"achieved": round(alu_achieved / 1e9, 2), "peak": round(philox_peak / 1e9, 2),
+                "unit": "G Philox4x32-10 blocks/s", "frac": round(alu_achieved / philox_peak, 4),
+                "blocks_per_site": round(blocks / N, 6),
+                "site_updates_per_ns_ceiling": round(philox_peak / (blocks / N) / 1e9, 1),
+                "peak_source": "measured in this run: sw_bench_philox, 2^32 BOND blocks per launch"},
+        "l2_gbs_peak": round(l2_peak, 1),
+        "l2_peak_source": "measured in this run: sw_bench_l2, 32 MiB copy resident in L2",
+        "binding": "neither ceiling: instruction issue (about 2/3 of cycles) and dependent shared-memory "
+                   "latency in the union-find, with phase barriers (profiles/k_tile_L4096_full.md)",
+    }
+
+
 # ------------------------------------------------------ batched vs solo
-def run_batch_vs_solo(swgpu, workloads, rank, world, barrier):
+def run_batch_vs_solo(swgpu, workloads, rank, world, barrier, pool=None):
     """The uneven 512-replica mix (500 sweeps each) through the batch server,
-    then the same replicas one at a time through sw_create/sw_sweep, on the
-    same GPU; replicas shard over ranks with no exchange."""
-    jobs = shard_jobs(workloads.batch_manifest(), rank, world)
+    then the same replicas one at a time on the same GPU: once with each
+    lattice created (and destroyed) inside the timed region, once with the
+    lattices created and their sweep graphs captured beforehand (sweeps
+    only).  Replicas shard over ranks with no exchange."""
+    all_jobs = workloads.batch_manifest()
+    jobs = shard_jobs(all_jobs, rank, world)
     specs = [{"L": j.L, "T": j.T, "sweeps": j.sweeps, "seed": j.seed} for j in jobs]
     updates = sum(j.L * j.L * j.sweeps for j in jobs)
     srv = swgpu.Server()
@@ -364,6 +488,7 @@ def run_batch_vs_solo(swgpu, workloads, rank, world, barrier):
     assert all(r is not None and r[0].status == 0 for r in res)
     stats = srv.stats()
     srv.close()
+    # solo, create + sweeps + observables + destroy per replica
     barrier()
     t0 = time.perf_counter()
     for sp in specs:
@@ -372,38 +497,46 @@ def run_batch_vs_solo(swgpu, workloads, rank, world, barrier):
         lat.observables()
         lat.close()
     t_solo = max_over_ranks(time.perf_counter() - t0)
+    # solo, sweeps only: lattices made and their graphs captured beforehand
+    lats = [swgpu.Lattice(sp["L"], T=sp["T"], seed=sp["seed"]) for sp in specs]
+    for lat, sp in zip(lats, specs):
+        lat.sweep(sp["sweeps"])   # captures the graph of this run length
+        lat.sync()
+        lat.observables()
+    barrier()
+    t0 = time.perf_counter()
+    for lat, sp in zip(lats, specs):
+        lat.sweep(sp["sweeps"])
+        lat.observables()         # waits for the lattice's sweeps
+    t_solo_sweeps = max_over_ranks(time.perf_counter() - t0)
+    for lat in lats:
+        lat.close()
     total = updates * world   # equal shares by construction, up to one job
-    return {"replicas": 512, "sweeps": 500, "site_updates": int(total),
-            "value": round(total / (t_batch * 1e9), 3), "unit": UNIT,
-            "solo_value": round(total / (t_solo * 1e9), 3),
-            "speedup_vs_solo": round(t_solo / t_batch, 3),
-            "batch_s": round(t_batch, 3), "solo_s": round(t_solo, 3),
-            "launch_groups": int(stats["launches"]),
-            "timing": "wall clock from submit to last completion (host), max over ranks"}
+    out = {"replicas": 512, "sweeps": 500, "site_updates": int(total),
+           "value": round(total / (t_batch * 1e9), 3), "unit": UNIT,
+           "solo_value": round(total / (t_solo * 1e9), 3),
+           "solo_sweep_only_value": round(total / (t_solo_sweeps * 1e9), 3),
+           "speedup_vs_solo": round(t_solo / t_batch, 3),
+           "speedup_vs_solo_sweep_only": round(t_solo_sweeps / t_batch, 3),
+           "batch_s": round(t_batch, 3), "solo_s": round(t_solo, 3), "solo_sweep_only_s": round(t_solo_sweeps, 3),
+           "launch_groups": int(stats["launches"]),
+           "timing": "wall clock from submit to last completion (host), max over ranks; solo: the same "
+                     "replicas one at a time through sw_create/sw_sweep/sw_observables, with and without "
+                     "creation, graph capture and destruction in the timed region"}
+    if rank == 0 and world == 1 and pool is not None:
+        out["cpu_baseline"] = cpu_baseline_batch(pool, all_jobs)
+    return out
 
 
 # ------------------------------------------------------------------- serve
-def run_serve(args):
-    """The Poisson trace replayed in real time: a client submits each job at
+def serve_trace_run(swgpu, jobs, duration_s):
+    """Replays jobs in real time against a fresh server: each is submitted at
     its arrival time; latency = submit -> finished (server clocks)."""
-    import torch
-    from paper_0808_2109_gb300 import _build, swgpu, workloads
-
-    rank, world, local = dist_env()
-    if rank != 0:
-        return None
-    torch.cuda.set_device(local)
-    _build.build()
-    trace = workloads.serve_trace(duration_s=args.serve_seconds)
-    for L in (32, 64, 128, 256, 512, 1024, 2048, 4096):
-        for T in (2.0, 2.3, 2.6):
-            swgpu.sw_autotune(L, T)
+    import numpy as np
     srv = swgpu.Server()
-    clocks = ClockSampler(local)
-    clocks.start()
     ids = []
     t0 = time.perf_counter()
-    for job in trace:
+    for job in jobs:
         delay = job.arrival_s - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
@@ -415,25 +548,168 @@ def run_serve(args):
         ids += srv.submit([sp], want_obs=False)
     srv.wait_all(0.0)
     wall = time.perf_counter() - t0
-    clk = clocks.stop()
     lat, upd = [], 0
-    for i, job in zip(ids, trace):
+    for i, job in zip(ids, jobs):
         r, _ = srv.poll(i)
         assert r.status == 0
         lat.append(r.queued_s + r.run_s)
         upd += job.L * job.L * job.sweeps
     srv.close()
-    import numpy as np
     lat = np.array(lat)
-    return {"metric": "served SW/PCC site updates/ns (Poisson 200 jobs/s)", "value": round(upd / (wall * 1e9), 3),
-            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "jobs": len(trace),
-            "offered_site_updates_per_ns": round(upd / (args.serve_seconds * 1e9), 3),
+    return {"jobs": len(jobs), "value": round(upd / (wall * 1e9), 3), "unit": UNIT,
+            "offered_site_updates_per_ns": round(upd / (duration_s * 1e9), 3),
             "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4),
                           "p99": round(float(np.percentile(lat, 99)), 4),
                           "max": round(float(lat.max()), 4)},
-            "wall_s": round(wall, 2), "arrival_window_s": args.serve_seconds, "clocks": clk,
-            "config": {"workload": "Poisson 200 jobs/s, L log-uniform [32,4096], sweeps U[10,1000], "
-                                   "80% SW T~U[1.8,3.2], 20% PCC", "data": "synthetic"}}
+            "wall_s": round(wall, 2), "arrival_window_s": duration_s,
+            "drain_s": round(wall - duration_s, 2)}
+
+
+def run_served(swgpu, workloads, local, duration_s, rate=200.0, probe_s=20.0):
+    """The configured Poisson trace (200 jobs/s), then a probe of the rate
+    the server keeps up with: the trace's job mix at 85% of the rate its
+    measured capacity can absorb (capacity / mean work per job), for
+    probe_s seconds.  While the first trace's queue never empties, its
+    aggregate throughput is the server's capacity."""
+    for L in (32, 64, 128, 256, 512, 1024, 2048, 4096):
+        for T in (2.0, 2.3, 2.6):
+            swgpu.sw_autotune(L, T)
+    clocks = ClockSampler(local)
+    clocks.start()
+    trace = workloads.serve_trace(rate_hz=rate, duration_s=duration_s)
+    main = serve_trace_run(swgpu, trace, duration_s)
+    mean_work = sum(j.L * j.L * j.sweeps for j in trace) / len(trace)
+    capacity = main["value"] * 1e9   # site updates/s while the queue is never empty
+    keep_rate = 0.85 * capacity / mean_work
+    probe = serve_trace_run(swgpu, workloads.serve_trace(rate_hz=keep_rate, duration_s=probe_s, rng_seed=20262),
+                            probe_s)
+    probe["rate_jobs_per_s"] = round(keep_rate, 1)
+    main.update({"rate_jobs_per_s": rate, "clocks": clocks.stop(),
+                 "workload": "Poisson arrivals, L log-uniform [32,4096], sweeps U[10,1000], 80% SW T~U[1.8,3.2], "
+                             "20% PCC; lattice state resident on the device, admission by device memory",
+                 "served_jobs_per_s": round(capacity / mean_work, 1),
+                 "keep_up_probe": probe})
+    return main
+
+
+def run_serve(args):
+    """--workload serve: the trace at --serve-rate for --serve-seconds."""
+    import torch
+    from paper_0808_2109_gb300 import _build, swgpu, workloads
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    _build.build()
+    for L in (32, 64, 128, 256, 512, 1024, 2048, 4096):
+        for T in (2.0, 2.3, 2.6):
+            swgpu.sw_autotune(L, T)
+    clocks = ClockSampler(local)
+    clocks.start()
+    trace = workloads.serve_trace(rate_hz=args.serve_rate, duration_s=args.serve_seconds)
+    out = serve_trace_run(swgpu, trace, args.serve_seconds)
+    out.update({"metric": f"served SW/PCC site updates/ns (Poisson {args.serve_rate:g} jobs/s)", "n_gpus": 1,
+                "higher_is_better": True, "clocks": clocks.stop(), "data": "synthetic", "impl": "gb300"})
+    return out
+
+
+# ------------------------------------------------------- configured runs
+def run_configs(args):
+    """Every configured run once on the GPU (CUDA events around one whole
+    run, after one untimed run) with its roofline fraction -- HBM, or L2 when
+    the lattice's state fits L2 -- and the oracle timed beside it on a
+    bounded sample (one core)."""
+    import torch
+    import oracle
+    from paper_0808_2109_gb300 import _build, swgpu, workloads
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    _build.build()
+    oracle.build()
+    stream = torch.cuda.Stream()
+    hbm, _ = hbm_peak_gbs()
+    l2 = measure_l2_peak(torch, swgpu, stream)
+    cases = [("plain", workloads.SMALL, 1000)] + [("plain", r, 2) for r in workloads.REGIMES] + \
+            [("plain", workloads.LARGE, 1), ("pcc", workloads.PCC_RUN, 20)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    rows = []
+    for kind, w, osweeps in cases:
+        L = w.L
+        n = w.sweeps
+        if kind == "pcc":
+            mk = lambda: swgpu.Lattice(L, seed=w.seed, pcc=True)
+            ork = lambda: oracle.pcc_chain(L, w.seed)
+        else:
+            th = swgpu.sw_autotune(L, w.T)
+            mk = lambda: swgpu.Lattice(L, T=w.T, seed=w.seed, tile_h=th)
+            ork = lambda: oracle.sw_chain(L, 1.0, w.T, w.seed)
+        with mk() as lat:
+            lat.set_stream(stream)
+            lat.sweep(n)
+            lat.sync()
+            lat.observables()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.sweep(n)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            lat.observables()
+        rate = L * L * n / (ms * 1e6)
+        state_bytes = L * L * 3 + (L * L) // 4   # spins, site codes, bond bits: the per-site state
+        resident = state_bytes < (96 << 20)
+        peak = l2 if resident else hbm
+        ch = ork()
+        t0 = time.perf_counter()
+        ch.run(osweeps)
+        ot = time.perf_counter() - t0
+        rows.append({"config": (f"PCC L={L} {n} sweeps" if kind == "pcc" else f"SW L={L} T={w.T} {n} sweeps"),
+                     "gpu_site_updates_per_ns": round(rate, 3), "gpu_ms": round(ms, 3),
+                     "roofline": {"bound": "l2" if resident else "hbm",
+                                  "achieved_gbs": round(rate * ALG_BYTES_PER_SITE, 1), "peak_gbs": round(peak, 1),
+                                  "frac": round(rate * ALG_BYTES_PER_SITE / peak, 4)},
+                     "cpu_oracle_1core": {"value": round(L * L * osweeps / (ot * 1e9), 6), "unit": UNIT,
+                                          "sample": f"{osweeps} sweeps from the hot start ({ot:.1f} s)"}})
+    return {"metric": "configured runs: site updates/ns, roofline fraction, oracle beside", "rows": rows,
+            "l2_gbs_peak": round(l2, 1), "hbm_gbs_peak": round(hbm, 1), "clocks": clocks.stop(),
+            "n_gpus": 1, "data": "synthetic", "impl": "gb300"}
+
+
+def run_batch64(args):
+    """Launch gaps of the batched form on small lattices: 512 L=64 replicas
+    through the server, wall clock against the device time of the launches
+    (the sum of kernel times comes from a separate ncu launch list)."""
+    import torch
+    from paper_0808_2109_gb300 import _build, swgpu, workloads
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    _build.build()
+    swgpu.sw_autotune(64, 2.3)
+    specs = [{"L": 64, "T": 2.0 + 0.6 * (r % 32) / 31.0, "sweeps": args.sweeps or 500, "seed": 1000 + r}
+             for r in range(512)]
+    res = {}
+    for rep in range(args.warmup + args.steps):
+        with swgpu.Server() as srv:
+            t0 = time.perf_counter()
+            ids = srv.submit(specs, want_obs=True)
+            srv.wait_all(0.0)
+            dt = time.perf_counter() - t0
+            st = srv.stats()
+        if rep >= args.warmup:
+            res.setdefault("wall_s", []).append(round(dt, 4))
+            res["launch_groups"] = int(st["launches"])
+    upd = 512 * 64 * 64 * (args.sweeps or 500)
+    return {"metric": "batched SW, 512 x L=64 (launch-bound)", "wall_s": res["wall_s"],
+            "value": round(upd / (min(res["wall_s"]) * 1e9), 3), "unit": UNIT,
+            "launch_groups": res["launch_groups"], "n_gpus": 1, "impl": "gb300"}
 
 
 # ------------------------------------------------------------- Potts / 3D
@@ -485,8 +761,7 @@ def run_potts(args):
                          "value": round(n / (ms * 1e6), 3), "ms_per_sweep": round(ms / (SW * args.steps), 4)})
     clk = clocks.stop()
     value = upd / (ms_tot * 1e6)
-    peaks = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm, src = hbm_peak_gbs()
     achieved = value * POTTS_BYTES_PER_SITE   # site-updates/ns x B/site = GB/s
     return {"metric": "Potts/3D SW site updates/ns (four critical lattices)", "value": round(value, 3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -494,16 +769,22 @@ def run_potts(args):
             "config": {"workload": "q-state Potts, hot start, 10 sweeps per step", "cases": rows,
                        "l2": "every lattice larger than L2 (states, labels and bond bytes >= 400 MB)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(hbm, 1), "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "traffic": None,
-                         "kernel": "all five kernels of a sweep",
+                         "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
+                         "kernel": "all kernels of a sweep",
                          "bytes_per_site": POTTS_BYTES_PER_SITE},
             "clocks": clk, "impl": "gb300"}
 
 
 # ---------------------------------------------------------- reference arm
+REF_SAMPLE_L = 4096
+
+
 def run_reference(args):
-    """The CPU oracle, single-threaded, one sweep of an L=4096 lattice of the
-    same configuration per step (an L=16384 sweep takes ~30 s on one core)."""
+    """The CPU oracle, single-threaded, as it stands.  Each step is a bounded
+    sample of the benchmark workload: one sweep of an L=4096 lattice with the
+    workload's J, T, seed and hot start (an L=16384 sweep takes ~17 s on one
+    core, too long for K steps).  The line names the same workload, metric
+    and unit as the GPU arm; its `sample` says what each step timed."""
     from paper_0808_2109_gb300 import workloads
     import oracle
 
@@ -512,7 +793,7 @@ def run_reference(args):
         return None
     oracle.build()
     w = workloads.LARGE
-    Ls = 4096
+    Ls = REF_SAMPLE_L
     chain = oracle.sw_chain(Ls, 1.0, w.T, w.seed)
     for _ in range(args.warmup):
         chain.run(1)
@@ -521,12 +802,15 @@ def run_reference(args):
         chain.run(1)
     dt = time.perf_counter() - t0
     value = Ls * Ls * args.steps / (dt * 1e9)
-    sample = f"one sweep of an L={Ls} lattice at T={w.T} per step, single-threaded oracle"
+    sample = (f"each step: one sweep of an L={Ls} lattice at T={w.T}, J=1, seed {w.seed}, hot start "
+              f"(a bounded sample of the L={w.L} workload), single-threaded oracle")
     return {
         "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "config": workload_config(w, {"sample_L": Ls}), "impl": "reference",
+        "data": "synthetic", "config": workload_config(w, {"parallelism": f"replicas x{world}",
+                                                          "seeds": f"{w.seed}..{w.seed + world - 1}"}),
+        "sample": sample, "site_updates_per_step": Ls * Ls, "impl": "reference",
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -542,6 +826,10 @@ def main():
         out = run_serve(args)
     elif args.workload == "potts":
         out = run_potts(args)
+    elif args.workload == "configs":
+        out = run_configs(args)
+    elif args.workload == "batch64":
+        out = run_batch64(args)
     else:
         out = run_gb300(args)
     if out is not None:
