@@ -551,6 +551,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
     constexpr int SPT = (S + NT - 1) / NT;   // node slots per thread
     constexpr int NQ = TH * TW / 8 / NT;     // 8-site groups per thread
     static_assert(NQ * 8 * NT == TH * TW, "tile sites must split into 8-site groups");
+    static_assert(TH * TWW == NT, "one 32-site word of the tile per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<TH> &sm = *reinterpret_cast<TileSmem<TH> *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
@@ -1155,7 +1156,7 @@ __device__ __forceinline__ const Replica *merge_lattice(const SweepArgs &a, int 
 // W: compiled with the topological rule (lattices with RF_WIND unite their
 // nodes with displacements in nlink); every kernel of the merge has it.
 template <int TH, bool W>
-__global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_union(const SweepArgs a)
+__global__ void __launch_bounds__(MergeCfg<TH>::MT, 64 / ((MergeCfg<TH>::MT + 31) / 32)) k_merge_union(const SweepArgs a)
 {
     using SL = Slots<TH>;
     using MC = MergeCfg<TH>;
@@ -1198,16 +1199,69 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_union(const SweepArg
         const uint32_t kb = (uint32_t)R.nkey[nb[q]] ^ (uint32_t)R.nkey[nb[q] - 1];
         if (((ka | kb) & KEY_MASK) == 0) na[q] = -1;
     }
-    const bool wind = W && (R.flags & RF_WIND);
+    if (W && (R.flags & RF_WIND)) {
 #pragma unroll
-    for (int q = 0; q < MC::EPT; ++q) {
-        if (na[q] < 0) continue;
-        if (wind) {   // a right link moves by (+1, 0), a down link by (0, +1)
+        for (int q = 0; q < MC::EPT; ++q) {
+            if (na[q] < 0) continue;
+            // a right link moves by (+1, 0), a down link by (0, +1)
             const bool right = threadIdx.x + q * MC::MT < TH;
             wunite(R.nlink, R.nkey, na[q], nb[q], right ? wind_off(1, 0) : wind_off(0, 1), R.obs + j);
-        } else {
-            gunite_by_key(R.npar, R.nkey, na[q], nb[q]);
         }
+        return;
+    }
+    // The thread's unions (gunite_by_key's steps) advance in lock step, both
+    // finds of every link at once, so their L2 round trips overlap: each pass
+    // loads the parent and key of every current node, climbs every find that
+    // is not at a root (path splitting: the node it came from is pointed at
+    // the parent just read, an ancestor), and links two distinct roots by
+    // compare-and-swap, the larger key under the smaller; a failed swap
+    // climbs on from the root that was linked meanwhile.
+    int xa[MC::EPT], xb[MC::EPT], sa[MC::EPT], sb[MC::EPT];
+    bool live[MC::EPT];
+#pragma unroll
+    for (int q = 0; q < MC::EPT; ++q) {
+        live[q] = na[q] >= 0;
+        xa[q] = na[q];
+        xb[q] = nb[q];
+        sa[q] = sb[q] = -1;
+    }
+    for (;;) {
+        int pa[MC::EPT], pb[MC::EPT], ka[MC::EPT], kb[MC::EPT];
+#pragma unroll
+        for (int q = 0; q < MC::EPT; ++q) {
+            if (!live[q]) continue;
+            pa[q] = gload(R.npar + xa[q]);
+            pb[q] = gload(R.npar + xb[q]);
+            ka[q] = R.nkey[xa[q]];
+            kb[q] = R.nkey[xb[q]];
+        }
+        bool more = false;
+#pragma unroll
+        for (int q = 0; q < MC::EPT; ++q) {
+            if (!live[q]) continue;
+            const bool ra = pa[q] == xa[q], rb = pb[q] == xb[q];
+            if (!ra || !rb) {
+                if (!ra) {
+                    if (sa[q] >= 0) *(volatile int32_t *)(R.npar + sa[q]) = pa[q];
+                    sa[q] = xa[q];
+                    xa[q] = pa[q];
+                }
+                if (!rb) {
+                    if (sb[q] >= 0) *(volatile int32_t *)(R.npar + sb[q]) = pb[q];
+                    sb[q] = xb[q];
+                    xb[q] = pb[q];
+                }
+                more = true;
+            } else if (xa[q] == xb[q]) {
+                live[q] = false;
+            } else {
+                const bool a_lo = ka[q] < kb[q];
+                const int lo = a_lo ? xa[q] : xb[q], hi = a_lo ? xb[q] : xa[q];
+                if (atomicCAS(R.npar + hi, hi, lo) == hi) live[q] = false;
+                else more = true;
+            }
+        }
+        if (!more) break;
     }
 }
 
