@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
         }
     }
     __syncthreads();
+    uint8_t bits = 0;
     if (valid) {
         const uint8_t s = st[lz][ly][lx];
-        uint8_t bits = 0;
 #pragma unroll
         for (int dir = 0; dir < DIM; ++dir) {
             const uint32_t u = uw[DIM * t + dir];   // link DIM * i + dir
@@ -158,14 +158,35 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
             if (ns == s && (uint64_t)u < p.thr) bits |= (uint8_t)(1u << dir);
         }
         p.bond[i] = bits;
-        // bonds whose far end is in the brick (not across the lattice's edge)
-        if ((bits & 1) && lx + 1 < B::BX && gx + 1 < L) sunite(par, t, t + 1);
-        if ((bits & 2) && ly + 1 < B::BY && gy + 1 < L) sunite(par, t, t + B::BX);
-        if (DIM == 3 && (bits & 4) && lz + 1 < B::BZ && gz + 1 < L) sunite(par, t, t + B::BX * B::BY);
+    }
+    // bonds whose far end is in the brick (not across the lattice's edge)
+    const bool bx = (bits & 1) && lx + 1 < B::BX && gx + 1 < L;
+    const bool by = (bits & 2) && ly + 1 < B::BY && gy + 1 < L;
+    int head = t;   // the site whose root is this site's root
+    if (DIM == 2) {
+        // A warp is one 32-site row of the brick.  The union-find runs on
+        // run heads (the leftmost site of a maximal chain of x bonds), so the
+        // x bonds need no unions; a down bond is a contact between the run
+        // above and the run below, skipped when the down bond to its left
+        // already joins the same two runs.
+        __shared__ uint32_t heads_of[B::BY];
+        const uint32_t hbits = __ballot_sync(0xFFFFFFFFu, bx);
+        const uint32_t vbits = __ballot_sync(0xFFFFFFFFu, by);
+        const uint32_t heads = run_heads(hbits);
+        if (lx == 0) heads_of[ly] = heads;
+        head = head_of(heads, B::BX * ly, lx);
+        __syncthreads();
+        const uint32_t below = ly + 1 < B::BY ? heads_of[ly + 1] : 0xFFFFFFFFu;
+        const uint32_t u = vbits & (~(vbits << 1) | heads | below);
+        if ((u >> lx) & 1u) sunite(par, head, head_of(below, B::BX * (ly + 1), lx));
+    } else if (valid) {
+        if (bx) sunite(par, t, t + 1);
+        if (by) sunite(par, t, t + B::BX);
+        if ((bits & 4) && lz + 1 < B::BZ && gz + 1 < L) sunite(par, t, t + B::BX * B::BY);
     }
     __syncthreads();
     if (valid) {
-        const int r = sroot(par, t);
+        const int r = sroot(par, head);
         const int rx = r % B::BX, ry = (r / B::BX) % B::BY, rz = r / (B::BX * B::BY);
         p.label[i] = (int32_t)((uint32_t)(x0 + rx) + uL * ((uint32_t)(y0 + ry) + uL * (uint32_t)(z0 + rz)));
         if (p.size) atomicAdd(&cnt[r], 1);
