@@ -641,8 +641,9 @@ def run_configs(args):
     for kind, w, osweeps in cases:
         L = w.L
         n = w.sweeps
-        if kind == "pcc":
-            mk = lambda: swgpu.Lattice(L, seed=w.seed, pcc=True)
+        if kind == "pcc":   # the tile height the autotuner picks for the critical plain lattice
+            th = swgpu.sw_autotune(L, workloads.T_CRITICAL_ROUNDED)
+            mk = lambda: swgpu.Lattice(L, seed=w.seed, pcc=True, tile_h=th)
             ork = lambda: oracle.pcc_chain(L, w.seed)
         else:
             th = swgpu.sw_autotune(L, w.T)

@@ -93,7 +93,7 @@ struct Replica {
     uint32_t *pmask;        // tiles * S * 8: a piece's column mask (4 words), row mask (4 words)
     int32_t *cid;           // tiles * S * 2: candidate id + 2 of a root node (x, y), 0 = none
     int32_t *cand;          // [2][L] candidate roots (x, then y)
-    int32_t *ncand;         // [2] candidate counts
+    int32_t *ncand;         // [3]: candidate counts (x, y), decide blocks finished
     uint32_t *cov;
     // cluster sizes (RF_CSIZE): sites of each border piece at its
     // representative node, and of each cluster at its root node
@@ -1520,72 +1520,88 @@ __global__ void k_pcc_cover(const SweepArgs a)
     }
 }
 
-// Step 3 (one block per lattice): a candidate spans x iff its coverage of
-// every tile column is that column's full mask (P_x(C) = [0, L-1]); y alike.
-// Record the flags, apply the PCC feedback to the threshold for the next
-// sweep -- down by delta_k if the clusters percolate, up otherwise, delta_k =
-// 2^(32 - min(8 + floor(k/1000), 20)), clamped to [0, 2^32] -- and clear the
-// scratch.  Under the topological rule (RF_WIND) the flags are the windings
-// the unions recorded.
+// Step 3 (PCC_DECIDE_BLOCKS blocks per lattice, blockIdx.y = the lattice): a
+// candidate spans x iff its coverage of every tile column is that column's
+// full mask (P_x(C) = [0, L-1]); y alike.  Each block checks its share of the
+// candidates, clears their scratch and ORs what it found into the sweep's
+// spans_x / spans_y; the lattice's last block to finish (a counter, ncand[2],
+// taken after a fence: no block waits for another) applies the PCC feedback
+// to the threshold for the next sweep -- down by delta_k if the clusters
+// percolate, up otherwise, delta_k = 2^(32 - min(8 + floor(k/1000), 20)),
+// clamped to [0, 2^32] -- and resets the counts.  Under the topological rule
+// (RF_WIND) there are no candidates: the flags are the windings the unions
+// recorded.
+constexpr int PCC_DECIDE_BLOCKS = 8;
 template <int TH>
 __global__ void k_pcc_decide(const SweepArgs a, int n_reps)
 {
-    const int rr = blockIdx.x;
+    const int rr = blockIdx.y;
     if (rr >= n_reps) return;
     const Replica &R = a.reps[rr];
     if (R.L <= 0) return;                  // unused slot of a batch
     const int j = lattice_launch(a, R);
     if (!(R.flags & RF_PCC) || j < 0 || j >= R.nsweeps) return;
     const int nx = R.ncand[0], ny = R.ncand[1];
-    const uint32_t *covx = R.cov;
-    const uint32_t *covy = R.cov + (size_t)R.L * R.tiles_x * 4;
+    uint32_t *covx = R.cov;
+    uint32_t *covy = R.cov + (size_t)R.L * R.tiles_x * 4;
+    // block b takes a contiguous range of each axis's candidates: checks stop
+    // at the first tile column (row) a candidate does not cover, and the
+    // range's coverage is cleared with coalesced stores afterwards
+    const int cx = (nx + gridDim.x - 1) / gridDim.x, cy = (ny + gridDim.x - 1) / gridDim.x;
+    const int x0 = blockIdx.x * cx, x1 = min(nx, x0 + cx);
+    const int y0 = blockIdx.x * cy, y1 = min(ny, y0 + cy);
     int sx = 0, sy = 0;
-    for (int id = threadIdx.x; id < nx; id += blockDim.x) {
+    for (int id = x0 + threadIdx.x; id < x1; id += blockDim.x) {
         bool full = true;
         for (int tx = 0; tx < R.tiles_x && full; ++tx) {
             const int tw = min(TW, R.L - TW * tx);
+            const uint32_t *cv = covx + ((size_t)id * R.tiles_x + tx) * 4;
             for (int q = 0; q < 4; ++q) {
                 const uint32_t m = valid_mask(q, tw);
-                full &= (covx[((size_t)id * R.tiles_x + tx) * 4 + q] & m) == m;
+                full &= (cv[q] & m) == m;
             }
         }
         sx |= full;
+        R.cid[(size_t)R.cand[id] * 2 + 0] = 0;
     }
-    for (int id = threadIdx.x; id < ny; id += blockDim.x) {
+    for (int id = y0 + threadIdx.x; id < y1; id += blockDim.x) {
         bool full = true;
         for (int ty = 0; ty < R.tiles_y && full; ++ty) {
             const int th = min(TH, R.L - TH * ty);
+            const uint32_t *cv = covy + ((size_t)id * R.tiles_y + ty) * 4;
             for (int q = 0; q < 4; ++q) {
                 const uint32_t m = valid_mask(q, th);
-                full &= (covy[((size_t)id * R.tiles_y + ty) * 4 + q] & m) == m;
+                full &= (cv[q] & m) == m;
             }
         }
         sy |= full;
+        R.cid[(size_t)R.cand[R.L + id] * 2 + 1] = 0;
     }
+    __syncthreads();   // every check of this block's range has read its coverage
+    for (int64_t q = (int64_t)x0 * R.tiles_x * 4 + threadIdx.x; q < (int64_t)x1 * R.tiles_x * 4; q += blockDim.x)
+        covx[q] = 0u;
+    for (int64_t q = (int64_t)y0 * R.tiles_y * 4 + threadIdx.x; q < (int64_t)y1 * R.tiles_y * 4; q += blockDim.x)
+        covy[q] = 0u;
     sx = __syncthreads_or(sx);
     sy = __syncthreads_or(sy);
-    if (R.flags & RF_WIND) {   // topological rule: the unions recorded the windings
-        sx = R.obs[j].spans_x;
-        sy = R.obs[j].spans_y;
-    }
-    for (int64_t q = threadIdx.x; q < (int64_t)nx * R.tiles_x * 4; q += blockDim.x) R.cov[q] = 0u;
-    for (int64_t q = threadIdx.x; q < (int64_t)ny * R.tiles_y * 4; q += blockDim.x)
-        R.cov[(size_t)R.L * R.tiles_x * 4 + q] = 0u;
-    for (int id = threadIdx.x; id < nx; id += blockDim.x) R.cid[(size_t)R.cand[id] * 2 + 0] = 0;
-    for (int id = threadIdx.x; id < ny; id += blockDim.x) R.cid[(size_t)R.cand[R.L + id] * 2 + 1] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        R.obs[j].spans_x = sx;
-        R.obs[j].spans_y = sy;
-        const uint64_t k = R.sweep0 + (uint64_t)j;
-        const uint64_t e = 8 + k / 1000;
-        const uint64_t delta = (uint64_t)1 << (32 - (e < 20 ? e : 20));
-        const uint64_t top = (uint64_t)1 << 32;
-        const uint64_t t = *R.thr_dev;
-        *R.thr_dev = (sx || sy) ? (t > delta ? t - delta : 0) : (t + delta < top ? t + delta : top);
-        R.ncand[0] = 0;
-        R.ncand[1] = 0;
-    }
+    if (threadIdx.x != 0) return;
+    DevObs &o = R.obs[j];
+    if (sx) atomicOr(&o.spans_x, 1);
+    if (sy) atomicOr(&o.spans_y, 1);
+    __threadfence();
+    if (atomicAdd(R.ncand + 2, 1) != (int)gridDim.x - 1) return;
+    // the last block: every other block's flags are visible
+    __threadfence();
+    const int fx = *(volatile int32_t *)&o.spans_x, fy = *(volatile int32_t *)&o.spans_y;
+    const uint64_t k = R.sweep0 + (uint64_t)j;
+    const uint64_t e = 8 + k / 1000;
+    const uint64_t delta = (uint64_t)1 << (32 - (e < 20 ? e : 20));
+    const uint64_t top = (uint64_t)1 << 32;
+    const uint64_t t = *R.thr_dev;
+    *R.thr_dev = (fx || fy) ? (t > delta ? t - delta : 0) : (t + delta < top ? t + delta : top);
+    R.ncand[0] = 0;
+    R.ncand[1] = 0;
+    R.ncand[2] = 0;
 }
 
 // ------------------------------------------------------------ small kernels

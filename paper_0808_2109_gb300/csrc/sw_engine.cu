@@ -77,7 +77,7 @@ void launch_merge_w(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
     if (pcc) {   // reads the compressed forest; the spins do not depend on it
         k_pcc_candidates<TH><<<bu, MERGE_THREADS, 0, st>>>(a);
         k_pcc_cover<TH><<<bn, MERGE_THREADS, 0, st>>>(a);
-        k_pcc_decide<TH><<<n_reps, 256, 0, st>>>(a, n_reps);
+        k_pcc_decide<TH><<<dim3(PCC_DECIDE_BLOCKS, n_reps), 256, 0, st>>>(a, n_reps);
     }
 }
 
@@ -364,10 +364,10 @@ int ctx_create(sw_ctx **out, int32_t L, uint64_t thr, uint64_t seed, bool pcc, u
         if ((e = dalloc(&c->pmask, nt * c->S * 8)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&c->cid, nt * c->S * 2)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&c->cand, (size_t)2 * L)) != cudaSuccess) return fail(e);
-        if ((e = dalloc(&c->ncand, 2)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->ncand, 3)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&c->cov, ncov)) != cudaSuccess) return fail(e);
         if ((e = cudaMemsetAsync(c->cid, 0, nt * c->S * 2 * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
-        if ((e = cudaMemsetAsync(c->ncand, 0, 2 * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(c->ncand, 0, 3 * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
         if ((e = cudaMemsetAsync(c->cov, 0, ncov * sizeof(uint32_t), c->stream)) != cudaSuccess) return fail(e);
     }
     if (flags & SW_FLAG_CSIZE) {

@@ -114,7 +114,7 @@ JobLayout job_layout(int L, int TH, int nsweeps, bool pcc, bool csize, bool wind
         o.pmask = take(nt * S * 8 * 4);
         o.cid = take(nt * S * 2 * 4);
         o.cand = take(2 * (size_t)L * 4);
-        o.ncand = take(2 * 4);
+        o.ncand = take(3 * 4);
         o.cov = take((size_t)L * (tx + ty) * 4 * 4);
         o.pcc_end = at;
     }
