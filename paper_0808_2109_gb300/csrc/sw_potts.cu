@@ -43,6 +43,7 @@ namespace {
 
 constexpr uint32_t STREAM_QSPIN = 3;
 constexpr int PT = 256;   // threads per block
+constexpr int POTTS_BY2 = 16;   // rows of a 2D brick (16 measured best of 8, 16 and 32)
 
 __device__ __forceinline__ uint8_t potts_state(uint32_t w, int q)
 {
@@ -89,7 +90,7 @@ __global__ void k_potts_hot_start(const PottsDev p)
 // one site on the + side of every axis.
 template <int DIM>
 struct Brick {
-    static constexpr int BX = DIM == 2 ? 32 : 8, BY = DIM == 2 ? 32 : 8, BZ = DIM == 2 ? 1 : 8;
+    static constexpr int BX = DIM == 2 ? 32 : 8, BY = DIM == 2 ? POTTS_BY2 : 8, BZ = DIM == 2 ? 1 : 8;
     static constexpr int NT = BX * BY * BZ;
     static constexpr int HX = BX + 1, HY = BY + 1, HZ = DIM == 2 ? 1 : BZ + 1;
 };
@@ -106,17 +107,29 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
     __shared__ uint8_t st[B::HZ][B::HY][B::HX];
     __shared__ int par[B::NT];
     __shared__ int cnt[B::NT];
-    __shared__ uint32_t uw[DIM * B::NT];   // the BOND words of the brick's links
+    __shared__ __align__(16) uint32_t uw[DIM * B::NT];   // the BOND words of the brick's links
     const int L = p.L;
     const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
     const uint32_t uL = (uint32_t)L;
     // past the lattice's last site the halo wraps (a lattice narrower than a
     // brick wraps more than once)
     auto wrap = [L](int g) { return (uint32_t)(g < L ? g : g % L); };
-    for (int q = threadIdx.x; q < B::HX * B::HY * B::HZ; q += B::NT) {
-        const int hx = q % B::HX, hy = (q / B::HX) % B::HY, hz = q / (B::HX * B::HY);
-        const uint32_t gx = wrap(x0 + hx), gy = wrap(y0 + hy), gz = DIM == 3 ? wrap(z0 + hz) : 0u;
-        st[hz][hy][hx] = p.spin[gx + uL * (gy + uL * gz)];
+    if (DIM == 2) {
+        // a warp per halo row: lane x loads site x0 + x, lane 0 also the
+        // halo column's site
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const uint32_t gx = wrap(x0 + lane), gh = wrap(x0 + B::BX);
+        for (int hy = warp; hy < B::HY; hy += B::NT / 32) {
+            const uint8_t *row = p.spin + (size_t)uL * wrap(y0 + hy);
+            st[0][hy][lane] = row[gx];
+            if (lane == 0) st[0][hy][B::BX] = row[gh];
+        }
+    } else {
+        for (int q = threadIdx.x; q < B::HX * B::HY * B::HZ; q += B::NT) {
+            const int hx = q % B::HX, hy = (q / B::HX) % B::HY, hz = q / (B::HX * B::HY);
+            const uint32_t gx = wrap(x0 + hx), gy = wrap(y0 + hy), gz = wrap(z0 + hz);
+            st[hz][hy][hx] = p.spin[gx + uL * (gy + uL * gz)];
+        }
     }
     const int t = threadIdx.x;
     const int lx = t % B::BX, ly = (t / B::BX) % B::BY, lz = t / (B::BX * B::BY);
@@ -127,7 +140,20 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
     if (p.size) cnt[t] = 0;
     const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
-    {
+    if (DIM == 2 && (L & 1) == 0) {
+        // even L: a 2D brick row of 32 sites starts on an even site, so its
+        // 64 links are exactly the 16 Philox blocks from (site index) / 2;
+        // thread t < 16 BY draws block t & 15 of row t >> 4 (words of sites
+        // past the lattice's edge are drawn but never read)
+        if (t < 16 * B::BY) {
+            const int row = t >> 4, jb = t & 15;
+            if (y0 + row < L) {
+                const uint32_t i0 = (uint32_t)x0 + uL * (uint32_t)(y0 + row);
+                const U4 r = philox4x32_10((i0 >> 1) + (uint32_t)jb, klo, khi, STREAM_BOND, k0, k1);
+                *reinterpret_cast<uint4 *>(&uw[64 * row + 4 * jb]) = make_uint4(r.x, r.y, r.z, r.w);
+            }
+        }
+    } else {
         // a brick row's BX sites own DIM * BX consecutive links, which span
         // RB - 1 or RB Philox blocks; each block is drawn once, by one thread
         // (words of sites past the lattice's edge are drawn but never read)
@@ -217,6 +243,7 @@ __global__ void __launch_bounds__(Faces<DIM>::NT) k_potts_cross(const PottsDev p
     const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
     const int f = threadIdx.x / FS, r = threadIdx.x % FS;   // f: the face's axis
     const int a = DIM == 2 ? r : r % 8, b = DIM == 2 ? 0 : r / 8;
+    if (DIM == 2 && f == 0 && a >= B::BY) return;   // the x face is BY sites long
     int gx, gy, gz;
     if (f == 0) {
         gx = min(x0 + B::BX, L) - 1;
