@@ -186,8 +186,8 @@ __device__ __forceinline__ uint32_t valid_mask(int c, int tw)
 }
 
 // Resolved final (root | spin << 30) of an edge slot.  A representative
-// holds its own; any other slot holds FINAL_ALIAS | a representative of the
-// same cluster.  Only nfinal is read: the tile kernel that reads a
+// holds its own; any other top or left slot (the ones a neighbour reads for
+// its halo) holds FINAL_ALIAS | a representative of the same cluster.  Only nfinal is read: the tile kernel that reads a
 // neighbour's finals rewrites that neighbour's npar and nkey concurrently.
 constexpr uint32_t FINAL_ALIAS = 0x80000000u;
 __device__ __forceinline__ uint32_t node_final(const Replica &R, size_t node)
@@ -1329,7 +1329,10 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs
 #pragma unroll
     for (int q = 0; q < MC::NPT; ++q) key[q] = (uint32_t)R.nkey[base + threadIdx.x + q * MC::MT];
 #pragma unroll
-    for (int q = 0; q < MC::NPT; ++q) p[q] = (key[q] & KEY_REP) ? gload(R.npar + base + threadIdx.x + q * MC::MT) : -1;
+    for (int q = 0; q < MC::NPT; ++q) {   // loaded with the key, not after it: one round trip less
+        const int pq = gload(R.npar + base + threadIdx.x + q * MC::MT);
+        p[q] = (key[q] & KEY_REP) ? pq : -1;
+    }
     for (int r = 0; r < MERGE_JUMP_ROUNDS; ++r) {
 #pragma unroll
         for (int q = 0; q < MC::NPT; ++q) gp[q] = p[q] >= 0 ? gload(R.npar + p[q]) : -1;
@@ -1409,7 +1412,10 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
                     tot = wind_add(tot, wind_neg((uint32_t)(v >> 32)));
                     x = (int)(uint32_t)v;
                 }
-            } else {
+            } else if (R.flags & RF_PCC) {
+                // the PCC kernels that follow read a representative's root
+                // straight from its parent; no other kernel reads the forest
+                // again before the next tile launch rewrites it
                 for (int x = n; x != r[q];) {
                     const int nx = gload(R.npar + x);
                     *(volatile int32_t *)(R.npar + x) = r[q];
@@ -1422,9 +1428,13 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
             const int bit = rkey[q] & 127;
             const uint32_t spin = (u4_word(u, bit >> 5) >> (bit & 31)) & 1u;
             R.nfinal[n] = rkey[q] | (spin ? FINAL_SPIN : 0u);
-        } else {
-            // the alias points at a representative: its parent since the tile
-            // kernel, moved up the same cluster by path halving at most
+        } else if (threadIdx.x + q * MC::MT < Slots<TH>::BOTTOM ||
+                   (threadIdx.x + q * MC::MT >= Slots<TH>::LEFT && threadIdx.x + q * MC::MT < Slots<TH>::RIGHT)) {
+            // a top or left slot, whose final a neighbour's tile kernel reads
+            // for its halo: an alias of a representative (its parent since
+            // the tile kernel, moved up the same cluster by path halving at
+            // most); past the tile's sites, 0.  No kernel reads the final of
+            // any other slot that is not a representative.
             R.nfinal[n] = key[q] == KEY_NONE ? 0u : FINAL_ALIAS | (uint32_t)p[q];
         }
     }
