@@ -1296,8 +1296,11 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_wind_init(const SweepArgs 
 // leave behind.  The rounds run in one launch, so a round may read a parent
 // that its own thread has already moved up; every value read is still an
 // ancestor, and the resolve kernel walks to the root whatever depth is left.
+// One round is best since the unions split their paths (L=16384, 64-row
+// tiles, merge per sweep with 0 / 1 / 2 / 3 rounds: 0.31 / 0.28 / 0.29 / 0.34
+// ms at T_c, 0.45 / 0.50 / 0.59 ms for 1 / 2 / 3 rounds at T = 2.0).
 // Other slots only alias their piece's representative.
-constexpr int MERGE_JUMP_ROUNDS = 3;
+constexpr int MERGE_JUMP_ROUNDS = 1;
 template <int TH, bool W>
 __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs a)
 {
