@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
     const bool bx = (bits & 1) && lx + 1 < B::BX && gx + 1 < L;
     const bool by = (bits & 2) && ly + 1 < B::BY && gy + 1 < L;
     int head = t;   // the site whose root is this site's root
-    if (DIM == 2) {
+    if constexpr (DIM == 2) {
         // A warp is one 32-site row of the brick.  The union-find runs on
         // run heads (the leftmost site of a maximal chain of x bonds), so the
         // x bonds need no unions; a down bond is a contact between the run
@@ -205,10 +205,39 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
         const uint32_t below = ly + 1 < B::BY ? heads_of[ly + 1] : 0xFFFFFFFFu;
         const uint32_t u = vbits & (~(vbits << 1) | heads | below);
         if ((u >> lx) & 1u) sunite(par, head, head_of(below, B::BX * (ly + 1), lx));
-    } else if (valid) {
-        if (bx) sunite(par, t, t + 1);
-        if (by) sunite(par, t, t + B::BX);
-        if ((bits & 4) && lz + 1 < B::BZ && gz + 1 < L) sunite(par, t, t + B::BX * B::BY);
+    } else {
+        // 3D: a warp holds four 8-site rows of one layer (lane = x + 8 (y mod
+        // 4)).  The union-find runs on the heads of x runs inside those rows;
+        // a y or z bond is a contact between the run of its site and the run
+        // of the site it reaches (the next row: in the same warp or the next
+        // one; the next layer: two warps on), skipped when the bond of the
+        // same direction to its left joins the same two runs.
+        static_assert(B::BX == 8 && B::BY == 8, "3D bricks of 8 x 8 x 8 sites");
+        __shared__ uint32_t heads_of[B::NT / 32];
+        const bool bz = (bits & 4) && lz + 1 < B::BZ && gz + 1 < L;
+        const int lane = t & 31, warp = t >> 5;
+        const uint32_t hbits = __ballot_sync(0xFFFFFFFFu, bx);
+        const uint32_t ybits = __ballot_sync(0xFFFFFFFFu, by);
+        const uint32_t zbits = __ballot_sync(0xFFFFFFFFu, bz);
+        const uint32_t heads = run_heads(hbits);   // bit x = 0 of every row is set: no bond crosses lx = 7
+        if (lane == 0) heads_of[warp] = heads;
+        head = head_of(heads, 32 * warp, lane);
+        __syncthreads();
+        const bool left = lx > 0;   // the site to the left is in the same row
+        if (by) {
+            const int tw = (lane < 24) ? warp : warp + 1, tl = (lane + 8) & 31;   // the site t + 8
+            const uint32_t th_ = heads_of[tw];
+            const bool own_head = (heads >> lane) & 1u, tgt_head = (th_ >> tl) & 1u;
+            if (!(left && ((ybits >> (lane - 1)) & 1u) && !own_head && !tgt_head))
+                sunite(par, head, head_of(th_, 32 * tw, tl));
+        }
+        if (bz) {
+            const int tw = warp + 2;   // the site t + 64, same lane
+            const uint32_t th_ = heads_of[tw];
+            const bool own_head = (heads >> lane) & 1u, tgt_head = (th_ >> lane) & 1u;
+            if (!(left && ((zbits >> (lane - 1)) & 1u) && !own_head && !tgt_head))
+                sunite(par, head, head_of(th_, 32 * tw, lane));
+        }
     }
     __syncthreads();
     if (valid) {
