@@ -298,6 +298,23 @@ __device__ __forceinline__ void sunite(volatile int *par, int a, int b)
     }
 }
 
+// As sunite, reporting whether this call linked two sets (false: a and b
+// were already in one set).
+__device__ __forceinline__ bool sunite_linked(volatile int *par, int a, int b)
+{
+    for (;;) {
+        a = sfind(par, a);
+        b = sfind(par, b);
+        if (a == b) return false;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS((int *)&par[b], b, a) == b) return true;
+    }
+}
+
 // Threads of a tile CTA: one warp per 32 x 32 sub-tile.
 template <int TH>
 struct TileCfg {
@@ -1189,17 +1206,17 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT, 64 / ((MergeCfg<TH>::MT + 31
             }
         }
     }
-    // A link whose two ends lie in the same two pieces as the bonded link just
-    // before it along the edge joins nothing new (pieces are known by their
-    // keys, which no union changes): skip it.
-#pragma unroll
-    for (int q = 0; q < MC::EPT; ++q) {
-        if (!prev[q]) continue;
-        const uint32_t ka = (uint32_t)R.nkey[na[q]] ^ (uint32_t)R.nkey[na[q] - 1];
-        const uint32_t kb = (uint32_t)R.nkey[nb[q]] ^ (uint32_t)R.nkey[nb[q] - 1];
-        if (((ka | kb) & KEY_MASK) == 0) na[q] = -1;
-    }
     if (W && (R.flags & RF_WIND)) {
+        // A link whose two ends lie in the same two pieces as the bonded link
+        // just before it along the edge joins nothing new (pieces are known
+        // by their keys, which no union changes): skip it.
+#pragma unroll
+        for (int q = 0; q < MC::EPT; ++q) {
+            if (!prev[q]) continue;
+            const uint32_t ka = (uint32_t)R.nkey[na[q]] ^ (uint32_t)R.nkey[na[q] - 1];
+            const uint32_t kb = (uint32_t)R.nkey[nb[q]] ^ (uint32_t)R.nkey[nb[q] - 1];
+            if (((ka | kb) & KEY_MASK) == 0) na[q] = -1;
+        }
 #pragma unroll
         for (int q = 0; q < MC::EPT; ++q) {
             if (na[q] < 0) continue;
@@ -1209,32 +1226,54 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT, 64 / ((MergeCfg<TH>::MT + 31
         }
         return;
     }
-    // The thread's unions (gunite_by_key's steps) advance in lock step, both
-    // finds of every link at once, so their L2 round trips overlap: each pass
-    // loads the parent and key of every current node, climbs every find that
-    // is not at a root (path splitting: the node it came from is pointed at
-    // the parent just read, an ancestor), and links two distinct roots by
-    // compare-and-swap, the larger key under the smaller; a failed swap
-    // climbs on from the root that was linked meanwhile.
-    int xa[MC::EPT], xb[MC::EPT], sa[MC::EPT], sb[MC::EPT];
+    // The block's links first meet in a small forest in shared memory over
+    // the pieces they touch: the tile's own pieces (ids [0, S): a piece's
+    // representative slot), the right neighbour's ([S, 2S)) and the lower
+    // neighbour's ([2S, 3S)).  Only a link that joins two of those sets there
+    // goes on to the global forest; every other link joins pieces that the
+    // block's global unions connect already.  A slot's piece: its own slot
+    // for a representative (whose parent other blocks may be relinking), else
+    // its parent, which is its representative: no find ever passes through a
+    // slot that is not a representative, and each such slot ends one link only.
+    __shared__ int lp[3 * S];
+    for (int i = threadIdx.x; i < 3 * S; i += MC::MT) lp[i] = i;
+    int pa[MC::EPT], pb[MC::EPT], ka[MC::EPT], kb[MC::EPT];
+#pragma unroll
+    for (int q = 0; q < MC::EPT; ++q) {
+        if (na[q] < 0) continue;
+        pa[q] = gload(R.npar + na[q]);
+        pb[q] = gload(R.npar + nb[q]);
+        ka[q] = R.nkey[na[q]];
+        kb[q] = R.nkey[nb[q]];
+    }
+    __syncthreads();
     bool live[MC::EPT];
 #pragma unroll
     for (int q = 0; q < MC::EPT; ++q) {
-        live[q] = na[q] >= 0;
+        live[q] = false;
+        if (na[q] < 0) continue;
+        const bool right = threadIdx.x + q * MC::MT < TH;
+        const int own = t.lt * S, nbr = (right ? t.g_right : t.g_down) * S;
+        const int la = ((uint32_t)ka[q] & KEY_REP) ? na[q] - own : pa[q] - own;
+        const int lb = (right ? S : 2 * S) + (((uint32_t)kb[q] & KEY_REP) ? nb[q] - nbr : pb[q] - nbr);
+        live[q] = sunite_linked(lp, la, lb);
+    }
+    // The thread's remaining unions (gunite_by_key's steps) advance in lock
+    // step, both finds of every link at once, so their L2 round trips
+    // overlap: each pass climbs every find that is not at a root (path
+    // splitting: the node it came from is pointed at the parent just read, an
+    // ancestor), links two distinct roots by compare-and-swap, the larger key
+    // under the smaller (a failed swap climbs on from the root that was
+    // linked meanwhile), and loads the parent and key of every current node
+    // for the next pass (the first pass uses the loads above).
+    int xa[MC::EPT], xb[MC::EPT], sa[MC::EPT], sb[MC::EPT];
+#pragma unroll
+    for (int q = 0; q < MC::EPT; ++q) {
         xa[q] = na[q];
         xb[q] = nb[q];
         sa[q] = sb[q] = -1;
     }
     for (;;) {
-        int pa[MC::EPT], pb[MC::EPT], ka[MC::EPT], kb[MC::EPT];
-#pragma unroll
-        for (int q = 0; q < MC::EPT; ++q) {
-            if (!live[q]) continue;
-            pa[q] = gload(R.npar + xa[q]);
-            pb[q] = gload(R.npar + xb[q]);
-            ka[q] = R.nkey[xa[q]];
-            kb[q] = R.nkey[xb[q]];
-        }
         bool more = false;
 #pragma unroll
         for (int q = 0; q < MC::EPT; ++q) {
@@ -1262,6 +1301,14 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT, 64 / ((MergeCfg<TH>::MT + 31
             }
         }
         if (!more) break;
+#pragma unroll
+        for (int q = 0; q < MC::EPT; ++q) {
+            if (!live[q]) continue;
+            pa[q] = gload(R.npar + xa[q]);
+            pb[q] = gload(R.npar + xb[q]);
+            ka[q] = R.nkey[xa[q]];
+            kb[q] = R.nkey[xb[q]];
+        }
     }
 }
 
