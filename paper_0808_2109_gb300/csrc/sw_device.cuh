@@ -619,6 +619,12 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             cv[q] = ((idx * 8) / TW < t.th) ? code4[idx] : make_uint4(0u, 0u, 0u, 0u);
         }
         for (int s = tid; s < S; s += NT) sm.u.finfo[s] = R.nfinal[(size_t)t.lt * S + s];
+        // the halos' finals (new spins of the top row of the tile below and of
+        // the left column of the tile to the right), issued with the codes;
+        // an alias is followed once the loads are back
+        uint32_t fb = 0u, fr = 0u;
+        if (warp < TWW && 32 * warp + lane < t.tw) fb = R.nfinal[(size_t)t.g_down * S + SL::TOP + 32 * warp + lane];
+        if (tid < t.th) fr = R.nfinal[(size_t)t.g_right * S + SL::LEFT + tid];
         for (int w = tid; w < TH / 32; w += NT) sm.spx[w] = 0u;
         __syncthreads();
 #pragma unroll
@@ -665,18 +671,15 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
             }
         }
         // bottom halo row: new spins of the top row of the tile below
-        for (int w = warp; w < TWW; w += NW) {
-            const int x = 32 * w + lane;
-            int spin = 0;
-            if (x < t.tw) spin = (node_final(R, (size_t)t.g_down * S + SL::TOP + x) & FINAL_SPIN) ? 1 : 0;
-            const uint32_t word = __ballot_sync(0xFFFFFFFFu, spin);
-            if (lane == 0) sm.sp[t.th][w] = word;
+        if (warp < TWW) {
+            if (fb & FINAL_ALIAS) fb = R.nfinal[fb & ~FINAL_ALIAS];
+            const uint32_t word = __ballot_sync(0xFFFFFFFFu, (fb & FINAL_SPIN) != 0u);
+            if (lane == 0) sm.sp[t.th][warp] = word;
         }
+        if (fr & FINAL_ALIAS) fr = R.nfinal[fr & ~FINAL_ALIAS];
         __syncthreads();
         // right halo column: new spins of the left column of the tile to the right
-        for (int y = tid; y < t.th; y += NT) {
-            if (node_final(R, (size_t)t.g_right * S + SL::LEFT + y) & FINAL_SPIN) set_halo(y);
-        }
+        if (fr & FINAL_SPIN) set_halo(tid);
         __syncthreads();
         long long bs = 0, mag = 0;
         for (int w = tid; w < t.th * TWW; w += NT) {
