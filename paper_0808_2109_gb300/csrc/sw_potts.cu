@@ -124,6 +124,21 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
             st[0][hy][lane] = row[gx];
             if (lane == 0) st[0][hy][B::BX] = row[gh];
         }
+    } else if ((L & 7) == 0) {
+        // L a multiple of 8: each halo row's 8 brick sites are one aligned
+        // 8-byte load (x0 is a multiple of 8, so is every row start); thread
+        // t < 81 loads row (t mod 9, t / 9) and its halo site
+        if (threadIdx.x < B::HY * B::HZ) {
+            const int hy = threadIdx.x % B::HY, hz = threadIdx.x / B::HY;
+            const size_t row = (size_t)uL * (wrap(y0 + hy) + (size_t)uL * wrap(z0 + hz));
+            const uint2 v = *reinterpret_cast<const uint2 *>(p.spin + row + (uint32_t)x0);
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                st[hz][hy][x] = (uint8_t)(v.x >> (8 * x));
+                st[hz][hy][4 + x] = (uint8_t)(v.y >> (8 * x));
+            }
+            st[hz][hy][B::BX] = p.spin[row + wrap(x0 + B::BX)];
+        }
     } else {
         for (int q = threadIdx.x; q < B::HX * B::HY * B::HZ; q += B::NT) {
             const int hx = q % B::HX, hy = (q / B::HX) % B::HY, hz = q / (B::HX * B::HY);
@@ -151,6 +166,19 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
                 const uint32_t i0 = (uint32_t)x0 + uL * (uint32_t)(y0 + row);
                 const U4 r = philox4x32_10((i0 >> 1) + (uint32_t)jb, klo, khi, STREAM_BOND, k0, k1);
                 *reinterpret_cast<uint4 *>(&uw[64 * row + 4 * jb]) = make_uint4(r.x, r.y, r.z, r.w);
+            }
+        }
+    } else if (DIM == 3 && (L & 3) == 0) {
+        // L a multiple of 4: a 3D brick row of 8 sites starts on a site i0
+        // that is a multiple of 4, so its 24 links are exactly the 6 Philox
+        // blocks from 3 i0 / 4; thread t < 384 draws block t mod 6 of row t / 6
+        if (t < 6 * B::BY * B::BZ) {
+            const int row = t / 6, jb = t % 6;
+            const int ry = row % B::BY, rz = row / B::BY;
+            if (y0 + ry < L && z0 + rz < L) {
+                const uint32_t i0 = (uint32_t)x0 + uL * ((uint32_t)(y0 + ry) + uL * (uint32_t)(z0 + rz));
+                const U4 r = philox4x32_10(3u * (i0 >> 2) + (uint32_t)jb, klo, khi, STREAM_BOND, k0, k1);
+                *reinterpret_cast<uint4 *>(&uw[24 * row + 4 * jb]) = make_uint4(r.x, r.y, r.z, r.w);
             }
         }
     } else {
