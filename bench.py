@@ -165,12 +165,14 @@ class ClockSampler:
 def philox_calls_per_start(L: int) -> int:
     """Philox blocks the tile kernel draws to start one sweep: per 128-wide
     tile row, 64 BOND blocks (one per two sites; 128 on rows that begin on an
-    odd site, which odd L gives every other row) and 2 SPIN blocks for the
-    clusters that end inside the tile."""
+    odd site, which odd L gives every other row) and the SPIN blocks for the
+    clusters that end inside the tile: one when the row's first site is a
+    multiple of 128 (its 128 bits are one block), else the two it straddles."""
     tiles_x = (L + 127) // 128
     odd_rows = L // 2 if L % 2 else 0
     bond = tiles_x * (64 * (L - odd_rows) + 128 * odd_rows)
-    return bond + 2 * L * tiles_x
+    spin = tiles_x * sum(1 if (y * L) % 128 == 0 else 2 for y in range(L))   # tile rows start at y L + 128 tx
+    return bond + spin
 
 
 def profile_traffic(kernel_src_sha: str, tile_h: int):
