@@ -128,6 +128,14 @@ def lib():
             L.swo_potts_measure.restype = None
             L.swo_potts_run.argtypes = [i32, i32, i32, u64, u64, i32, i32, u64, P, P, P, P]
             L.swo_potts_run.restype = ctypes.c_int
+            L.swo_potts_bonds_open.argtypes = [i32, i32, u64, u64, u64, P, P, i32]
+            L.swo_potts_bonds_open.restype = i64
+            L.swo_potts_measure_open.argtypes = [i32, i32, i32, P, i32, P, P]
+            L.swo_potts_measure_open.restype = None
+            L.swo_spans_nd.argtypes = [i32, i32, P, P]
+            L.swo_spans_nd.restype = ctypes.c_int
+            L.swo_potts_run_pcc.argtypes = [i32, i32, i32, u64, u64, i32, i32, i32, i32, P, P, P, P, P]
+            L.swo_potts_run_pcc.restype = ctypes.c_int
             L.swo_csize2.argtypes = [i32, P]
             L.swo_csize2.restype = i64
             L.swo_pcc_delta.argtypes = [u64]
@@ -317,11 +325,20 @@ def potts_hot_start(dim: int, L: int, q: int, seed: int) -> np.ndarray:
     return spin
 
 
-def potts_bonds(dim: int, L: int, seed: int, sweep: int, thr: int, spin: np.ndarray):
+def potts_bonds(dim: int, L: int, seed: int, sweep: int, thr: int, spin: np.ndarray, open: bool = False):
     spin = np.ascontiguousarray(spin, dtype=np.uint8)
     bond = np.empty(L ** dim, dtype=np.uint8)
-    nb = lib().swo_potts_bonds(dim, L, seed, sweep, thr, _ptr(spin), _ptr(bond))
+    nb = lib().swo_potts_bonds_open(dim, L, seed, sweep, thr, _ptr(spin), _ptr(bond), 1 if open else 0)
     return bond, int(nb)
+
+
+def spans_nd(dim: int, L: int, lab: np.ndarray):
+    """Extension rule per axis: (spans x, spans y[, spans z])."""
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    out = np.zeros(3, dtype=np.int32)
+    if lib().swo_spans_nd(dim, L, _ptr(lab), _ptr(out)) != 0:
+        raise MemoryError("swo_spans_nd")
+    return tuple(int(v) for v in out[:dim])
 
 
 def label_nd(dim: int, L: int, bond: np.ndarray):
@@ -345,22 +362,26 @@ def potts_assign(dim: int, L: int, q: int, seed: int, sweep: int, lab: np.ndarra
     return spin
 
 
-def potts_measure(dim: int, L: int, q: int, spin: np.ndarray):
+def potts_measure(dim: int, L: int, q: int, spin: np.ndarray, open: bool = False):
     spin = np.ascontiguousarray(spin, dtype=np.uint8)
     bs = np.zeros(1, dtype=np.int64)
     m = np.zeros(1, dtype=np.int64)
-    lib().swo_potts_measure(dim, L, q, _ptr(spin), _ptr(bs), _ptr(m))
+    lib().swo_potts_measure_open(dim, L, q, _ptr(spin), 1 if open else 0, _ptr(bs), _ptr(m))
     return int(bs[0]), int(m[0])
 
 
 class PottsChain:
-    """A q-state Potts lattice (d = 2 or 3) advanced by the oracle."""
+    """A q-state Potts lattice (d = 2 or 3) advanced by the oracle; open=True
+    gives open boundaries, pcc=True the PCC feedback (the threshold starts at
+    2^31 and J, T are ignored)."""
 
-    def __init__(self, dim: int, L: int, q: int, J: float, T: float, seed: int, csize: bool = False):
+    def __init__(self, dim: int, L: int, q: int, J: float, T: float, seed: int, csize: bool = False,
+                 open: bool = False, pcc: bool = False):
         if dim not in (2, 3) or L < 2 or not 2 <= q <= 256:
             raise ValueError("dim in {2, 3}, L >= 2, 2 <= q <= 256")
         self.dim, self.L, self.q, self.seed, self.csize = int(dim), int(L), int(q), int(seed), bool(csize)
-        self.threshold = threshold_potts(J, T)
+        self.open, self.pcc = bool(open), bool(pcc)
+        self.threshold = (1 << 31) if pcc else threshold_potts(J, T)
         self.sweep = 0
         self.spin = potts_hot_start(dim, L, q, seed)
         self.label = np.arange(L ** dim, dtype=np.int32)
@@ -370,10 +391,12 @@ class PottsChain:
         obs = np.zeros(nsweeps, dtype=OBS_DTYPE)
         if nsweeps <= 0:
             return obs
-        rc = lib().swo_potts_run(self.dim, self.L, self.q, self.seed, self.sweep, nsweeps,
-                                 1 if self.csize else 0, self.threshold, _ptr(self.spin),
-                                 _ptr(self.label), _ptr(self.bond), _ptr(obs))
+        thr = np.array([self.threshold], dtype=np.uint64)
+        rc = lib().swo_potts_run_pcc(self.dim, self.L, self.q, self.seed, self.sweep, nsweeps,
+                                     1 if self.pcc else 0, 1 if self.open else 0, 1 if self.csize else 0,
+                                     _ptr(thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond), _ptr(obs))
         if rc != 0:
-            raise MemoryError("swo_potts_run")
+            raise MemoryError("swo_potts_run_pcc")
+        self.threshold = int(thr[0])
         self.sweep += nsweeps
         return obs

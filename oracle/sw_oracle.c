@@ -548,6 +548,16 @@ static uint64_t nd_neighbour(int32_t dim, int32_t L, uint64_t i, int dir)
     return dim == 2 ? y * l + x : (z * l + y) * l + x;
 }
 
+/* The link of site i in direction dir exists unless open boundaries cut it:
+ * under open boundaries the last coordinate along dir has no + link. */
+static int nd_link_exists(int32_t L, uint64_t i, int dir, int32_t open)
+{
+    if (!open)
+        return 1;
+    uint64_t l = (uint64_t)L, c = dir == 0 ? i % l : dir == 1 ? (i / l) % l : i / (l * l);
+    return c + 1 < l;
+}
+
 static uint64_t nd_sites(int32_t dim, int32_t L)
 {
     uint64_t n = (uint64_t)L * (uint64_t)L;
@@ -577,11 +587,19 @@ void swo_potts_hot_start(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint8
 int64_t swo_potts_bonds(int32_t dim, int32_t L, uint64_t seed, uint64_t sweep, uint64_t thr,
                         const uint8_t *spin, uint8_t *bond)
 {
+    return swo_potts_bonds_open(dim, L, seed, sweep, thr, spin, bond, 0);
+}
+
+int64_t swo_potts_bonds_open(int32_t dim, int32_t L, uint64_t seed, uint64_t sweep, uint64_t thr,
+                             const uint8_t *spin, uint8_t *bond, int32_t open)
+{
     uint64_t N = nd_sites(dim, L);
     int64_t nb = 0;
     for (uint64_t i = 0; i < N; i++) {
         uint8_t b = 0;
         for (int dir = 0; dir < dim; dir++) {
+            if (!nd_link_exists(L, i, dir, open))
+                continue;
             uint64_t j = nd_neighbour(dim, L, i, dir);
             uint64_t l = (uint64_t)dim * i + (uint64_t)dir;
             uint32_t w[4];
@@ -640,20 +658,83 @@ void swo_potts_assign(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t
 void swo_potts_measure(int32_t dim, int32_t L, int32_t q, const uint8_t *spin, int64_t *bond_sum,
                        int64_t *mag)
 {
+    swo_potts_measure_open(dim, L, q, spin, 0, bond_sum, mag);
+}
+
+void swo_potts_measure_open(int32_t dim, int32_t L, int32_t q, const uint8_t *spin, int32_t open,
+                            int64_t *bond_sum, int64_t *mag)
+{
     uint64_t N = nd_sites(dim, L);
     int64_t bs = 0, m = 0;
     for (uint64_t i = 0; i < N; i++) {
         m += spin[i] == 0 ? q - 1 : -1;
         for (int dir = 0; dir < dim; dir++)
-            bs += spin[i] == spin[nd_neighbour(dim, L, i, dir)] ? 1 : -1;
+            if (nd_link_exists(L, i, dir, open))
+                bs += spin[i] == spin[nd_neighbour(dim, L, i, dir)] ? 1 : -1;
     }
     *bond_sum = bs;
     *mag = m;
 }
 
+/* ------------------------------------------------------------------------
+ * Extension rule on the d-dimensional lattice (Sec. III states it for any
+ * dimension): a cluster spans axis a iff its projection on that axis is the
+ * whole range [0, L-1], i.e. iff it occupies every one of the L hyperplanes
+ * perpendicular to a.  Each root's number of distinct hyperplanes is counted
+ * by scanning the hyperplanes in order and stamping each root with the last
+ * one it was seen in (as swo_spans does for the rows and columns of d = 2).
+ * Under open boundaries a cluster cannot wrap, so its projection is an
+ * interval and occupying every hyperplane is touching both opposite faces.
+ * ---------------------------------------------------------------------- */
+int swo_spans_nd(int32_t dim, int32_t L, const int32_t *label, int32_t *spans)
+{
+    uint64_t N = nd_sites(dim, L), l = (uint64_t)L;
+    int32_t *stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t *count = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!stamp || !count) {
+        free(stamp);
+        free(count);
+        return -1;
+    }
+    uint64_t inner = dim == 3 ? l * l : l;   /* sites of one hyperplane */
+    for (int a = 0; a < dim; a++) {
+        for (uint64_t i = 0; i < N; i++) {
+            stamp[i] = -1;
+            count[i] = 0;
+        }
+        spans[a] = 0;
+        for (uint64_t c = 0; c < l; c++) {           /* the hyperplane: coordinate a = c */
+            for (uint64_t u = 0; u < inner; u++) {   /* its sites */
+                uint64_t v0 = u % l, v1 = u / l, x, y, z;
+                if (a == 0) { x = c; y = v0; z = v1; }
+                else if (a == 1) { x = v0; y = c; z = v1; }
+                else { x = v0; y = v1; z = c; }
+                uint64_t i = dim == 2 ? y * l + x : (z * l + y) * l + x;
+                int32_t r = label[i];
+                if (stamp[r] != (int32_t)c) {
+                    stamp[r] = (int32_t)c;
+                    if (++count[r] == L)
+                        spans[a] = 1;
+                }
+            }
+        }
+    }
+    free(stamp);
+    free(count);
+    return 0;
+}
+
 int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
                   int32_t csize, uint64_t thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
 {
+    return swo_potts_run_pcc(dim, L, q, seed, sweep0, nsweeps, 0, 0, csize, &thr, spin, label, bond, obs);
+}
+
+int swo_potts_run_pcc(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
+                      int32_t pcc, int32_t open, int32_t csize, uint64_t *thr_io, uint8_t *spin, int32_t *label,
+                      uint8_t *bond, swo_obs *obs)
+{
+    uint64_t thr = *thr_io;
     uint64_t N = nd_sites(dim, L);
     uint8_t *b = bond ? bond : (uint8_t *)malloc((size_t)N);
     if (!b)
@@ -664,8 +745,17 @@ int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t swe
         swo_obs o;
         memset(&o, 0, sizeof(o));
         o.threshold = thr;
-        o.nbonds = swo_potts_bonds(dim, L, seed, k, thr, spin, b);
+        o.nbonds = swo_potts_bonds_open(dim, L, seed, k, thr, spin, b, open);
         o.nclusters = swo_label_nd(dim, L, b, label);
+        if (pcc) {
+            int32_t sp[3] = {0, 0, 0};
+            if (swo_spans_nd(dim, L, label, sp) != 0) {
+                rc = -1;
+                break;
+            }
+            o.spans_x = sp[0];
+            o.spans_y = sp[1] | sp[2];   /* y, or in 3D y or z */
+        }
         if (csize) {
             int64_t *count = (int64_t *)calloc((size_t)N, sizeof(int64_t));
             if (!count) {
@@ -679,9 +769,12 @@ int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t swe
             free(count);
         }
         swo_potts_assign(dim, L, q, seed, k, label, spin);
-        swo_potts_measure(dim, L, q, spin, &o.bond_sum, &o.mag);
+        swo_potts_measure_open(dim, L, q, spin, open, &o.bond_sum, &o.mag);
         obs[n] = o;
+        if (pcc)
+            thr = swo_pcc_update(thr, k, o.spans_x || o.spans_y);
     }
+    *thr_io = thr;
     if (!bond)
         free(b);
     return rc;

@@ -133,6 +133,24 @@ void swo_potts_assign(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t
                       const int32_t *label, uint8_t *spin);
 void swo_potts_measure(int32_t dim, int32_t L, int32_t q, const uint8_t *spin, int64_t *bond_sum,
                        int64_t *mag);
+/* open != 0: open boundaries (the last coordinate along a direction has no
+ * + link; no bond, no energy term). */
+int64_t swo_potts_bonds_open(int32_t dim, int32_t L, uint64_t seed, uint64_t sweep, uint64_t thr,
+                             const uint8_t *spin, uint8_t *bond, int32_t open);
+void swo_potts_measure_open(int32_t dim, int32_t L, int32_t q, const uint8_t *spin, int32_t open,
+                            int64_t *bond_sum, int64_t *mag);
+/* Extension rule in d = 2 or 3 dimensions (Sec. III): spans[a] = 1 iff some
+ * cluster occupies all L hyperplanes perpendicular to axis a (a < dim).
+ * Returns 0, or -1 when memory is short. */
+int swo_spans_nd(int32_t dim, int32_t L, const int32_t *label, int32_t *spans);
+/* As swo_potts_run, with open boundaries (open != 0) and the PCC feedback
+ * (pcc != 0): *thr_io is the first sweep's threshold and, after each sweep,
+ * moves by swo_pcc_update on (some cluster spans some axis); obs[].spans_x
+ * reports the x axis, spans_y the y axis (in 3D: the y or the z axis).  On
+ * return *thr_io holds the next sweep's threshold. */
+int swo_potts_run_pcc(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
+                      int32_t pcc, int32_t open, int32_t csize, uint64_t *thr_io, uint8_t *spin, int32_t *label,
+                      uint8_t *bond, swo_obs *obs);
 /* nsweeps sweeps at the fixed threshold thr (obs[].csize2 filled when csize). */
 int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
                   int32_t csize, uint64_t thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
