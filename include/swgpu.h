@@ -148,12 +148,24 @@ int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags);
  * state floor(w q / 2^32), w = word (r mod 4) of Philox(r/4, k, stream 3);
  * the hot start is the same of word (i mod 4) of Philox(i/4, 0, INIT).
  * Observables: bond_sum = sum over links of (2 delta - 1), mag = sum over
- * sites of (q [s_i = 0] - 1).  flags: SW_FLAG_CSIZE or 0.  The other calls
- * take the context as usual (spins, labels and bond bytes have L^d entries,
- * bond bit dir); pcc_step and sw_profile answer SW_ERR_STATE.  Errors:
- * SW_ERR_ARG, SW_ERR_NOMEM, SW_ERR_CUDA. */
+ * sites of (q [s_i = 0] - 1).  flags: SW_FLAG_CSIZE and SW_FLAG_OPEN (open
+ * boundaries: the last coordinate along a direction has no + link, which
+ * neither bonds nor enters bond_sum), or 0.  The other calls take the context
+ * as usual (spins, labels and bond bytes have L^d entries, bond bit dir);
+ * pcc_step (on a lattice not made by pcc_create_potts) and sw_profile answer
+ * SW_ERR_STATE.  Errors: SW_ERR_ARG, SW_ERR_NOMEM, SW_ERR_CUDA. */
 int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, double T, uint64_t seed,
                     uint32_t flags);
+
+/* A PCC lattice on the Potts path (Sec. III, whose percolation criteria hold
+ * in any dimension): as sw_create_potts, with the bond threshold starting at
+ * 2^31 and moved after every sweep by the feedback of pcc_create (down by
+ * delta_k if some cluster spans some axis, up otherwise).  A cluster spans
+ * axis a when it occupies all L hyperplanes perpendicular to a (the
+ * extension rule; under open boundaries, touching both faces).  Per sweep
+ * spans_x reports the x axis and spans_y the y axis, or in 3D the y or the z
+ * axis.  flags: SW_FLAG_CSIZE, SW_FLAG_OPEN or 0.  Errors as sw_create_potts. */
+int pcc_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t seed, uint32_t flags);
 
 /* Release the context and all its device memory.  NULL is accepted. */
 int sw_destroy(sw_ctx *ctx);

@@ -664,21 +664,25 @@ int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags)
     return ctx_create(out, L, (uint64_t)1 << 31, seed, true, flags);   // p = 1/2
 }
 
-int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, double T, uint64_t seed,
-                    uint32_t flags)
+}  // extern "C"
+
+namespace {
+
+// A q-state Potts lattice (plain at threshold thr, or PCC from thr with the
+// feedback on the device): the body of sw_create_potts and pcc_create_potts.
+int potts_create(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t thr, uint64_t seed, uint32_t flags,
+                 bool pcc)
 {
     if (!out) return SW_ERR_ARG;
     *out = nullptr;
-    if ((dim != 2 && dim != 3) || L < 2 || q < 2 || q > 256 || (flags & ~SW_FLAG_CSIZE) != 0) return SW_ERR_ARG;
+    if ((dim != 2 && dim != 3) || L < 2 || q < 2 || q > 256 || (flags & ~(SW_FLAG_CSIZE | SW_FLAG_OPEN)) != 0)
+        return SW_ERR_ARG;
     const int64_t N = dim == 2 ? (int64_t)L * L : (int64_t)L * L * L;
     if (N > ((int64_t)1 << 30)) return SW_ERR_ARG;
-    // P = 1 - exp(-J/T): the Ising threshold at J/2 (the same double)
-    uint64_t thr = 0;
-    int rc = sw_threshold(0.5 * J, T, &thr);
-    if (rc != SW_OK) return rc;
     cudaGetLastError();
     sw_ctx *c = new (std::nothrow) sw_ctx();
     if (!c) return SW_ERR_NOMEM;
+    int rc = SW_OK;
     std::unique_lock<std::mutex> lk(sw_capture_mutex());
     auto fail = [&](cudaError_t e) {
         rc = sw_cuda_fail(e, __LINE__);
@@ -693,6 +697,8 @@ int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, d
     c->nsites = N;
     c->seed = seed;
     c->thr = thr;
+    c->pcc = pcc;
+    c->open = (flags & SW_FLAG_OPEN) != 0;
     if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     c->stream = c->own_stream;
     if ((e = dalloc(&c->spin, (size_t)N)) != cudaSuccess) return fail(e);
@@ -711,11 +717,55 @@ int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, d
     p.bond = c->bond_bytes;
     p.label = c->label;
     p.size = c->psize;
+    p.open = c->open ? 1 : 0;
+    if (pcc) {
+        // per axis: candidate ids of the roots, the candidates of the face
+        // (F = L^(dim-1) sites), their counts and coverage (W words each)
+        const size_t F = dim == 2 ? (size_t)L : (size_t)L * L, W = ((size_t)L + 31) / 32;
+        if ((e = dalloc(&c->thr_dev, 1)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->cid, (size_t)dim * N)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->cand, (size_t)dim * F)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->ncand, 4)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->cov, (size_t)dim * F * W)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(c->cid, 0, (size_t)dim * N * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(c->ncand, 0, 4 * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(c->cov, 0, (size_t)dim * F * W * sizeof(uint32_t), c->stream)) != cudaSuccess)
+            return fail(e);
+        if ((e = cudaMemcpyAsync(c->thr_dev, &c->thr, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream)) !=
+            cudaSuccess)
+            return fail(e);
+        p.thr_dev = c->thr_dev;
+        p.cid = c->cid;
+        p.cand = c->cand;
+        p.ncand = c->ncand;
+        p.cov = c->cov;
+    }
     if ((e = potts_enqueue_hot_start(p, c->stream)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
     lk.unlock();
     *out = c;
     return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, double T, uint64_t seed,
+                    uint32_t flags)
+{
+    if (!out) return SW_ERR_ARG;
+    *out = nullptr;
+    // P = 1 - exp(-J/T): the Ising threshold at J/2 (the same double)
+    uint64_t thr = 0;
+    int rc = sw_threshold(0.5 * J, T, &thr);
+    if (rc != SW_OK) return rc;
+    return potts_create(out, dim, L, q, thr, seed, flags, false);
+}
+
+int pcc_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t seed, uint32_t flags)
+{
+    return potts_create(out, dim, L, q, (uint64_t)1 << 31, seed, flags, true);   // p = 1/2
 }
 
 int sw_destroy(sw_ctx *ctx)

@@ -40,6 +40,15 @@ struct PottsDev {
     uint64_t thr, seed;
     uint8_t *spin, *bond;
     int32_t *label, *size;
+    int32_t open;              // open boundaries: no link leaves the lattice
+    // PCC (null otherwise): the threshold lives on the device and follows the
+    // feedback; per axis a < dim, candidate ids of roots (cid + a N, id + 2),
+    // the candidates (cand + a F, F = L^(dim-1) face sites), their counts
+    // (ncand[a]; ncand[3] counts finished decision blocks) and coverage
+    // (cov + a F W, W = ceil(L / 32) words per candidate)
+    uint64_t *thr_dev;
+    int32_t *cid, *cand, *ncand;
+    uint32_t *cov;
 };
 __attribute__((visibility("hidden"))) cudaError_t potts_enqueue_hot_start(const PottsDev &p, cudaStream_t st);
 __attribute__((visibility("hidden"))) cudaError_t potts_enqueue_sweep(const PottsDev &p, uint64_t sweep, DevObs *obs,

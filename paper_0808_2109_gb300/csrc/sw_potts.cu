@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
     if (p.size) cnt[t] = 0;
     const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    const uint64_t thr = p.thr_dev ? *p.thr_dev : p.thr;
     if (DIM == 2 && (L & 1) == 0) {
         // even L: a 2D brick row of 32 sites starts on an even site, so its
         // 64 links are exactly the 16 Philox blocks from (site index) / 2;
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p
         for (int dir = 0; dir < DIM; ++dir) {
             const uint32_t u = uw[DIM * t + dir];   // link DIM * i + dir
             const uint8_t ns = dir == 0 ? st[lz][ly][lx + 1] : dir == 1 ? st[lz][ly + 1][lx] : st[lz + 1][ly][lx];
-            if (ns == s && (uint64_t)u < p.thr) bits |= (uint8_t)(1u << dir);
+            const int c = dir == 0 ? gx : dir == 1 ? gy : gz;   // under open boundaries the last one links out
+            if (ns == s && (uint64_t)u < thr && !(p.open && c + 1 == L)) bits |= (uint8_t)(1u << dir);
         }
         p.bond[i] = bits;
     }
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(Faces<DIM>::NT) k_potts_cross(const PottsDev p
     }
     if (gx >= L || gy >= L || (DIM == 3 && gz >= L)) return;
     const uint32_t i = (uint32_t)gx + uL * ((uint32_t)gy + uL * (uint32_t)gz);
-    if (!((p.bond[i] >> f) & 1u)) return;
+    if (!((p.bond[i] >> f) & 1u)) return;   // (open boundaries: no bond leaves the lattice)
     uint32_t j;
     if (f == 0)
         j = i - (uint32_t)gx + (gx + 1 == L ? 0u : (uint32_t)gx + 1u);
@@ -370,7 +372,7 @@ __global__ void k_potts_resolve(const PottsDev p, uint64_t k, DevObs *obs)
         long long n = 0;
         for (int w = 0; w < PT / 32; ++w) n += red[w];
         if (n) atomicAdd(&obs->nclusters, (unsigned long long)n);
-        if (blockIdx.x == 0) obs->threshold = p.thr;
+        if (blockIdx.x == 0) obs->threshold = p.thr_dev ? *p.thr_dev : p.thr;
     }
 }
 
@@ -394,8 +396,10 @@ __global__ void k_potts_measure(const PottsDev p, DevObs *obs)
         const uint8_t *row_z = p.spin + (size_t)Rz * uL;
         for (uint32_t x = lane; x < uL; x += 32) {
             const uint8_t s = row[x];
-            v[0] += (row[x + 1 == uL ? 0u : x + 1] == s ? 1 : -1) + (row_y[x] == s ? 1 : -1);
-            if (p.dim == 3) v[0] += row_z[x] == s ? 1 : -1;
+            // each link that exists (open boundaries drop those leaving the lattice)
+            if (!(p.open && x + 1 == uL)) v[0] += row[x + 1 == uL ? 0u : x + 1] == s ? 1 : -1;
+            if (!(p.open && y + 1 == uL)) v[0] += row_y[x] == s ? 1 : -1;
+            if (p.dim == 3 && !(p.open && z + 1 == uL)) v[0] += row_z[x] == s ? 1 : -1;
             v[1] += s == 0 ? p.q - 1 : -1;
             const size_t i = (size_t)R * uL + x;
             v[2] += __popc((uint32_t)p.bond[i]);
@@ -407,6 +411,119 @@ __global__ void k_potts_measure(const PottsDev p, DevObs *obs)
     }
     unsigned long long *const dst[4] = {&obs->bond_sum, &obs->mag, &obs->nbonds, &obs->csize2};
     block_sum_atomic<PT, 4>(v, dst, red);
+}
+
+// ------------------------------------------------------------- Potts PCC
+// The extension rule in d dimensions (Sec. III): a cluster spans axis a iff it
+// occupies all L hyperplanes perpendicular to a.  Such a cluster holds a site
+// of the hyperplane a = 0, so the roots found there are the candidates; every
+// site then marks its coordinate along a in its root's coverage (when the root
+// is a candidate), and a candidate spans iff its coverage is full.  Labels are
+// cluster roots by now (k_potts_resolve).
+
+// Coordinate of site i along axis a, and the site of face a = 0 with index f
+// (the other coordinates in order).
+__device__ __forceinline__ uint32_t coord_of(uint32_t i, uint32_t L, int a)
+{
+    return a == 0 ? i % L : a == 1 ? (i / L) % L : i / (L * L);
+}
+__device__ __forceinline__ uint32_t face_site(uint32_t f, uint32_t L, int a)
+{
+    const uint32_t u = f % L, v = f / L;   // v = 0 in 2D
+    return a == 0 ? L * u + L * L * v : a == 1 ? u + L * L * v : u + L * v;
+}
+
+// Step 1: candidate ids for the roots on each axis's face a = 0.
+__global__ void k_potts_pcc_cand(const PottsDev p, int64_t F)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= F * p.dim) return;
+    const int a = (int)(q / F);
+    const uint32_t f = (uint32_t)(q % F);
+    const int32_t r = p.label[face_site(f, (uint32_t)p.L, a)];
+    int32_t *c = p.cid + (size_t)a * p.N + r;
+    if (atomicCAS(c, 0, 1) == 0) {
+        const int id = atomicAdd(p.ncand + a, 1);   // < F: at most one per face site
+        p.cand[(size_t)a * F + id] = r;
+        *(volatile int32_t *)c = id + 2;
+    }
+}
+
+// Step 2: every site marks its coordinates in its root's coverage, for each
+// axis whose candidate the root is.  A warp of 32 consecutive sites of one row
+// (L a multiple of 32) shares its y and z and one word of x: one atomic per
+// root and axis.
+__global__ void k_potts_pcc_cover(const PottsDev p, int64_t F)
+{
+    const uint32_t L = (uint32_t)p.L, W = (L + 31) / 32;
+    const bool rows = (L & 31u) == 0;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; i0 < p.N;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + lane;
+        const bool ok = i < p.N;
+        const int32_t r = ok ? p.label[i] : -1;
+        for (int a = 0; a < p.dim; ++a) {
+            const int32_t c = ok ? p.cid[(size_t)a * p.N + r] : 0;
+            const uint32_t x = ok ? coord_of((uint32_t)i, L, a) : 0u;
+            uint32_t *cov = p.cov + (size_t)a * F * W;
+            if (rows) {
+                const unsigned grp = __match_any_sync(0xFFFFFFFFu, c);
+                if (c >= 2 && lane == __ffs(grp) - 1) {
+                    // the group's bits: x along the row (lane = x mod 32), else one coordinate
+                    const uint32_t bits = a == 0 ? grp : 1u << (x & 31);
+                    atomicOr(cov + (size_t)(c - 2) * W + (x >> 5), bits);
+                }
+            } else if (c >= 2) {
+                atomicOr(cov + (size_t)(c - 2) * W + (x >> 5), 1u << (x & 31));
+            }
+        }
+    }
+}
+
+// Step 3 (PCC_DECIDE blocks): each block checks a contiguous range of every
+// axis's candidates, clears their scratch and ORs its flags into the sweep's
+// spans_x (axis x) / spans_y (axis y, and z in 3D); the last block to finish
+// (a counter, after a fence: no block waits) applies the feedback to the
+// threshold -- down by delta_k if some cluster spans, up otherwise, clamped
+// to [0, 2^32] -- and resets the counts.
+constexpr int POTTS_PCC_DECIDE = 16;
+__global__ void k_potts_pcc_decide(const PottsDev p, int64_t F, uint64_t k, DevObs *obs)
+{
+    const uint32_t L = (uint32_t)p.L, W = (L + 31) / 32;
+    int sx = 0, sy = 0;
+    for (int a = 0; a < p.dim; ++a) {
+        const int n = p.ncand[a];
+        const int chunk = (n + gridDim.x - 1) / gridDim.x;
+        const int c0 = blockIdx.x * chunk, c1 = min(n, c0 + chunk);
+        uint32_t *cov = p.cov + (size_t)a * F * W;
+        int s = 0;
+        for (int id = c0 + threadIdx.x; id < c1; id += blockDim.x) {
+            bool full = true;
+            for (uint32_t w = 0; w < W && full; ++w) {
+                const uint32_t m = w + 1 < W || (L & 31u) == 0 ? 0xFFFFFFFFu : (1u << (L & 31u)) - 1u;
+                full = (cov[(size_t)id * W + w] & m) == m;
+            }
+            s |= full;
+            p.cid[(size_t)a * p.N + p.cand[(size_t)a * F + id]] = 0;
+        }
+        s = __syncthreads_or(s);   // also: every check of this range has read its coverage
+        for (int64_t q = (int64_t)c0 * W + threadIdx.x; q < (int64_t)c1 * W; q += blockDim.x) cov[q] = 0u;
+        if (a == 0) sx |= s; else sy |= s;
+    }
+    if (threadIdx.x != 0) return;
+    if (sx) atomicOr(&obs->spans_x, 1);
+    if (sy) atomicOr(&obs->spans_y, 1);
+    __threadfence();
+    if (atomicAdd(p.ncand + 3, 1) != (int)gridDim.x - 1) return;
+    __threadfence();   // the last block: every other block's flags are visible
+    const int fx = *(volatile int32_t *)&obs->spans_x, fy = *(volatile int32_t *)&obs->spans_y;
+    const uint64_t e = 8 + k / 1000;
+    const uint64_t delta = (uint64_t)1 << (32 - (e < 20 ? e : 20));
+    const uint64_t top = (uint64_t)1 << 32;
+    const uint64_t t = *p.thr_dev;
+    *p.thr_dev = (fx || fy) ? (t > delta ? t - delta : 0) : (t + delta < top ? t + delta : top);
+    for (int a = 0; a < 4; ++a) p.ncand[a] = 0;
 }
 
 // Sets *bad if any of the n states is >= q.
@@ -449,6 +566,12 @@ cudaError_t potts_enqueue_sweep(const PottsDev &p, uint64_t sweep, DevObs *obs, 
     }
     const unsigned ns = std::min(nb, MAX_BLOCKS);
     k_potts_resolve<<<ns, PT, 0, st>>>(p, sweep, obs);
+    if (p.thr_dev) {   // PCC: the span test on the cluster roots, then the feedback
+        const int64_t F = p.dim == 2 ? (int64_t)p.L : (int64_t)p.L * p.L;
+        k_potts_pcc_cand<<<(unsigned)((F * p.dim + PT - 1) / PT), PT, 0, st>>>(p, F);
+        k_potts_pcc_cover<<<ns, PT, 0, st>>>(p, F);
+        k_potts_pcc_decide<<<POTTS_PCC_DECIDE, PT, 0, st>>>(p, F, sweep, obs);
+    }
     k_potts_measure<<<ns, PT, 0, st>>>(p, obs);
     return cudaGetLastError();
 }

@@ -139,6 +139,7 @@ SIGNATURES = {
     "sw_create_p": ([_P, _i32, _dbl, _u64, _u32], ctypes.c_int),
     "pcc_create": ([_P, _i32, _u64, _u32], ctypes.c_int),
     "sw_create_potts": ([_P, _i32, _i32, _i32, _dbl, _dbl, _u64, _u32], ctypes.c_int),
+    "pcc_create_potts": ([_P, _i32, _i32, _i32, _u64, _u32], ctypes.c_int),
     "sw_checkpoint_bytes": ([_P, _P], ctypes.c_int),
     "sw_save": ([_P, _P, _u64], ctypes.c_int),
     "sw_load": ([_P, _P, _u64], ctypes.c_int),
@@ -236,6 +237,12 @@ def pcc_create(L: int, seed: int, flags: int = 0) -> ctypes.c_void_p:
 def sw_create_potts(dim: int, L: int, q: int, J: float, T: float, seed: int, flags: int = 0) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     _check(lib().sw_create_potts(ctypes.byref(h), dim, L, q, J, T, seed, flags), "sw_create_potts")
+    return h
+
+
+def pcc_create_potts(dim: int, L: int, q: int, seed: int, flags: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().pcc_create_potts(ctypes.byref(h), dim, L, q, seed, flags), "pcc_create_potts")
     return h
 
 
@@ -480,13 +487,20 @@ class Lattice:
 
 
 class PottsLattice:
-    """A q-state Potts lattice on the periodic d-dimensional torus (d = 2, 3)."""
+    """A q-state Potts lattice on the d-dimensional torus (d = 2, 3), with
+    open=True on the open d-dimensional box; pcc=True runs the PCC feedback
+    (the threshold starts at 2^31; T is then ignored)."""
 
-    def __init__(self, dim: int, L: int, q: int, *, J: float = 1.0, T: float, seed: int = 1,
-                 csize: bool = False):
+    def __init__(self, dim: int, L: int, q: int, *, J: float = 1.0, T: float = 1.0, seed: int = 1,
+                 csize: bool = False, open: bool = False, pcc: bool = False):
         self.dim, self.L, self.q = int(dim), int(L), int(q)
         self.N = self.L ** self.dim
-        self.h = sw_create_potts(self.dim, self.L, self.q, J, T, seed, SW_FLAG_CSIZE if csize else 0)
+        self.pcc = bool(pcc)
+        flags = (SW_FLAG_CSIZE if csize else 0) | (SW_FLAG_OPEN if open else 0)
+        if pcc:
+            self.h = pcc_create_potts(self.dim, self.L, self.q, seed, flags)
+        else:
+            self.h = sw_create_potts(self.dim, self.L, self.q, J, T, seed, flags)
 
     def close(self):
         if getattr(self, "h", None):
