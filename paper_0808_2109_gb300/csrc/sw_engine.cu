@@ -257,9 +257,11 @@ struct sw_ctx {
     int32_t *psize = nullptr, *csize = nullptr;
     // topological rule (SW_FLAG_WIND)
     unsigned long long *nlink = nullptr;
-    // a q-state Potts lattice (sw_create_potts): spin, label, bond_bytes and
-    // psize hold its state; none of the tile scratch exists
+    // a q-state Potts lattice (sw_create_potts): spin, label and bond_bytes
+    // hold its state, the tile scratch above its tiles' codes and nodes, and
+    // nstate its representatives' new states
     bool is_potts = false;
+    uint8_t *nstate = nullptr;
     PottsDev pd{};
     int64_t nsites = 0;   // L^d
 
@@ -291,7 +293,7 @@ void ctx_free(sw_ctx *c)
     c->ev_pool.clear();
     void *ptrs[] = {c->spin, c->label, c->code, c->bondbits, c->cross, c->npar, c->nkey,
                     c->nfinal, c->thr_dev, c->rep_dev, c->tile_rep, c->jbase, c->bond_bytes, c->obs,
-                    c->pmask, c->cid, c->cand, c->ncand, c->cov, c->psize, c->csize, c->nlink};
+                    c->pmask, c->cid, c->cand, c->ncand, c->cov, c->psize, c->csize, c->nlink, c->nstate};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -536,8 +538,7 @@ int run_sweeps(sw_ctx *c, int32_t n)
     if (c->is_potts) {
         DevObs *obs = c->obs + c->obs_tail;
         SW_CUDA(cudaMemsetAsync(obs, 0, (size_t)n * sizeof(DevObs), c->stream));
-        for (int32_t k = 0; k < n; ++k)
-            SW_CUDA(potts_enqueue_sweep(c->pd, c->sweep + (uint64_t)k, obs + k, c->stream));
+        SW_CUDA(potts_enqueue_sweeps(c->pd, n, c->sweep, obs, c->stream));
         c->obs_tail += n;
         c->sweep += (uint64_t)n;
         c->swept = true;
@@ -701,33 +702,59 @@ int potts_create(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t thr, 
     c->open = (flags & SW_FLAG_OPEN) != 0;
     if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     c->stream = c->own_stream;
+    PottsGeometry g{};
+    potts_geometry(dim, L, &g);
+    const size_t nt = (size_t)g.ntiles, S = (size_t)g.slots;
     if ((e = dalloc(&c->spin, (size_t)N)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&c->label, (size_t)N)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&c->bond_bytes, (size_t)N)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&c->jbase, 1)) != cudaSuccess) return fail(e);
-    if ((flags & SW_FLAG_CSIZE) && (e = dalloc(&c->psize, (size_t)N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->code, nt * (size_t)g.sites_per_tile)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->cross, nt * (size_t)g.cross_words)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->npar, nt * S)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->nkey, nt * S)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->nfinal, nt * S)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&c->nstate, nt * S)) != cudaSuccess) return fail(e);
+    if (flags & SW_FLAG_CSIZE) {
+        if ((e = dalloc(&c->psize, nt * S)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->csize, nt * S)) != cudaSuccess) return fail(e);
+    }
     PottsDev &p = c->pd;
     p.dim = dim;
     p.L = L;
     p.q = q;
+    p.flags = (pcc ? RF_PCC : 0) | (c->open ? RF_OPEN : 0) | ((flags & SW_FLAG_CSIZE) ? RF_CSIZE : 0);
+    p.ntx = g.ntx;
+    p.nty = g.nty;
+    p.ntz = g.ntz;
+    p.ntiles = g.ntiles;
     p.N = N;
     p.thr = thr;
     p.seed = seed;
     p.spin = c->spin;
     p.bond = c->bond_bytes;
     p.label = c->label;
-    p.size = c->psize;
-    p.open = c->open ? 1 : 0;
+    p.code = c->code;
+    p.cross = c->cross;
+    p.npar = c->npar;
+    p.nkey = c->nkey;
+    p.nfinal = c->nfinal;
+    p.nstate = c->nstate;
+    p.psize = c->psize;
+    p.csize = c->csize;
     if (pcc) {
-        // per axis: candidate ids of the roots, the candidates of the face
-        // (F = L^(dim-1) sites), their counts and coverage (W words each)
+        // per node and axis the candidate ids of roots; per axis the
+        // candidates of the face (F = L^(dim-1) sites), their counts and
+        // coverage (W words each); per node its piece's coordinates
         const size_t F = dim == 2 ? (size_t)L : (size_t)L * L, W = ((size_t)L + 31) / 32;
         if ((e = dalloc(&c->thr_dev, 1)) != cudaSuccess) return fail(e);
-        if ((e = dalloc(&c->cid, (size_t)dim * N)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->cid, nt * S * (size_t)dim)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&c->pmask, nt * S * (size_t)g.pmask_words)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&c->cand, (size_t)dim * F)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&c->ncand, 4)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&c->cov, (size_t)dim * F * W)) != cudaSuccess) return fail(e);
-        if ((e = cudaMemsetAsync(c->cid, 0, (size_t)dim * N * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemsetAsync(c->cid, 0, nt * S * (size_t)dim * sizeof(int32_t), c->stream)) != cudaSuccess)
+            return fail(e);
         if ((e = cudaMemsetAsync(c->ncand, 0, 4 * sizeof(int32_t), c->stream)) != cudaSuccess) return fail(e);
         if ((e = cudaMemsetAsync(c->cov, 0, (size_t)dim * F * W * sizeof(uint32_t), c->stream)) != cudaSuccess)
             return fail(e);
@@ -735,6 +762,7 @@ int potts_create(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t thr, 
             cudaSuccess)
             return fail(e);
         p.thr_dev = c->thr_dev;
+        p.pmask = c->pmask;
         p.cid = c->cid;
         p.cand = c->cand;
         p.ncand = c->ncand;

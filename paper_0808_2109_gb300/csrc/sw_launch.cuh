@@ -32,27 +32,48 @@ __attribute__((visibility("hidden"))) cudaError_t enqueue_job_init(uint8_t *spin
 
 inline int slots_of(int TH) { return 2 * TW + 2 * TH; }
 
-// A q-state Potts lattice on the periodic d-dimensional torus (sw_potts.cu):
-// N = L^d sites; size is null unless cluster sizes are summed.
+// A q-state Potts lattice on the d-dimensional lattice (sw_potts.cu): N =
+// L^d sites cut into tiles (128 x 64 in 2D, 32 x 16 x 16 in 3D) of which the
+// kernels keep per-tile scratch as the 2D Ising path does: a 2-byte code per
+// site, crossing-bond bits and the face nodes' forest (parent, key, final,
+// the new state of a representative), and with RF_CSIZE the sizes of the
+// pieces and clusters at their nodes.
 struct PottsDev {
-    int32_t dim, L, q;
+    int32_t dim, L, q, flags;          // flags: RF_OPEN | RF_CSIZE | RF_PCC
+    int32_t ntx, nty, ntz, ntiles;     // tiles along x, y, z (1 in 2D)
     int64_t N;
     uint64_t thr, seed;
-    uint8_t *spin, *bond;
-    int32_t *label, *size;
-    int32_t open;              // open boundaries: no link leaves the lattice
+    uint8_t *spin, *bond;              // N states (read by launch 0, written by the last), N bond bytes
+    int32_t *label;                    // N labels of the last sweep
+    uint16_t *code;                    // ntiles * sites-per-tile
+    uint32_t *cross;                   // ntiles * cross words
+    int32_t *npar, *nkey;              // ntiles * slots
+    uint32_t *nfinal;                  // ntiles * slots: root, or FINAL_ALIAS | a representative
+    uint8_t *nstate;                   // ntiles * slots: a representative's new state
+    int32_t *psize, *csize;            // ntiles * slots (RF_CSIZE only)
     // PCC (null otherwise): the threshold lives on the device and follows the
-    // feedback; per axis a < dim, candidate ids of roots (cid + a N, id + 2),
-    // the candidates (cand + a F, F = L^(dim-1) face sites), their counts
+    // feedback; per node and axis a < dim, a root's candidate id (cid, id + 2),
+    // per border piece its occupied coordinates (pmask), per axis the
+    // candidates (cand + a F, F = L^(dim-1) face sites), their counts
     // (ncand[a]; ncand[3] counts finished decision blocks) and coverage
     // (cov + a F W, W = ceil(L / 32) words per candidate)
     uint64_t *thr_dev;
+    uint32_t *pmask;
     int32_t *cid, *cand, *ncand;
     uint32_t *cov;
 };
+
+// Tile counts and per-tile sizes of a Potts lattice's scratch.
+struct PottsGeometry {
+    int32_t ntx, nty, ntz, ntiles;
+    int32_t sites_per_tile, slots, cross_words, pmask_words;
+};
+__attribute__((visibility("hidden"))) void potts_geometry(int dim, int L, PottsGeometry *g);
 __attribute__((visibility("hidden"))) cudaError_t potts_enqueue_hot_start(const PottsDev &p, cudaStream_t st);
-__attribute__((visibility("hidden"))) cudaError_t potts_enqueue_sweep(const PottsDev &p, uint64_t sweep, DevObs *obs,
-                                                                      cudaStream_t st);
+// One call of nsweeps sweeps (observables into obs[0 .. nsweeps-1]).
+__attribute__((visibility("hidden"))) cudaError_t potts_enqueue_sweeps(const PottsDev &p, int nsweeps,
+                                                                       uint64_t sweep0, DevObs *obs,
+                                                                       cudaStream_t st);
 __attribute__((visibility("hidden"))) cudaError_t potts_enqueue_check(const uint8_t *s, int64_t n, int q, int32_t *bad,
                                                                       cudaStream_t st);
 

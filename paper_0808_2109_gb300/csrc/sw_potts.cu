@@ -1,31 +1,37 @@
-// sw_potts.cu -- the q-state Potts model on periodic 2D and 3D lattices
-// (sw_create_potts in include/swgpu.h): the cluster update of Sec. I with
-// "equal spins" read as "equal states", on the d-dimensional lattice the
-// paper states its method for (Sec. II).
+// sw_potts.cu -- the q-state Potts model on 2D and 3D lattices
+// (sw_create_potts, pcc_create_potts in include/swgpu.h): the cluster update
+// of Sec. I with "equal spins" read as "equal states", on the d-dimensional
+// lattice the paper states its method for (Sec. II), split as the 2D Ising
+// sweep of sw_device.cuh is (Sec. II.A's slaves and master inside one GPU):
 //
-// Per sweep, four kernels, the first two over bricks of sites (32 x 32 in 2D,
-// 8 x 8 x 8 in 3D):
-//   1. k_potts_local: the brick's states (with a halo on the + side) in shared
-//      memory, its bonds, and a shared-memory union-find over the bonds inside
-//      the brick; every site's label becomes its piece's minimum site;
-//   2. k_potts_cross: the bonds that leave a brick unite pieces in a global
-//      union-find over those labels (the smaller index wins, so roots are
-//      cluster minima);
-//   3. k_potts_resolve: every label becomes its cluster's root, piece sizes
-//      move to the roots, every site takes its cluster's new state, and the
-//      clusters are counted;
-//   4. k_potts_measure: the sums.
-// The tiled 2D Ising kernels keep spins as single bits and do not carry over
-// to q states or a third dimension.
+//   k_ptile   one CTA per tile (128 x 64 sites in 2D, 32 x 16 x 16 in 3D).
+//             It finishes sweep k-1 (each site's 2-byte tile-local cluster
+//             code, the border clusters' new states from the merged node
+//             table, the halo from the neighbours' tables, the observables)
+//             and starts sweep k on those states, which stay in shared
+//             memory: Philox bonds between equal states, a shared-memory
+//             union-find over the bonds inside the tile, the new state of
+//             every cluster that ends inside the tile, one node per site of
+//             each tile face, and the site codes.
+//   k_pmerge_union / k_pmerge_jump / k_pmerge_resolve
+//             the master's step 2: a union-find over the face nodes joined by
+//             the bonds that leave a tile (the wrapping links included),
+//             smaller key (cluster minimum) wins; then every representative
+//             node gets its cluster's root and new state.
+//   k_ppcc_candidates / k_ppcc_cover / k_ppcc_decide
+//             PCC (Sec. III): the extension rule per axis on the merged
+//             clusters, and the feedback on the threshold.
 //
 // Conventions (both sides implement them; the CPU oracle is the reference):
 //   - N = L^d sites, i = x + L*y (+ L*L*z); site i owns link dir = 0 (+x),
-//     1 (+y), 2 (+z) with index l = d*i + dir; bond byte bit dir.
+//     1 (+y), 2 (+z) with index l = d*i + dir; bond byte bit dir.  Under open
+//     boundaries the + link of the last coordinate along an axis does not
+//     exist.
 //   - A link between equal states bonds iff word (l mod 4) of Philox(l/4, k,
 //     BOND) < t, t = floor((1 - exp(-J/T)) 2^32).
-//   - A cluster with root r takes state floor(w q / 2^32), w = word (r mod 4)
-//     of Philox(r/4, k, QSPIN); the hot start is the same function of word
-//     (i mod 4) of Philox(i/4, 0, INIT).
+//   - A cluster with root r (its minimum site) takes state floor(w q / 2^32),
+//     w = word (r mod 4) of Philox(r/4, k, QSPIN); the hot start is the same
+//     function of word (i mod 4) of Philox(i/4, 0, INIT).
 //   - bond_sum = sum over links of (2 delta - 1), mag = sum over sites of
 //     (q [s_i = 0] - 1).
 #include "swgpu.h"
@@ -36,412 +42,1054 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
+#include <mutex>
 
 using namespace swg;
 
 namespace {
 
 constexpr uint32_t STREAM_QSPIN = 3;
-constexpr int PT = 256;   // threads per block
-constexpr int POTTS_BY2 = 16;   // rows of a 2D brick (16 measured best of 8, 16 and 32)
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr int PT = 256;   // threads of the per-site helper kernels
 
 __device__ __forceinline__ uint8_t potts_state(uint32_t w, int q)
 {
     return (uint8_t)(((uint64_t)w * (uint32_t)q) >> 32);
 }
 
-__device__ __forceinline__ int pfind(int32_t *lab, int x)
+// New state of the cluster whose root is global site r in sweep k.
+__device__ __forceinline__ uint8_t cluster_state(uint32_t r, uint32_t klo, uint32_t khi, uint32_t k0, uint32_t k1,
+                                                 int q)
 {
-    int p = gload(lab + x);
-    while (p != x) {
-        const int gp = gload(lab + p);
-        if (gp != p) *(volatile int32_t *)(lab + x) = gp;   // halving: an ancestor
-        x = gp;
-        p = gload(lab + x);
-    }
-    return x;
+    const U4 u = philox4x32_10(r >> 2, klo, khi, STREAM_QSPIN, k0, k1);
+    return potts_state(u4_word(u, (int)(r & 3u)), q);
 }
 
-// Hang the larger root under the smaller (roots end as cluster minima).
-__device__ __forceinline__ void punite(int32_t *lab, int a, int b)
-{
-    for (;;) {
-        a = pfind(lab, a);
-        b = pfind(lab, b);
-        if (a == b) return;
-        if (a > b) {
-            const int t = a;
-            a = b;
-            b = t;
-        }
-        if (atomicCAS(lab + b, b, a) == b) return;
-    }
-}
-
-__global__ void k_potts_hot_start(const PottsDev p)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.N) return;
-    const U4 r = philox4x32_10((uint32_t)(i >> 2), 0u, 0u, STREAM_INIT, (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-    p.spin[i] = potts_state(u4_word(r, (int)(i & 3)), p.q);
-}
-
-// Sites of a brick, one thread each, and its shared states with a halo of
-// one site on the + side of every axis.
+// ------------------------------------------------------------ tile geometry
+// A tile is TX x TY (x TZ) sites; its rows (y, z) are row index r = y + TY z,
+// each of TWW 32-site words.  One thread per word: NT = 256 threads.
+// Face nodes: for each axis a, a "-" face (local coordinate a = 0) and a "+"
+// face (the tile's last valid coordinate along a), each of Fa slots indexed
+// by the site's other coordinates (axis 0: y + TY z; axis 1: x + TX z; axis
+// 2: x + TX y).  Slot layout: [x-, x+, y-, y+, z-, z+].
 template <int DIM>
-struct Brick {
-    static constexpr int BX = DIM == 2 ? 32 : 8, BY = DIM == 2 ? POTTS_BY2 : 8, BZ = DIM == 2 ? 1 : 8;
-    static constexpr int NT = BX * BY * BZ;
-    static constexpr int HX = BX + 1, HY = BY + 1, HZ = DIM == 2 ? 1 : BZ + 1;
+struct PG {
+    static constexpr int TX = DIM == 2 ? 128 : 32;
+    static constexpr int TY = DIM == 2 ? 64 : 16;
+    static constexpr int TZ = DIM == 2 ? 1 : 16;
+    static constexpr int TWW = TX / 32;
+    static constexpr int NR = TY * TZ;          // rows
+    static constexpr int NT = NR * TWW;         // threads
+    static constexpr int NW = NT / 32;          // warps
+    static constexpr int NS = TX * TY * TZ;     // sites
+    static constexpr int PW = TX + 1;           // forest row pitch (rows on distinct banks)
+    static constexpr int RS = TX + 4;           // state row pitch in bytes (the halo column, padded)
+    static constexpr int HY = TY + 1, HZ = DIM == 2 ? 1 : TZ + 1;
+    static constexpr int F0 = TY * TZ, F1 = TX * TZ, F2 = DIM == 3 ? TX * TY : 0;
+    static constexpr int FT = F0 + F1 + F2;     // + face sites: crossing links, and halo sites
+    static constexpr int S = 2 * FT;            // node slots
+    static constexpr int CW = FT / 32;          // crossing-bit words
+    static constexpr int PMW = DIM == 2 ? 6 : 2;   // PCC coverage words of a piece
+    static constexpr int NQ = NS / 8 / NT;      // 8-site groups per thread
+    static constexpr int SPT = (S + NT - 1) / NT;  // node slots per thread
+    static_assert(NT == 256 && NQ == 4, "tile launch shape");
+    static_assert(F0 % 32 == 0 && F1 % 32 == 0 && F2 % 32 == 0, "faces of whole words");
+    static_assert(S <= 0x7FFF, "slots fit the code");
 };
 
-// Bonds of every site's own links (Sec. I step 1); unions of the bonds inside
-// the brick (step 2) in shared memory, larger root under smaller (local order
-// is global order inside a brick, so a piece's root is its minimum site).
-// Every site's label: its piece's minimum site; with cluster sizes, each piece
-// root's size holds the piece's site count and every other size is zero.
 template <int DIM>
-__global__ void __launch_bounds__(Brick<DIM>::NT) k_potts_local(const PottsDev p, uint64_t k)
+__device__ __forceinline__ int face_off(int a, int side)
 {
-    using B = Brick<DIM>;
-    __shared__ uint8_t st[B::HZ][B::HY][B::HX];
-    __shared__ int par[B::NT];
-    __shared__ int cnt[B::NT];
-    __shared__ __align__(16) uint32_t uw[DIM * B::NT];   // the BOND words of the brick's links
-    const int L = p.L;
-    const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
-    const uint32_t uL = (uint32_t)L;
-    // past the lattice's last site the halo wraps (a lattice narrower than a
-    // brick wraps more than once)
-    auto wrap = [L](int g) { return (uint32_t)(g < L ? g : g % L); };
-    if (DIM == 2) {
-        // a warp per halo row: lane x loads site x0 + x, lane 0 also the
-        // halo column's site
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const uint32_t gx = wrap(x0 + lane), gh = wrap(x0 + B::BX);
-        for (int hy = warp; hy < B::HY; hy += B::NT / 32) {
-            const uint8_t *row = p.spin + (size_t)uL * wrap(y0 + hy);
-            st[0][hy][lane] = row[gx];
-            if (lane == 0) st[0][hy][B::BX] = row[gh];
-        }
-    } else if ((L & 7) == 0) {
-        // L a multiple of 8: each halo row's 8 brick sites are one aligned
-        // 8-byte load (x0 is a multiple of 8, so is every row start); thread
-        // t < 81 loads row (t mod 9, t / 9) and its halo site
-        if (threadIdx.x < B::HY * B::HZ) {
-            const int hy = threadIdx.x % B::HY, hz = threadIdx.x / B::HY;
-            const size_t row = (size_t)uL * (wrap(y0 + hy) + (size_t)uL * wrap(z0 + hz));
-            const uint2 v = *reinterpret_cast<const uint2 *>(p.spin + row + (uint32_t)x0);
+    using G = PG<DIM>;
+    return (a == 0 ? 0 : a == 1 ? 2 * G::F0 : 2 * G::F0 + 2 * G::F1) +
+           side * (a == 0 ? G::F0 : a == 1 ? G::F1 : G::F2);
+}
+
+// The local site of slot s (false past the tile's valid sites).
+template <int DIM>
+__device__ __forceinline__ bool slot_xyz(int s, const int (&e)[3], int &x, int &y, int &z)
+{
+    using G = PG<DIM>;
+    if (s < 2 * G::F0) {
+        const int side = s >= G::F0, f = s - side * G::F0;
+        x = side ? e[0] - 1 : 0;
+        y = f % G::TY;
+        z = f / G::TY;
+    } else if (s < 2 * G::F0 + 2 * G::F1) {
+        const int s2 = s - 2 * G::F0, side = s2 >= G::F1, f = s2 - side * G::F1;
+        y = side ? e[1] - 1 : 0;
+        x = f % G::TX;
+        z = f / G::TX;
+    } else {
+        const int s2 = s - 2 * G::F0 - 2 * G::F1, side = s2 >= G::F2, f = s2 - side * G::F2;
+        z = side ? e[2] - 1 : 0;
+        x = f % G::TX;
+        y = f / G::TX;
+    }
+    return x < e[0] && y < e[1] && z < e[2];
+}
+
+// A slot on a "-" face: the halo of the neighbour on that side reads its final.
+template <int DIM>
+__device__ __forceinline__ bool minus_slot(int s)
+{
+    using G = PG<DIM>;
+    return s < G::F0 || (s >= 2 * G::F0 && s < 2 * G::F0 + G::F1) ||
+           (DIM == 3 && s >= 2 * G::F0 + 2 * G::F1 && s < 2 * G::F0 + 2 * G::F1 + G::F2);
+}
+
+struct PTile {
+    int c[3];      // tile coordinates
+    int o[3];      // origin (sites)
+    int e[3];      // extent (valid sites; 1 along z in 2D)
+    int nb[3];     // tile index of the + neighbour along each axis (periodic)
+    uint32_t gbase;   // global index of local site (0, 0, 0)
+};
+
+template <int DIM>
+__device__ __forceinline__ PTile ptile_of(const PottsDev &p, int lt)
+{
+    using G = PG<DIM>;
+    PTile t;
+    const int n[3] = {p.ntx, p.nty, p.ntz};
+    const int T[3] = {G::TX, G::TY, G::TZ};
+    t.c[0] = lt % p.ntx;
+    t.c[1] = (lt / p.ntx) % p.nty;
+    t.c[2] = lt / (p.ntx * p.nty);
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                st[hz][hy][x] = (uint8_t)(v.x >> (8 * x));
-                st[hz][hy][4 + x] = (uint8_t)(v.y >> (8 * x));
+    for (int a = 0; a < 3; ++a) {
+        t.o[a] = t.c[a] * T[a];
+        t.e[a] = a < DIM ? min(T[a], p.L - t.o[a]) : 1;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int cc[3] = {t.c[0], t.c[1], t.c[2]};
+        cc[a] = (cc[a] + 1) % n[a];
+        t.nb[a] = cc[0] + n[0] * (cc[1] + n[1] * cc[2]);
+    }
+    const uint32_t uL = (uint32_t)p.L;
+    t.gbase = (uint32_t)t.o[0] + uL * ((uint32_t)t.o[1] + uL * (uint32_t)t.o[2]);
+    return t;
+}
+
+// ------------------------------------------------- 3D tile union-find
+// Connected components of the bonds inside a 32 x 16 x 16 tile (X: +x bonds,
+// whose link leaving the tile's last column is ignored; Y, Z: +y / +z bonds,
+// ignored in the tile's last row / layer).  The forest lives on run heads (a
+// run = maximal chain of x bonds in a row; its head is its leftmost site):
+//   1. warp w holds the rows y = 4 (w mod 4) + (lane mod 4), z = 8 (w / 4) +
+//      lane / 4; lane = row unites its runs with those of the next row along
+//      y and along z inside the warp, skipping a bond when the bond of the
+//      same direction to its left joins the same two runs;
+//   2. the y and z bonds between the warps' row blocks, one thread per link,
+//      with the same skip rule.
+// Links hang the larger root under the smaller, so roots are piece minima in
+// local row-major order, which is global order.
+__device__ void tile_label3(volatile int *par, const uint32_t (*X)[1], const uint32_t (*Y)[1],
+                            const uint32_t (*Z)[1], int tw, int th, int td)
+{
+    using G = PG<3>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int yy = lane & 3, zz = lane >> 2;
+    const int y = 4 * (warp & 3) + yy, z = 8 * (warp >> 2) + zz;
+    const int r = y + G::TY * z;
+    const bool ok = y < th && z < td;
+    const uint32_t vx = valid_mask(0, tw - 1);
+    const uint32_t heads = run_heads(ok ? X[r][0] & vx : 0u);
+    const uint32_t hy = __shfl_down_sync(FULL, heads, 1);   // row (y + 1, z) when yy < 3
+    const uint32_t hz = __shfl_down_sync(FULL, heads, 4);   // row (y, z + 1) when zz < 7
+    const int base = r * G::PW;
+    if (ok) {
+#pragma unroll
+        for (int x = 0; x < 32; ++x) par[base + x] = base + x;
+    }
+    __syncwarp();
+    const uint32_t vy = (ok && yy < 3 && y + 1 < th) ? Y[r][0] : 0u;
+    const uint32_t vz = (ok && zz < 7 && z + 1 < td) ? Z[r][0] : 0u;
+    const uint32_t uy = vy & (~(vy << 1) | heads | hy);
+    const uint32_t uz = vz & (~(vz << 1) | heads | hz);
+    int pa = -1, pb = -1, pr = 0;
+    for (uint32_t b = uy; b; b &= b - 1) {
+        const int x = __ffs(b) - 1;
+        const int ha = head_of(heads, base, x), hb = head_of(hy, base + G::PW, x);
+        pr = sunite_root(par, ha == pa ? pr : ha, hb == pb ? pr : hb);
+        pa = ha;
+        pb = hb;
+    }
+    pa = pb = -1;
+    for (uint32_t b = uz; b; b &= b - 1) {
+        const int x = __ffs(b) - 1;
+        const int ha = head_of(heads, base, x), hb = head_of(hz, base + G::TY * G::PW, x);
+        pr = sunite_root(par, ha == pa ? pr : ha, hb == pb ? pr : hb);
+        pa = ha;
+        pb = hb;
+    }
+    __syncthreads();
+    // y bonds from rows y = 3, 7, 11 (every z), z bonds from layer z = 7 (every y)
+    constexpr int NYB = 3 * G::TZ * 32, NZB = G::TY * 32;
+    for (int q = threadIdx.x; q < NYB + NZB; q += G::NT) {
+        int A, B, x;
+        uint32_t bw;
+        if (q < NYB) {
+            const int bnd = q / (G::TZ * 32), rem = q % (G::TZ * 32);
+            const int zq = rem >> 5, yq = 4 * bnd + 3;
+            x = rem & 31;
+            if (yq + 1 >= th || zq >= td) continue;
+            A = yq + G::TY * zq;
+            B = A + 1;
+            bw = Y[A][0];
+        } else {
+            const int rem = q - NYB, yq = rem >> 5;
+            x = rem & 31;
+            if (8 >= td || yq >= th) continue;
+            A = yq + G::TY * 7;
+            B = A + G::TY;
+            bw = Z[A][0];
+        }
+        if (!((bw >> x) & 1u)) continue;
+        const uint32_t hA = run_heads(X[A][0] & vx), hB = run_heads(X[B][0] & vx);
+        if (x > 0 && ((bw >> (x - 1)) & 1u) && !((hA >> x) & 1u) && !((hB >> x) & 1u)) continue;
+        sunite(par, head_of(hA, A * G::PW, x), head_of(hB, B * G::PW, x));
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ shared layout
+template <int DIM>
+struct PSmem {
+    using G = PG<DIM>;
+    int par[G::NR * G::PW];                 // union-find forest over run heads (padded rows)
+    uint8_t st[G::HZ][G::HY][G::RS];        // states; row TY, layer TZ and column tw: + halo
+    uint32_t bx[G::NR][G::TWW];             // +x bonds (bit x of word c: site 32 c + x)
+    uint32_t by[G::NR][G::TWW];             // +y bonds
+    uint32_t bz[DIM == 3 ? G::NR : 1][G::TWW];   // +z bonds
+    union {
+        uint8_t fst[G::S];                  // finish: new states of the tile's pieces, by slot
+        long long red[G::NW][4];            // the reduction that ends each half
+    } u;
+    uint32_t pm[G::S][G::PMW];              // PCC: coordinates each border piece occupies
+};
+
+template <int DIM>
+constexpr size_t ptile_smem(bool pcc)
+{
+    return pcc ? sizeof(PSmem<DIM>) : offsetof(PSmem<DIM>, pm);
+}
+
+// bytes 0 .. n-1 of a word (n in [0, 4])
+__device__ __forceinline__ uint32_t byte_mask(int n)
+{
+    return n >= 4 ? 0xFFFFFFFFu : (n <= 0 ? 0u : (1u << (8 * n)) - 1u);
+}
+
+// ----------------------------------------------------------------- k_ptile
+// Launch j finishes sweep j-1 (j >= 1) and starts sweep j (j < nsweeps).
+// F: FEAT_* bits compiled in (0: periodic plain lattices only).
+template <int DIM, int F>
+__global__ void __launch_bounds__(PG<DIM>::NT, 4)
+    k_ptile(const PottsDev p, int j, int nsweeps, uint64_t sweep0, DevObs *obs)
+{
+    using G = PG<DIM>;
+    constexpr int NT = G::NT, NW = G::NW, S = G::S, TWW = G::TWW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PSmem<DIM> &sm = *reinterpret_cast<PSmem<DIM> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lt = blockIdx.x;
+    if (lt >= p.ntiles) return;
+    const bool fin = j >= 1, start = j < nsweeps;
+    const PTile t = ptile_of<DIM>(p, lt);
+    const int tw = t.e[0], th = t.e[1], td = t.e[2];
+    const uint32_t uL = (uint32_t)p.L;
+    const int q = p.q;
+    const bool open = (F & FEAT_OPEN) && (p.flags & RF_OPEN);
+    const bool open_x = open && t.c[0] == p.ntx - 1;
+    const bool open_y = open && t.c[1] == p.nty - 1;
+    const bool open_z = DIM == 3 && open && t.c[2] == p.ntz - 1;
+    const bool csz = (F & FEAT_CSIZE) && (p.flags & RF_CSIZE);
+    const bool pcc = (F & FEAT_PCC) && (p.flags & RF_PCC);
+    uint16_t *code = p.code + (size_t)lt * G::NS;
+    const size_t nbase = (size_t)lt * S;
+    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    // global index of a local site, and of a forest index
+    auto gidx = [&](int x, int y, int z) { return t.gbase + (uint32_t)x + uL * ((uint32_t)y + uL * (uint32_t)z); };
+    auto gfor = [&](int fi) {
+        const int r = fi / G::PW;
+        return gidx(fi - r * G::PW, r % G::TY, r / G::TY);
+    };
+    // local site of 8-site group idx (row-major order), false past the valid rows
+    auto group = [&](int idx, int &x, int &y, int &z) {
+        const int li = 8 * idx, r = li / G::TX;
+        x = li - r * G::TX;
+        y = r % G::TY;
+        z = r / G::TY;
+        return y < th && z < td;
+    };
+    // intra-tile x bonds of word (r, c): the link leaving the tile's last column is ignored
+    auto ih = [&](int r, int c) { return sm.bx[r][c] & valid_mask(c, tw - 1); };
+
+    if (fin) {
+        // ---- finish sweep j-1: every site's new state
+        const bool last = j == nsweeps;
+        uint4 cv[G::NQ];
+        const uint4 *code4 = reinterpret_cast<const uint4 *>(code);
+#pragma unroll
+        for (int qq = 0; qq < G::NQ; ++qq) {
+            int x, y, z;
+            const int idx = tid + qq * NT;
+            cv[qq] = group(idx, x, y, z) ? code4[idx] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        {
+            const uint32_t *ns4 = reinterpret_cast<const uint32_t *>(p.nstate + nbase);
+            uint32_t *fs4 = reinterpret_cast<uint32_t *>(sm.u.fst);
+            for (int w = tid; w < S / 4; w += NT) fs4[w] = ns4[w];
+        }
+        // the + halo: new states of the neighbours' "-" face sites, through
+        // their finals (a representative's own, or an alias of one)
+        constexpr int HPT = (G::FT + NT - 1) / NT;
+        uint32_t hf[HPT];
+        int hnode[HPT], hpos[HPT];
+#pragma unroll
+        for (int qq = 0; qq < HPT; ++qq) {
+            const int h = tid + qq * NT;
+            hpos[qq] = -1;
+            hnode[qq] = 0;
+            if (h < G::F0) {
+                const int y = h % G::TY, z = h / G::TY;
+                if (y < th && z < td) {
+                    hnode[qq] = t.nb[0] * S + face_off<DIM>(0, 0) + h;
+                    hpos[qq] = (z * G::HY + y) * G::RS + tw;
+                }
+            } else if (h < G::F0 + G::F1) {
+                const int f = h - G::F0, x = f % G::TX, z = f / G::TX;
+                if (x < tw && z < td) {
+                    hnode[qq] = t.nb[1] * S + face_off<DIM>(1, 0) + f;
+                    hpos[qq] = (z * G::HY + th) * G::RS + x;
+                }
+            } else if (h < G::FT) {
+                const int f = h - G::F0 - G::F1, x = f % G::TX, y = f / G::TX;
+                if (x < tw && y < th) {
+                    hnode[qq] = t.nb[2] * S + face_off<DIM>(2, 0) + f;
+                    hpos[qq] = (td * G::HY + y) * G::RS + x;
+                }
             }
-            st[hz][hy][B::BX] = p.spin[row + wrap(x0 + B::BX)];
+            hf[qq] = hpos[qq] >= 0 ? p.nfinal[hnode[qq]] : 0u;
+        }
+        __syncthreads();
+        uint8_t *st = &sm.st[0][0][0];
+#pragma unroll
+        for (int qq = 0; qq < G::NQ; ++qq) {
+            int x, y, z;
+            const int idx = tid + qq * NT;
+            if (!group(idx, x, y, z)) continue;
+            const uint32_t wv[4] = {cv[qq].x, cv[qq].y, cv[qq].z, cv[qq].w};
+            uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t u = (wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                const uint32_t s = (u & CODE_BORDER) ? sm.u.fst[u & 0x7FFFu] : (u & 0xFFu);
+                if (e < 4) lo |= s << (8 * e);
+                else hi |= s << (8 * (e - 4));
+            }
+            const int nval = min(8, tw - x);
+            uint8_t *row = st + (z * G::HY + y) * G::RS + x;
+            if (nval == 8) {
+                reinterpret_cast<uint32_t *>(row)[0] = lo;
+                reinterpret_cast<uint32_t *>(row)[1] = hi;
+            } else {
+                for (int e = 0; e < nval; ++e) row[e] = (uint8_t)((e < 4 ? lo >> (8 * e) : hi >> (8 * (e - 4))) & 0xFFu);
+            }
+            if (last) {
+                const uint32_t gi0 = gidx(x, y, z);
+                if (nval == 8 && (gi0 & 7u) == 0) {
+                    *reinterpret_cast<uint2 *>(p.spin + gi0) = make_uint2(lo, hi);
+                } else {
+                    for (int e = 0; e < nval; ++e)
+                        p.spin[gi0 + e] = (uint8_t)((e < 4 ? lo >> (8 * e) : hi >> (8 * (e - 4))) & 0xFFu);
+                }
+                // border sites' labels: their cluster's root (the interior
+                // clusters' were written when the sweep started)
+                for (int e = 0; e < nval; ++e) {
+                    const uint32_t u = (wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                    if (u & CODE_BORDER) p.label[gi0 + e] = (int32_t)(p.nfinal[nbase + (u & 0x7FFFu)] & ROOT_MASK);
+                }
+            }
+        }
+#pragma unroll
+        for (int qq = 0; qq < HPT; ++qq) {
+            if (hpos[qq] < 0) continue;
+            const uint32_t f = hf[qq];
+            st[hpos[qq]] = p.nstate[(f & FINAL_ALIAS) ? (size_t)(f & ~FINAL_ALIAS) : (size_t)hnode[qq]];
+        }
+        __syncthreads();
+        // observables of sweep j-1: every link that exists, every site
+        long long bs = 0, mag = 0;
+        for (int w = tid; w < G::NR * TWW; w += NT) {
+            const int r = w / TWW, c = w % TWW;
+            const int y = r % G::TY, z = r / G::TY;
+            if (y >= th || z >= td) continue;
+            const uint8_t *row = st + (z * G::HY + y) * G::RS;
+            const uint8_t *rowy = row + G::RS;
+            const uint8_t *rowz = row + G::HY * G::RS;
+            const bool dy = !(open_y && y == th - 1), dz = DIM == 3 && !(open_z && z == td - 1);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int x = 32 * c + 4 * m;
+                const int nv = min(4, tw - x);
+                if (nv <= 0) break;
+                const uint32_t cur = *reinterpret_cast<const uint32_t *>(row + x);
+                const uint32_t nxt = *reinterpret_cast<const uint32_t *>(row + x + 4);
+                const uint32_t right = __funnelshift_r(cur, nxt, 8);
+                const uint32_t vm = byte_mask(nv);
+                const int nr = min(4, tw - x - (open_x ? 1 : 0));
+                bs += 2 * (__popc(__vcmpeq4(cur, right) & byte_mask(nr)) >> 3) - max(nr, 0);
+                if (dy) {
+                    const uint32_t down = *reinterpret_cast<const uint32_t *>(rowy + x);
+                    bs += 2 * (__popc(__vcmpeq4(cur, down) & vm) >> 3) - nv;
+                }
+                if (dz) {
+                    const uint32_t back = *reinterpret_cast<const uint32_t *>(rowz + x);
+                    bs += 2 * (__popc(__vcmpeq4(cur, back) & vm) >> 3) - nv;
+                }
+                mag += (long long)q * (__popc(__vcmpeq4(cur, 0u) & vm) >> 3) - nv;
+            }
+        }
+        // clusters that touch a tile face: their sizes were summed at their
+        // root nodes by the merge; each root node is in exactly one tile
+        long long c2 = 0;
+        if (csz)
+            for (int s = tid; s < S; s += NT) {
+                const long long c = p.csize[nbase + s];
+                c2 += c * c;
+            }
+        long long v[4] = {bs, mag, c2, 0};
+        DevObs *o = obs + (j - 1);
+        unsigned long long *const dst[4] = {&o->bond_sum, &o->mag, &o->csize2, nullptr};
+        block_sum_atomic<NT, 4>(v, dst, sm.u.red);
+        __syncthreads();
+    }
+
+    if (!start) return;
+
+    // ---- start sweep j
+    const uint64_t k = sweep0 + (uint64_t)j;
+    const uint64_t thr = p.thr_dev ? *p.thr_dev : p.thr;
+    const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
+    if (!fin) {
+        // first sweep of the call: states and + halos from global memory
+        const int hrows = (th + 1) * (DIM == 3 ? td + 1 : 1);
+        for (int rw = warp; rw < hrows; rw += NW) {
+            const int hy = rw % (th + 1), hz = rw / (th + 1);
+            const uint32_t gy = (uint32_t)((t.o[1] + hy) % p.L), gz = DIM == 3 ? (uint32_t)((t.o[2] + hz) % p.L) : 0u;
+            const uint8_t *grow = p.spin + (size_t)uL * (gy + (size_t)uL * gz);
+            for (int x = lane; x <= tw; x += 32) {
+                int gx = t.o[0] + x;
+                if (gx >= p.L) gx -= p.L;
+                sm.st[hz][hy][x] = grow[gx];
+            }
+        }
+        __syncthreads();
+    }
+    if (pcc)
+        for (int w = tid; w < S * G::PMW; w += NT) (&sm.pm[0][0])[w] = 0u;
+    if (lt == 0 && tid == 0) {
+        obs[j].threshold = thr;
+        obs[j].spans_x = 0;
+        obs[j].spans_y = 0;
+    }
+
+    // Step 1 (Sec. I): bonds between equal states.
+    const bool any_bond = thr != 0;
+    const uint32_t tm1 = (uint32_t)(thr - 1);
+    // row (y, z) from its random bond bits (rx, ry, rz: bit x of word c set
+    // iff the link's Philox word is below the threshold)
+    auto store_row = [&](int y, int z, const uint32_t (&rx)[TWW], const uint32_t (&ry)[TWW],
+                         const uint32_t (&rz)[TWW]) {
+        const int r = y + G::TY * z;
+        const bool dy = !(open_y && y == th - 1), dz = !(open_z && z == td - 1);
+#pragma unroll
+        for (int c = 0; c < TWW; ++c) {
+            const int x = 32 * c + lane;
+            const uint8_t s = sm.st[z][y][x];
+            const uint32_t ex = __ballot_sync(FULL, s == sm.st[z][y][x + 1]);
+            const uint32_t ey = __ballot_sync(FULL, s == sm.st[z][y + 1][x]);
+            uint32_t ez = 0u;
+            if (DIM == 3) ez = __ballot_sync(FULL, s == sm.st[DIM == 3 ? z + 1 : z][y][x]);
+            const uint32_t vm = valid_mask(c, tw);
+            const uint32_t vr = open_x ? valid_mask(c, tw - 1) : vm;
+            if (lane == c) {
+                sm.bx[r][c] = rx[c] & ex & vr;
+                sm.by[r][c] = dy ? ry[c] & ey & vm : 0u;
+                if (DIM == 3) sm.bz[DIM == 3 ? r : 0][c] = dz ? rz[c] & ez & vm : 0u;
+            }
+        }
+    };
+    if constexpr (DIM == 2) {
+        // link l = 2i + d: sites 2m and 2m + 1 share Philox block m
+        // aligned row: lane l drew the blocks of sites (2l, 2l+1) (r0) and
+        // (64+2l, 65+2l) (r1); lane x of each 32-site word takes its two bits
+        // by shuffle
+        auto draws_aligned = [&](const U4 &r0, const U4 &r1, uint32_t (&rh)[TWW], uint32_t (&rv)[TWW]) {
+            const uint32_t nib0 = (below(r0.x, tm1) ? 1u : 0u) | (below(r0.y, tm1) ? 2u : 0u) |
+                                  (below(r0.z, tm1) ? 4u : 0u) | (below(r0.w, tm1) ? 8u : 0u);
+            const uint32_t nib1 = (below(r1.x, tm1) ? 1u : 0u) | (below(r1.y, tm1) ? 2u : 0u) |
+                                  (below(r1.z, tm1) ? 4u : 0u) | (below(r1.w, tm1) ? 8u : 0u);
+#pragma unroll
+            for (int c = 0; c < TWW; ++c) {
+                const uint32_t n = __shfl_sync(FULL, c < 2 ? nib0 : nib1, 16 * (c & 1) + (lane >> 1)) >>
+                                   (2 * (lane & 1));
+                rh[c] = __ballot_sync(FULL, n & 1u);
+                rv[c] = __ballot_sync(FULL, n & 2u);
+            }
+        };
+        uint32_t rz[TWW] = {};
+        if (any_bond && (uL & 1u) == 0) {
+            for (int y = warp; y < th; y += 2 * NW) {
+                const int y2 = y + NW;
+                const uint32_t b0 = ((t.gbase + (uint32_t)y * uL) >> 1) + lane;
+                const uint32_t b2 = ((t.gbase + (uint32_t)y2 * uL) >> 1) + lane;
+                const U4 r0 = philox4x32_10(b0, klo, khi, STREAM_BOND, k0, k1);
+                const U4 r1 = philox4x32_10(b0 + 32, klo, khi, STREAM_BOND, k0, k1);
+                const U4 r2 = philox4x32_10(b2, klo, khi, STREAM_BOND, k0, k1);
+                const U4 r3 = philox4x32_10(b2 + 32, klo, khi, STREAM_BOND, k0, k1);
+                uint32_t rh[TWW], rv[TWW], rh2[TWW], rv2[TWW];
+                draws_aligned(r0, r1, rh, rv);
+                draws_aligned(r2, r3, rh2, rv2);
+                store_row(y, 0, rh, rv, rz);
+                if (y2 < th) store_row(y2, 0, rh2, rv2, rz);
+            }
+        } else {
+            for (int y = warp; y < th; y += NW) {
+                const uint32_t G0 = t.gbase + (uint32_t)y * uL;
+                uint32_t rh[TWW], rv[TWW];
+#pragma unroll
+                for (int c = 0; c < TWW; ++c) {
+                    rh[c] = rv[c] = 0u;
+                    if (any_bond) {
+                        // odd L: a row may start on an odd site; every site draws its block
+                        const uint32_t gi = G0 + 32 * c + lane;
+                        const U4 r = philox4x32_10(gi >> 1, klo, khi, STREAM_BOND, k0, k1);
+                        const bool odd = gi & 1u;
+                        rh[c] = __ballot_sync(FULL, below(odd ? r.z : r.x, tm1));
+                        rv[c] = __ballot_sync(FULL, below(odd ? r.w : r.y, tm1));
+                    }
+                }
+                store_row(y, 0, rh, rv, rz);
+            }
         }
     } else {
-        for (int q = threadIdx.x; q < B::HX * B::HY * B::HZ; q += B::NT) {
-            const int hx = q % B::HX, hy = (q / B::HX) % B::HY, hz = q / (B::HX * B::HY);
-            const uint32_t gx = wrap(x0 + hx), gy = wrap(y0 + hy), gz = wrap(z0 + hz);
-            st[hz][hy][hx] = p.spin[gx + uL * (gy + uL * gz)];
+        // link l = 3i + d.  When 4 divides L every row starts on a multiple
+        // of 4, so its 96 links are exactly the 24 Philox blocks from 3 i0 / 4:
+        // lane b < 24 draws block b, and lane x takes bits 3x + d of the row's
+        // link string from four ballots (one per word of a block)
+        const int nrows = th * td;
+        auto bits_of = [&](const uint32_t (&B)[4], int l) { return (B[l & 3] >> (l >> 2)) & 1u; };
+        auto row_aligned = [&](const U4 &u, uint32_t (&rx)[1], uint32_t (&ry)[1], uint32_t (&rz)[1]) {
+            const bool act = lane < 24;
+            uint32_t B[4];
+            B[0] = __ballot_sync(FULL, act && below(u.x, tm1));
+            B[1] = __ballot_sync(FULL, act && below(u.y, tm1));
+            B[2] = __ballot_sync(FULL, act && below(u.z, tm1));
+            B[3] = __ballot_sync(FULL, act && below(u.w, tm1));
+            const int l = 3 * lane;
+            rx[0] = __ballot_sync(FULL, bits_of(B, l));
+            ry[0] = __ballot_sync(FULL, bits_of(B, l + 1));
+            rz[0] = __ballot_sync(FULL, bits_of(B, l + 2));
+        };
+        if (any_bond && (uL & 3u) == 0) {
+            for (int rw = warp; rw < nrows; rw += 2 * NW) {
+                const int rw2 = rw + NW;
+                const int y = rw % th, z = rw / th, y2 = rw2 % th, z2 = rw2 / th;
+                const uint32_t m0 = 3u * (gidx(0, y, z) >> 2), m2 = 3u * (gidx(0, y2, z2) >> 2);
+                const U4 u0 = philox4x32_10(m0 + (uint32_t)lane, klo, khi, STREAM_BOND, k0, k1);
+                const U4 u2 = philox4x32_10(m2 + (uint32_t)lane, klo, khi, STREAM_BOND, k0, k1);
+                uint32_t rx[1], ry[1], rz[1], rx2[1], ry2[1], rz2[1];
+                row_aligned(u0, rx, ry, rz);
+                row_aligned(u2, rx2, ry2, rz2);
+                store_row(y, z, rx, ry, rz);
+                if (rw2 < nrows) store_row(y2, z2, rx2, ry2, rz2);
+            }
+        } else {
+            for (int rw = warp; rw < nrows; rw += NW) {
+                const int y = rw % th, z = rw / th;
+                uint32_t rx[1] = {0u}, ry[1] = {0u}, rz[1] = {0u};
+                if (any_bond) {
+                    // each site's three links span one or two blocks
+                    const uint32_t l0 = 3u * gidx(lane, y, z);
+                    const uint32_t m0 = l0 >> 2, m1 = (l0 + 2u) >> 2;
+                    const U4 u0 = philox4x32_10(m0, klo, khi, STREAM_BOND, k0, k1);
+                    U4 u1 = u0;
+                    if (m1 != m0) u1 = philox4x32_10(m1, klo, khi, STREAM_BOND, k0, k1);
+                    bool bit[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const uint32_t l = l0 + (uint32_t)d;
+                        bit[d] = below(u4_word((l >> 2) == m0 ? u0 : u1, (int)(l & 3u)), tm1);
+                    }
+                    rx[0] = __ballot_sync(FULL, bit[0]);
+                    ry[0] = __ballot_sync(FULL, bit[1]);
+                    rz[0] = __ballot_sync(FULL, bit[2]);
+                }
+                store_row(y, z, rx, ry, rz);
+            }
         }
     }
-    const int t = threadIdx.x;
-    const int lx = t % B::BX, ly = (t / B::BX) % B::BY, lz = t / (B::BX * B::BY);
-    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-    const bool valid = gx < L && gy < L && (DIM == 2 || gz < L);
-    const uint32_t i = (uint32_t)gx + uL * ((uint32_t)gy + uL * (uint32_t)gz);   // N <= 2^30
-    par[t] = t;
-    if (p.size) cnt[t] = 0;
+    __syncthreads();
+
+    long long nb = 0;
+    for (int w = tid; w < G::NR * TWW; w += NT) {
+        const int r = w / TWW, c = w % TWW;
+        const int y = r % G::TY, z = r / G::TY;
+        if (y >= th || z >= td) continue;
+        nb += __popc(sm.bx[r][c]) + __popc(sm.by[r][c]) + (DIM == 3 ? __popc(sm.bz[DIM == 3 ? r : 0][c]) : 0);
+    }
+    // crossing bonds, bit f of face a at word (f / 32) of that face's block:
+    // x face f = r (the row), y face f = x + TX z, z face f = x + TX y
+    {
+        uint32_t *cross = p.cross + (size_t)lt * G::CW;
+        for (int qq = warp; qq < G::F0 / 32; qq += NW) {
+            const int r = 32 * qq + lane, y = r % G::TY, z = r / G::TY;
+            const int bit = (y < th && z < td) ? (sm.bx[r][(tw - 1) >> 5] >> ((tw - 1) & 31)) & 1 : 0;
+            const uint32_t word = __ballot_sync(FULL, bit);
+            if (lane == 0) cross[qq] = word;
+        }
+        for (int w = tid; w < G::F1 / 32; w += NT) {
+            const int c = w % TWW, z = w / TWW;
+            cross[G::F0 / 32 + w] = z < td ? sm.by[(th - 1) + G::TY * z][c] : 0u;
+        }
+        if (DIM == 3)
+            for (int w = tid; w < G::F2 / 32; w += NT) {
+                const int c = w % TWW, y = w / TWW;
+                cross[(G::F0 + G::F1) / 32 + w] = y < th ? sm.bz[DIM == 3 ? y + G::TY * (td - 1) : 0][c] : 0u;
+            }
+    }
+    const bool last_start = j == nsweeps - 1;
+    if (last_start) {
+        // the last sweep of the call keeps its bond bytes
+        for (int rw = warp; rw < th * td; rw += NW) {
+            const int y = rw % th, z = rw / th, r = y + G::TY * z;
+            const uint32_t g0 = gidx(0, y, z);
+#pragma unroll
+            for (int c = 0; c < TWW; ++c) {
+                const int x = 32 * c + lane;
+                if (x >= tw) break;
+                uint32_t b = ((sm.bx[r][c] >> lane) & 1u) | (((sm.by[r][c] >> lane) & 1u) << 1);
+                if (DIM == 3) b |= ((sm.bz[DIM == 3 ? r : 0][c] >> lane) & 1u) << 2;
+                p.bond[g0 + (uint32_t)x] = (uint8_t)b;
+            }
+        }
+    }
+
+    // Step 2 inside the tile
+    if constexpr (DIM == 2)
+        tile_label<64>(sm.par, sm.bx, sm.by, th, tw);
+    else
+        tile_label3(sm.par, sm.bx, sm.by, sm.bz, tw, th, td);
+
+    // One node per face site: key = global index of the piece's local root,
+    // parent = the piece's first face slot (the representative).
+    int rs[G::SPT];
+#pragma unroll
+    for (int qq = 0; qq < G::SPT; ++qq) {
+        const int s = tid + qq * NT;
+        int x, y, z;
+        rs[qq] = -1;
+        if (s < S && slot_xyz<DIM>(s, t.e, x, y, z)) {
+            const int r = y + G::TY * z, c = x >> 5;
+            rs[qq] = sroot(sm.par, head_of(run_heads(ih(r, c)), r * G::PW + 32 * c, x & 31));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int qq = 0; qq < G::SPT; ++qq)
+        if (rs[qq] >= 0) atomicMin((int *)&sm.par[rs[qq]], (int)(INFO_BORDER | (uint32_t)(tid + qq * NT)));
+    __syncthreads();
+#pragma unroll
+    for (int qq = 0; qq < G::SPT; ++qq) {
+        const int s = tid + qq * NT;
+        if (s >= S) break;
+        const size_t node = nbase + s;
+        if (rs[qq] >= 0) {
+            const int rep = sm.par[rs[qq]] & 0x7FFF;
+            p.npar[node] = (int32_t)(nbase + rep);
+            p.nkey[node] = (int32_t)(gfor(rs[qq]) | (rep == s ? KEY_REP : 0u));
+        } else {
+            p.npar[node] = (int32_t)node;
+            p.nkey[node] = (int32_t)KEY_NONE;
+        }
+        if (csz) p.csize[node] = 0;   // the merge adds piece sizes at root nodes
+    }
+    // Every run head learns its root; every interior root gets its record:
+    // its cluster's new state (Sec. I step 3, drawn here), and is counted.
+    // A walk stops at a root, a border record or an interior record; each
+    // thread writes only its own heads, so concurrent walks see ancestors.
+    long long ncl_interior = 0;
+    const int nrows = th * td;
+    for (int w = tid; w < nrows * TWW; w += NT) {
+        const int rr = w % nrows, c = w / nrows;   // a warp covers consecutive rows
+        const int y = rr % th, z = rr / th, r = y + G::TY * z;
+        const int base = r * G::PW + 32 * c;
+        for (uint32_t bits = run_heads(ih(r, c)); bits; bits &= bits - 1) {
+            const int hx = __ffs(bits) - 1;
+            const int hd = base + hx;
+            int x = hd, pp = sm.par[x];
+            while (pp != x && pp >= 0 && (uint32_t)pp < INFO_INTERIOR) {
+                x = pp;
+                pp = sm.par[x];
+            }
+            if (x != hd) {
+                sm.par[hd] = x;
+            } else if (pp == hd && 32 * c + hx < tw) {
+                const uint8_t s = cluster_state(gidx(32 * c + hx, y, z), klo, khi, k0, k1, q);
+                sm.par[hd] = (int)(INFO_INTERIOR | (uint32_t)s);
+                ++ncl_interior;
+            }
+        }
+    }
+    __syncthreads();
+    if (csz) {
+        // cluster sizes: every run adds its length to bits 16-30 of its root's
+        // record (a piece or cluster holds at most 8192 sites); the codes
+        // below read bits 0-15 only
+        for (int w = tid; w < nrows * TWW; w += NT) {
+            const int rr = w % nrows, c = w / nrows;
+            const int y = rr % th, z = rr / th, r = y + G::TY * z;
+            const int base = r * G::PW + 32 * c;
+            const int vw = min(32, tw - 32 * c);
+            for (uint32_t bits = run_heads(ih(r, c)); bits;) {
+                const int hx = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (hx >= vw) break;
+                const int nx = bits ? __ffs(bits) - 1 : 32;
+                const int v = sm.par[base + hx];
+                const int root = (v < 0 || (uint32_t)v >= INFO_INTERIOR) ? base + hx : v;
+                atomicAdd((int *)&sm.par[root], (min(nx, vw) - hx) << 16);
+            }
+        }
+        __syncthreads();
+    }
+    // Every site's 2-byte code (the low half of its root's record): border
+    // pieces by representative slot, interior clusters by new state.
+    uint4 *code4 = reinterpret_cast<uint4 *>(code);
+#pragma unroll
+    for (int qq = 0; qq < G::NQ; ++qq) {
+        int xb, y, z;
+        const int idx = tid + qq * NT;
+        if (!group(idx, xb, y, z)) continue;
+        const int r = y + G::TY * z, c = xb >> 5;
+        const uint32_t heads = run_heads(ih(r, c));
+        const int base = r * G::PW + 32 * c;
+        const uint32_t gi0 = gidx(xb, y, z);
+        uint32_t wv[4] = {0u, 0u, 0u, 0u};
+        int slot = -1;   // PCC: border piece of the sites gathered in cols
+        uint32_t cols = 0u;
+        int info = 0, root = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int x = xb + e;
+            if (x >= tw) break;
+            if (e == 0 || ((heads >> (x & 31)) & 1u)) {
+                const int hd = e == 0 ? head_of(heads, base, x & 31) : base + (x & 31);
+                const int v = sm.par[hd];
+                if ((uint32_t)v >= INFO_INTERIOR) {   // records: negative or >= INFO_INTERIOR
+                    info = v;
+                    root = hd;
+                } else {
+                    info = sm.par[v];
+                    root = v;
+                }
+            }
+            wv[e >> 1] |= ((uint32_t)info & 0xFFFFu) << (16 * (e & 1));
+            if (last_start && info >= 0) p.label[gi0 + e] = (int32_t)gfor(root);
+            if (pcc && info < 0) {
+                const int sl = info & 0x7FFF;
+                if (sl != slot) {
+                    if (slot >= 0) {
+                        if (DIM == 2) {
+                            atomicOr(&sm.pm[slot][c], cols);
+                            atomicOr(&sm.pm[slot][4 + (y >> 5)], 1u << (y & 31));
+                        } else {
+                            atomicOr(&sm.pm[slot][0], cols);
+                            atomicOr(&sm.pm[slot][1], (1u << y) | (1u << (16 + z)));
+                        }
+                    }
+                    slot = sl;
+                    cols = 0u;
+                }
+                cols |= 1u << (x & 31);
+            }
+        }
+        if (slot >= 0) {
+            if (DIM == 2) {
+                atomicOr(&sm.pm[slot][c], cols);
+                atomicOr(&sm.pm[slot][4 + (y >> 5)], 1u << (y & 31));
+            } else {
+                atomicOr(&sm.pm[slot][0], cols);
+                atomicOr(&sm.pm[slot][1], (1u << y) | (1u << (16 + z)));
+            }
+        }
+        code4[idx] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    if (pcc) {
+        __syncthreads();
+        for (int w = tid; w < S * G::PMW; w += NT) p.pmask[nbase * G::PMW + w] = (&sm.pm[0][0])[w];
+    }
+    long long c2 = 0;
+    if (csz) {
+        // every root: an interior cluster adds its |C|^2; a border piece hands
+        // its size to its representative node for the merge
+        for (int w = tid; w < nrows * TWW; w += NT) {
+            const int rr = w % nrows, c = w / nrows;
+            const int y = rr % th, z = rr / th, r = y + G::TY * z;
+            const int base = r * G::PW + 32 * c;
+            const int vw = min(32, tw - 32 * c);
+            for (uint32_t bits = run_heads(ih(r, c)) & valid_mask(0, vw); bits; bits &= bits - 1) {
+                const int v = sm.par[base + __ffs(bits) - 1];
+                if (v < 0) {   // piece size: bits 16-30 (bit 31 is the border flag)
+                    p.psize[nbase + (v & 0x7FFF)] = (int32_t)(((uint32_t)v >> 16) & 0x7FFFu);
+                } else if ((uint32_t)v >= INFO_INTERIOR) {   // bits 16-29 (bit 30 is the flag)
+                    const long long size = ((uint32_t)v >> 16) & 0x3FFFu;
+                    c2 += size * size;
+                }
+            }
+        }
+    }
+    long long v4[4] = {nb, ncl_interior, c2, 0};
+    DevObs *o = obs + j;
+    unsigned long long *const dst[4] = {&o->nbonds, &o->nclusters, &o->csize2, nullptr};
+    block_sum_atomic<NT, 4>(v4, dst, sm.u.red);
+}
+
+// ------------------------------------------------------------------ merge
+template <int DIM>
+struct PMC {
+    static constexpr int MT = DIM == 2 ? 96 : 256;                  // threads per block
+    static constexpr int EPT = (PG<DIM>::FT + MT - 1) / MT;        // crossing links per thread
+    static constexpr int NPT = PG<DIM>::S / MT;                    // slots per thread
+    static_assert(PG<DIM>::S % MT == 0, "merge launch shape");
+};
+
+// Master step 2 of Sec. II.A on the face nodes: link e of a tile joins slot
+// f of its + face along axis a to slot f of the - face of the next tile
+// along a (e = f, F0 + f, F0 + F1 + f for a = 0, 1, 2).  The block's links
+// first meet in a shared-memory forest over the pieces they touch (the
+// tile's own, ids [0, S); its + neighbour's along axis a, ids [(1 + a) S,
+// (2 + a) S)); only a link that joins two of those sets there goes on to
+// the global forest, union by key with the unions' finds advancing in lock
+// step.  A slot's piece: its own slot for a representative, else its
+// parent (its representative): each slot ends one link only.
+template <int DIM>
+__global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p)
+{
+    using G = PG<DIM>;
+    using MC = PMC<DIM>;
+    constexpr int S = G::S;
+    const int lt = blockIdx.x;
+    const PTile t = ptile_of<DIM>(p, lt);
+    const uint32_t *cross = p.cross + (size_t)lt * G::CW;
+    int na[MC::EPT], nb[MC::EPT], ax[MC::EPT], nt[MC::EPT];
+#pragma unroll
+    for (int qq = 0; qq < MC::EPT; ++qq) {
+        const int e = threadIdx.x + qq * MC::MT;
+        na[qq] = -1;
+        ax[qq] = 0;
+        nt[qq] = 0;
+        if (e < G::FT && ((cross[e >> 5] >> (e & 31)) & 1u)) {
+            const int a = e < G::F0 ? 0 : e < G::F0 + G::F1 ? 1 : 2;
+            const int f = e - (a == 0 ? 0 : a == 1 ? G::F0 : G::F0 + G::F1);
+            nt[qq] = a == 0 ? t.nb[0] : a == 1 ? t.nb[1] : t.nb[2];
+            na[qq] = lt * S + face_off<DIM>(a, 1) + f;
+            nb[qq] = nt[qq] * S + face_off<DIM>(a, 0) + f;
+            ax[qq] = a;
+        }
+    }
+    __shared__ int lp[(1 + DIM) * S];
+    for (int i = threadIdx.x; i < (1 + DIM) * S; i += MC::MT) lp[i] = i;
+    int pa[MC::EPT], pb[MC::EPT], ka[MC::EPT], kb[MC::EPT];
+#pragma unroll
+    for (int qq = 0; qq < MC::EPT; ++qq) {
+        if (na[qq] < 0) continue;
+        pa[qq] = gload(p.npar + na[qq]);
+        pb[qq] = gload(p.npar + nb[qq]);
+        ka[qq] = p.nkey[na[qq]];
+        kb[qq] = p.nkey[nb[qq]];
+    }
+    __syncthreads();
+    bool live[MC::EPT];
+#pragma unroll
+    for (int qq = 0; qq < MC::EPT; ++qq) {
+        live[qq] = false;
+        if (na[qq] < 0) continue;
+        const int own = lt * S, nbr = nt[qq] * S;
+        const int la = ((uint32_t)ka[qq] & KEY_REP) ? na[qq] - own : pa[qq] - own;
+        const int lb = (1 + ax[qq]) * S + (((uint32_t)kb[qq] & KEY_REP) ? nb[qq] - nbr : pb[qq] - nbr);
+        live[qq] = sunite_linked(lp, la, lb);
+    }
+    // the remaining unions in lock step (path splitting on the way up; the
+    // larger key's root is hung under the smaller by compare-and-swap)
+    int xa[MC::EPT], xb[MC::EPT], sa[MC::EPT], sb[MC::EPT];
+#pragma unroll
+    for (int qq = 0; qq < MC::EPT; ++qq) {
+        xa[qq] = na[qq];
+        xb[qq] = nb[qq];
+        sa[qq] = sb[qq] = -1;
+    }
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int qq = 0; qq < MC::EPT; ++qq) {
+            if (!live[qq]) continue;
+            const bool ra = pa[qq] == xa[qq], rb = pb[qq] == xb[qq];
+            if (!ra || !rb) {
+                if (!ra) {
+                    if (sa[qq] >= 0) *(volatile int32_t *)(p.npar + sa[qq]) = pa[qq];
+                    sa[qq] = xa[qq];
+                    xa[qq] = pa[qq];
+                }
+                if (!rb) {
+                    if (sb[qq] >= 0) *(volatile int32_t *)(p.npar + sb[qq]) = pb[qq];
+                    sb[qq] = xb[qq];
+                    xb[qq] = pb[qq];
+                }
+                more = true;
+            } else if (xa[qq] == xb[qq]) {
+                live[qq] = false;
+            } else {
+                const bool a_lo = ka[qq] < kb[qq];
+                const int lo = a_lo ? xa[qq] : xb[qq], hi = a_lo ? xb[qq] : xa[qq];
+                if (atomicCAS(p.npar + hi, hi, lo) == hi) live[qq] = false;
+                else more = true;
+            }
+        }
+        if (!more) break;
+#pragma unroll
+        for (int qq = 0; qq < MC::EPT; ++qq) {
+            if (!live[qq]) continue;
+            pa[qq] = gload(p.npar + xa[qq]);
+            pb[qq] = gload(p.npar + xb[qq]);
+            ka[qq] = p.nkey[xa[qq]];
+            kb[qq] = p.nkey[xb[qq]];
+        }
+    }
+}
+
+// One round of pointer jumping on the representatives' parents.
+template <int DIM>
+__global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_jump(const PottsDev p)
+{
+    using MC = PMC<DIM>;
+    const int base = blockIdx.x * PG<DIM>::S;
+    int pr[MC::NPT];
+#pragma unroll
+    for (int qq = 0; qq < MC::NPT; ++qq) {
+        const int n = base + threadIdx.x + qq * MC::MT;
+        const uint32_t key = (uint32_t)p.nkey[n];
+        const int pq = gload(p.npar + n);
+        pr[qq] = (key != KEY_NONE && (key & KEY_REP)) ? pq : -1;
+    }
+#pragma unroll
+    for (int qq = 0; qq < MC::NPT; ++qq) {
+        if (pr[qq] < 0) continue;
+        const int gp = gload(p.npar + pr[qq]);
+        if (gp != pr[qq]) *(volatile int32_t *)(p.npar + base + threadIdx.x + qq * MC::MT) = gp;
+    }
+}
+
+// Every representative walks to its root r (key: the cluster's minimum site)
+// and stores the cluster's root and new state (Sec. I step 3); under PCC it
+// also points every node of its walk at r.  A "-" face slot that is not a
+// representative stores FINAL_ALIAS | its parent (a representative of the
+// same cluster) for the neighbour's halo.  Counts the clusters that touch a
+// tile face (one root node each).
+template <int DIM>
+__global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_resolve(const PottsDev p, int j, uint64_t sweep0,
+                                                                 DevObs *obs)
+{
+    using MC = PMC<DIM>;
+    const int base = blockIdx.x * PG<DIM>::S;
+    uint32_t key[MC::NPT];
+    int r[MC::NPT], pr[MC::NPT];
+#pragma unroll
+    for (int qq = 0; qq < MC::NPT; ++qq) key[qq] = (uint32_t)p.nkey[base + threadIdx.x + qq * MC::MT];
+#pragma unroll
+    for (int qq = 0; qq < MC::NPT; ++qq) {
+        r[qq] = base + threadIdx.x + qq * MC::MT;
+        pr[qq] = gload(p.npar + r[qq]);
+    }
+    auto is_rep = [](uint32_t kk) { return kk != KEY_NONE && (kk & KEY_REP); };
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int qq = 0; qq < MC::NPT; ++qq)
+            if (is_rep(key[qq]) && pr[qq] != r[qq]) {
+                r[qq] = pr[qq];
+                more = true;
+            }
+        if (!more) break;
+#pragma unroll
+        for (int qq = 0; qq < MC::NPT; ++qq)
+            if (is_rep(key[qq])) pr[qq] = gload(p.npar + r[qq]);
+    }
+    const uint64_t k = sweep0 + (uint64_t)j;
     const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
-    const uint64_t thr = p.thr_dev ? *p.thr_dev : p.thr;
-    if (DIM == 2 && (L & 1) == 0) {
-        // even L: a 2D brick row of 32 sites starts on an even site, so its
-        // 64 links are exactly the 16 Philox blocks from (site index) / 2;
-        // thread t < 16 BY draws block t & 15 of row t >> 4 (words of sites
-        // past the lattice's edge are drawn but never read)
-        if (t < 16 * B::BY) {
-            const int row = t >> 4, jb = t & 15;
-            if (y0 + row < L) {
-                const uint32_t i0 = (uint32_t)x0 + uL * (uint32_t)(y0 + row);
-                const U4 r = philox4x32_10((i0 >> 1) + (uint32_t)jb, klo, khi, STREAM_BOND, k0, k1);
-                *reinterpret_cast<uint4 *>(&uw[64 * row + 4 * jb]) = make_uint4(r.x, r.y, r.z, r.w);
-            }
-        }
-    } else if (DIM == 3 && (L & 3) == 0) {
-        // L a multiple of 4: a 3D brick row of 8 sites starts on a site i0
-        // that is a multiple of 4, so its 24 links are exactly the 6 Philox
-        // blocks from 3 i0 / 4; thread t < 384 draws block t mod 6 of row t / 6
-        if (t < 6 * B::BY * B::BZ) {
-            const int row = t / 6, jb = t % 6;
-            const int ry = row % B::BY, rz = row / B::BY;
-            if (y0 + ry < L && z0 + rz < L) {
-                const uint32_t i0 = (uint32_t)x0 + uL * ((uint32_t)(y0 + ry) + uL * (uint32_t)(z0 + rz));
-                const U4 r = philox4x32_10(3u * (i0 >> 2) + (uint32_t)jb, klo, khi, STREAM_BOND, k0, k1);
-                *reinterpret_cast<uint4 *>(&uw[24 * row + 4 * jb]) = make_uint4(r.x, r.y, r.z, r.w);
-            }
-        }
-    } else {
-        // a brick row's BX sites own DIM * BX consecutive links, which span
-        // RB - 1 or RB Philox blocks; each block is drawn once, by one thread
-        // (words of sites past the lattice's edge are drawn but never read)
-        constexpr int RL = DIM * B::BX, RB = RL / 4 + 1, NR = B::BY * B::BZ;
-        for (int q = t; q < NR * RB; q += B::NT) {
-            const int row = q / RB, jb = q % RB;
-            const int ry = row % B::BY, rz = row / B::BY;
-            if (y0 + ry >= L || (DIM == 3 && z0 + rz >= L)) continue;
-            const uint32_t i0 = (uint32_t)x0 + uL * ((uint32_t)(y0 + ry) + uL * (uint32_t)(z0 + rz));
-            const uint32_t la = (uint32_t)DIM * i0, ma = la >> 2, mb = (la + RL - 1) >> 2;
-            if ((uint32_t)jb > mb - ma) continue;
-            const U4 r = philox4x32_10(ma + (uint32_t)jb, klo, khi, STREAM_BOND, k0, k1);
+    const bool pcc = (p.flags & RF_PCC) != 0;
+    int nroots = 0;
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const uint32_t l = 4u * (ma + (uint32_t)jb) + (uint32_t)w;
-                if (l >= la && l < la + RL) uw[RL * row + (l - la)] = u4_word(r, w);
+    for (int qq = 0; qq < MC::NPT; ++qq) {
+        const int s = threadIdx.x + qq * MC::MT, n = base + s;
+        if (is_rep(key[qq])) {
+            if (pcc) {
+                // the PCC kernels read a representative's root from its parent
+                for (int x = n; x != r[qq];) {
+                    const int nx = gload(p.npar + x);
+                    *(volatile int32_t *)(p.npar + x) = r[qq];
+                    x = nx;
+                }
             }
+            nroots += r[qq] == n;
+            if (p.flags & RF_CSIZE) atomicAdd(p.csize + r[qq], p.psize[n]);
+            const uint32_t rkey = (uint32_t)p.nkey[r[qq]] & KEY_MASK;
+            p.nstate[n] = cluster_state(rkey, klo, khi, k0, k1, p.q);
+            p.nfinal[n] = rkey;
+        } else if (minus_slot<DIM>(s)) {
+            // its parent since the tile kernel (a representative), moved up
+            // the same cluster by the unions' path splitting at most
+            p.nfinal[n] = key[qq] == KEY_NONE ? 0u : FINAL_ALIAS | (uint32_t)pr[qq];
         }
     }
-    __syncthreads();
-    uint8_t bits = 0;
-    if (valid) {
-        const uint8_t s = st[lz][ly][lx];
-#pragma unroll
-        for (int dir = 0; dir < DIM; ++dir) {
-            const uint32_t u = uw[DIM * t + dir];   // link DIM * i + dir
-            const uint8_t ns = dir == 0 ? st[lz][ly][lx + 1] : dir == 1 ? st[lz][ly + 1][lx] : st[lz + 1][ly][lx];
-            const int c = dir == 0 ? gx : dir == 1 ? gy : gz;   // under open boundaries the last one links out
-            if (ns == s && (uint64_t)u < thr && !(p.open && c + 1 == L)) bits |= (uint8_t)(1u << dir);
-        }
-        p.bond[i] = bits;
-    }
-    // bonds whose far end is in the brick (not across the lattice's edge)
-    const bool bx = (bits & 1) && lx + 1 < B::BX && gx + 1 < L;
-    const bool by = (bits & 2) && ly + 1 < B::BY && gy + 1 < L;
-    int head = t;   // the site whose root is this site's root
-    if constexpr (DIM == 2) {
-        // A warp is one 32-site row of the brick.  The union-find runs on
-        // run heads (the leftmost site of a maximal chain of x bonds), so the
-        // x bonds need no unions; a down bond is a contact between the run
-        // above and the run below, skipped when the down bond to its left
-        // already joins the same two runs.
-        __shared__ uint32_t heads_of[B::BY];
-        const uint32_t hbits = __ballot_sync(0xFFFFFFFFu, bx);
-        const uint32_t vbits = __ballot_sync(0xFFFFFFFFu, by);
-        const uint32_t heads = run_heads(hbits);
-        if (lx == 0) heads_of[ly] = heads;
-        head = head_of(heads, B::BX * ly, lx);
-        __syncthreads();
-        const uint32_t below = ly + 1 < B::BY ? heads_of[ly + 1] : 0xFFFFFFFFu;
-        const uint32_t u = vbits & (~(vbits << 1) | heads | below);
-        if ((u >> lx) & 1u) sunite(par, head, head_of(below, B::BX * (ly + 1), lx));
-    } else {
-        // 3D: a warp holds four 8-site rows of one layer (lane = x + 8 (y mod
-        // 4)).  The union-find runs on the heads of x runs inside those rows;
-        // a y or z bond is a contact between the run of its site and the run
-        // of the site it reaches (the next row: in the same warp or the next
-        // one; the next layer: two warps on), skipped when the bond of the
-        // same direction to its left joins the same two runs.
-        static_assert(B::BX == 8 && B::BY == 8, "3D bricks of 8 x 8 x 8 sites");
-        __shared__ uint32_t heads_of[B::NT / 32];
-        const bool bz = (bits & 4) && lz + 1 < B::BZ && gz + 1 < L;
-        const int lane = t & 31, warp = t >> 5;
-        const uint32_t hbits = __ballot_sync(0xFFFFFFFFu, bx);
-        const uint32_t ybits = __ballot_sync(0xFFFFFFFFu, by);
-        const uint32_t zbits = __ballot_sync(0xFFFFFFFFu, bz);
-        const uint32_t heads = run_heads(hbits);   // bit x = 0 of every row is set: no bond crosses lx = 7
-        if (lane == 0) heads_of[warp] = heads;
-        head = head_of(heads, 32 * warp, lane);
-        __syncthreads();
-        const bool left = lx > 0;   // the site to the left is in the same row
-        if (by) {
-            const int tw = (lane < 24) ? warp : warp + 1, tl = (lane + 8) & 31;   // the site t + 8
-            const uint32_t th_ = heads_of[tw];
-            const bool own_head = (heads >> lane) & 1u, tgt_head = (th_ >> tl) & 1u;
-            if (!(left && ((ybits >> (lane - 1)) & 1u) && !own_head && !tgt_head))
-                sunite(par, head, head_of(th_, 32 * tw, tl));
-        }
-        if (bz) {
-            const int tw = warp + 2;   // the site t + 64, same lane
-            const uint32_t th_ = heads_of[tw];
-            const bool own_head = (heads >> lane) & 1u, tgt_head = (th_ >> lane) & 1u;
-            if (!(left && ((zbits >> (lane - 1)) & 1u) && !own_head && !tgt_head))
-                sunite(par, head, head_of(th_, 32 * tw, lane));
-        }
-    }
-    __syncthreads();
-    if (valid) {
-        const int r = sroot(par, head);
-        const int rx = r % B::BX, ry = (r / B::BX) % B::BY, rz = r / (B::BX * B::BY);
-        p.label[i] = (int32_t)((uint32_t)(x0 + rx) + uL * ((uint32_t)(y0 + ry) + uL * (uint32_t)(z0 + rz)));
-        if (p.size) atomicAdd(&cnt[r], 1);
-    }
-    if (p.size) {
-        __syncthreads();
-        if (valid) p.size[i] = par[t] == t ? cnt[t] : 0;
-    }
+    const int wb = threadIdx.x & ~31;
+    const unsigned wm = MC::MT - wb >= 32 ? 0xFFFFFFFFu : (1u << (MC::MT - wb)) - 1u;
+    nroots = __reduce_add_sync(wm, nroots);
+    if ((threadIdx.x & 31) == 0 && nroots) atomicAdd(&obs[j].nclusters, (unsigned long long)nroots);
 }
 
-// Bonds that leave their brick (Sec. I step 2 across bricks): unite the two
-// ends' pieces in the global forest of labels.  One block per brick, one
-// thread per site of its + faces (the brick's last valid column, row and
-// layer, which also hold the lattice's wrapping links).
+// ------------------------------------------------------------------- PCC
+// The extension rule in d dimensions (Sec. III): a cluster spans axis a iff
+// it occupies all L hyperplanes perpendicular to a.  Such a cluster holds a
+// site of the hyperplane a = 0, on the - face of a tile of tile coordinate 0
+// along a: those nodes' roots are the candidates (cid of the root node, per
+// axis: id + 2).  Every border piece then ORs the coordinates it occupies
+// along a into its candidate root's coverage (L bits), and a candidate spans
+// iff its coverage is full.  Interior clusters touch no face and span nothing.
 template <int DIM>
-struct Faces {
-    static constexpr int FS = DIM == 2 ? 32 : 64;   // sites of one face
-    static constexpr int NT = DIM * FS;
-};
-
-template <int DIM>
-__global__ void __launch_bounds__(Faces<DIM>::NT) k_potts_cross(const PottsDev p)
+__global__ void k_ppcc_candidates(const PottsDev p, int64_t F)
 {
-    using B = Brick<DIM>;
-    constexpr int FS = Faces<DIM>::FS;
-    const int L = p.L;
-    const uint32_t uL = (uint32_t)L;
-    const int x0 = blockIdx.x * B::BX, y0 = blockIdx.y * B::BY, z0 = blockIdx.z * B::BZ;
-    const int f = threadIdx.x / FS, r = threadIdx.x % FS;   // f: the face's axis
-    const int a = DIM == 2 ? r : r % 8, b = DIM == 2 ? 0 : r / 8;
-    if (DIM == 2 && f == 0 && a >= B::BY) return;   // the x face is BY sites long
-    int gx, gy, gz;
-    if (f == 0) {
-        gx = min(x0 + B::BX, L) - 1;
-        gy = y0 + a;
-        gz = z0 + b;
-    } else if (f == 1) {
-        gx = x0 + a;
-        gy = min(y0 + B::BY, L) - 1;
-        gz = z0 + b;
-    } else {
-        gx = x0 + a;
-        gy = y0 + b;
-        gz = min(z0 + B::BZ, L) - 1;
-    }
-    if (gx >= L || gy >= L || (DIM == 3 && gz >= L)) return;
-    const uint32_t i = (uint32_t)gx + uL * ((uint32_t)gy + uL * (uint32_t)gz);
-    if (!((p.bond[i] >> f) & 1u)) return;   // (open boundaries: no bond leaves the lattice)
-    uint32_t j;
-    if (f == 0)
-        j = i - (uint32_t)gx + (gx + 1 == L ? 0u : (uint32_t)gx + 1u);
-    else if (f == 1)
-        j = gy + 1 == L ? i - (uint32_t)gy * uL : i + uL;
-    else
-        j = gz + 1 == L ? i - (uint32_t)gz * uL * uL : i + uL * uL;
-    punite(p.label, (int)i, (int)j);
-}
-
-// The per-site passes below stride over the lattice with a bounded grid, so
-// each block adds its sums to the observables once.
-constexpr unsigned MAX_BLOCKS = 4096;
-
-// Every site's label becomes its root, the cluster minimum (every write moves
-// a label to an ancestor, so concurrent walks stay on their paths), and the
-// site takes its cluster's new state (Sec. I step 3); cluster roots are
-// counted.  A piece root that is not a cluster root hands its size to the
-// cluster root.
-__global__ void k_potts_resolve(const PottsDev p, uint64_t k, DevObs *obs)
-{
-    int roots = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int first = gload(p.label + i);   // the piece's root, or an ancestor of it
-        int x = first, nx = gload(p.label + x);
-        while (nx != x) {
-            x = nx;
-            nx = gload(p.label + x);
-        }
-        // the other sites of the piece then stop one step later
-        if (x != first) *(volatile int32_t *)(p.label + first) = x;
-        if (p.size && x != (int)i) {
-            const int s = p.size[i];
-            if (s > 0) {
-                atomicAdd(p.size + x, s);
-                p.size[i] = 0;
-            }
-        }
-        p.label[i] = x;
-        const U4 w = philox4x32_10((uint32_t)x >> 2, (uint32_t)k, (uint32_t)(k >> 32), STREAM_QSPIN,
-                                   (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
-        p.spin[i] = potts_state(u4_word(w, x & 3), p.q);
-        roots += x == (int)i;
-    }
-    roots = __reduce_add_sync(0xFFFFFFFFu, roots);
-    __shared__ int red[PT / 32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = roots;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long n = 0;
-        for (int w = 0; w < PT / 32; ++w) n += red[w];
-        if (n) atomicAdd(&obs->nclusters, (unsigned long long)n);
-        if (blockIdx.x == 0) obs->threshold = p.thr_dev ? *p.thr_dev : p.thr;
-    }
-}
-
-// Sums of the new states: bond_sum, mag, the bond count and sum |C|^2.  A
-// warp takes one lattice row (L sites along x) at a time, so neighbours are
-// found without dividing site indices.
-__global__ void k_potts_measure(const PottsDev p, DevObs *obs)
-{
-    __shared__ long long red[PT / 32][4];
-    long long v[4] = {0, 0, 0, 0};
-    const uint32_t uL = (uint32_t)p.L;
-    const uint32_t rows = (uint32_t)(p.N / p.L);   // row R = y + L z
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t R = w0; R < rows; R += nw) {
-        const uint32_t y = R % uL, z = R / uL;
-        const uint32_t Ry = y + 1 == uL ? R - y : R + 1;                     // row at y + 1
-        const uint32_t Rz = p.dim == 3 ? (z + 1 == uL ? R - z * uL : R + uL) : 0u;   // row at z + 1
-        const uint8_t *row = p.spin + (size_t)R * uL;
-        const uint8_t *row_y = p.spin + (size_t)Ry * uL;
-        const uint8_t *row_z = p.spin + (size_t)Rz * uL;
-        for (uint32_t x = lane; x < uL; x += 32) {
-            const uint8_t s = row[x];
-            // each link that exists (open boundaries drop those leaving the lattice)
-            if (!(p.open && x + 1 == uL)) v[0] += row[x + 1 == uL ? 0u : x + 1] == s ? 1 : -1;
-            if (!(p.open && y + 1 == uL)) v[0] += row_y[x] == s ? 1 : -1;
-            if (p.dim == 3 && !(p.open && z + 1 == uL)) v[0] += row_z[x] == s ? 1 : -1;
-            v[1] += s == 0 ? p.q - 1 : -1;
-            const size_t i = (size_t)R * uL + x;
-            v[2] += __popc((uint32_t)p.bond[i]);
-            if (p.size) {
-                const long long c = p.size[i];
-                v[3] += c * c;
-            }
-        }
-    }
-    unsigned long long *const dst[4] = {&obs->bond_sum, &obs->mag, &obs->nbonds, &obs->csize2};
-    block_sum_atomic<PT, 4>(v, dst, red);
-}
-
-// ------------------------------------------------------------- Potts PCC
-// The extension rule in d dimensions (Sec. III): a cluster spans axis a iff it
-// occupies all L hyperplanes perpendicular to a.  Such a cluster holds a site
-// of the hyperplane a = 0, so the roots found there are the candidates; every
-// site then marks its coordinate along a in its root's coverage (when the root
-// is a candidate), and a candidate spans iff its coverage is full.  Labels are
-// cluster roots by now (k_potts_resolve).
-
-// Coordinate of site i along axis a, and the site of face a = 0 with index f
-// (the other coordinates in order).
-__device__ __forceinline__ uint32_t coord_of(uint32_t i, uint32_t L, int a)
-{
-    return a == 0 ? i % L : a == 1 ? (i / L) % L : i / (L * L);
-}
-__device__ __forceinline__ uint32_t face_site(uint32_t f, uint32_t L, int a)
-{
-    const uint32_t u = f % L, v = f / L;   // v = 0 in 2D
-    return a == 0 ? L * u + L * L * v : a == 1 ? u + L * L * v : u + L * v;
-}
-
-// Step 1: candidate ids for the roots on each axis's face a = 0.
-__global__ void k_potts_pcc_cand(const PottsDev p, int64_t F)
-{
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= F * p.dim) return;
-    const int a = (int)(q / F);
-    const uint32_t f = (uint32_t)(q % F);
-    const int32_t r = p.label[face_site(f, (uint32_t)p.L, a)];
-    int32_t *c = p.cid + (size_t)a * p.N + r;
+    using G = PG<DIM>;
+    constexpr int S = G::S;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)p.ntiles * G::FT) return;
+    const int lt = (int)(idx / G::FT), e = (int)(idx % G::FT);
+    const int a = e < G::F0 ? 0 : e < G::F0 + G::F1 ? 1 : 2;
+    const int f = e - (a == 0 ? 0 : a == 1 ? G::F0 : G::F0 + G::F1);
+    const PTile t = ptile_of<DIM>(p, lt);
+    if (t.c[a] != 0) return;
+    const int node = lt * S + face_off<DIM>(a, 0) + f;
+    const uint32_t key = (uint32_t)p.nkey[node];
+    if (key == KEY_NONE) return;
+    int r = gload(p.npar + node);
+    if (!(key & KEY_REP)) r = gload(p.npar + r);   // via a representative
+    int32_t *c = p.cid + (size_t)r * DIM + a;
     if (atomicCAS(c, 0, 1) == 0) {
         const int id = atomicAdd(p.ncand + a, 1);   // < F: at most one per face site
         p.cand[(size_t)a * F + id] = r;
@@ -449,48 +1097,58 @@ __global__ void k_potts_pcc_cand(const PottsDev p, int64_t F)
     }
 }
 
-// Step 2: every site marks its coordinates in its root's coverage, for each
-// axis whose candidate the root is.  A warp of 32 consecutive sites of one row
-// (L a multiple of 32) shares its y and z and one word of x: one atomic per
-// root and axis.
-__global__ void k_potts_pcc_cover(const PottsDev p, int64_t F)
+template <int DIM>
+__global__ void k_ppcc_cover(const PottsDev p)
 {
-    const uint32_t L = (uint32_t)p.L, W = (L + 31) / 32;
-    const bool rows = (L & 31u) == 0;
-    const int lane = threadIdx.x & 31;
-    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; i0 < p.N;
-         i0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = i0 + lane;
-        const bool ok = i < p.N;
-        const int32_t r = ok ? p.label[i] : -1;
-        for (int a = 0; a < p.dim; ++a) {
-            const int32_t c = ok ? p.cid[(size_t)a * p.N + r] : 0;
-            const uint32_t x = ok ? coord_of((uint32_t)i, L, a) : 0u;
-            uint32_t *cov = p.cov + (size_t)a * F * W;
-            if (rows) {
-                const unsigned grp = __match_any_sync(0xFFFFFFFFu, c);
-                if (c >= 2 && lane == __ffs(grp) - 1) {
-                    // the group's bits: x along the row (lane = x mod 32), else one coordinate
-                    const uint32_t bits = a == 0 ? grp : 1u << (x & 31);
-                    atomicOr(cov + (size_t)(c - 2) * W + (x >> 5), bits);
-                }
-            } else if (c >= 2) {
-                atomicOr(cov + (size_t)(c - 2) * W + (x >> 5), 1u << (x & 31));
+    using G = PG<DIM>;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (int64_t)p.ntiles * G::S) return;
+    const uint32_t key = (uint32_t)p.nkey[n];
+    if (key == KEY_NONE || !(key & KEY_REP)) return;
+    uint32_t m[G::PMW];
+    uint32_t any = 0u;
+#pragma unroll
+    for (int w = 0; w < G::PMW; ++w) any |= (m[w] = p.pmask[(size_t)n * G::PMW + w]);
+    if (!any) return;
+    const int r = gload(p.npar + n);
+    const PTile t = ptile_of<DIM>(p, (int)(n / G::S));
+    const uint32_t W = ((uint32_t)p.L + 31u) / 32u;
+    const int64_t F = DIM == 2 ? (int64_t)p.L : (int64_t)p.L * p.L;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const int c = p.cid[(size_t)r * DIM + a];
+        if (c < 2) continue;
+        uint32_t *cov = p.cov + ((size_t)a * F + (size_t)(c - 2)) * W + (size_t)(t.o[a] >> 5);
+        if (DIM == 2) {
+            if (a == 0) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if (m[w]) atomicOr(cov + w, m[w]);
+            } else {
+#pragma unroll
+                for (int w = 0; w < 2; ++w)
+                    if (m[4 + w]) atomicOr(cov + w, m[4 + w]);
             }
+        } else {
+            // 32-site x words; 16-site y and z halves at an origin that is a
+            // multiple of 16
+            const uint32_t bits = a == 0 ? m[0] : a == 1 ? (m[1] & 0xFFFFu) : (m[1] >> 16);
+            if (bits) atomicOr(cov, a == 0 ? bits : bits << (t.o[a] & 31));
         }
     }
 }
 
-// Step 3 (PCC_DECIDE blocks): each block checks a contiguous range of every
-// axis's candidates, clears their scratch and ORs its flags into the sweep's
+// PPCC_DECIDE blocks: each checks a contiguous range of every axis's
+// candidates, clears their scratch and ORs its flags into the sweep's
 // spans_x (axis x) / spans_y (axis y, and z in 3D); the last block to finish
-// (a counter, after a fence: no block waits) applies the feedback to the
-// threshold -- down by delta_k if some cluster spans, up otherwise, clamped
-// to [0, 2^32] -- and resets the counts.
-constexpr int POTTS_PCC_DECIDE = 16;
-__global__ void k_potts_pcc_decide(const PottsDev p, int64_t F, uint64_t k, DevObs *obs)
+// (a counter after a fence: no block waits) applies the feedback -- down by
+// delta_k if some cluster spans, up otherwise, delta_k = 2^(32 - min(8 +
+// floor(k / 1000), 20)), clamped to [0, 2^32] -- and resets the counts.
+constexpr int PPCC_DECIDE = 16;
+__global__ void k_ppcc_decide(const PottsDev p, int64_t F, int j, uint64_t sweep0, DevObs *obs)
 {
     const uint32_t L = (uint32_t)p.L, W = (L + 31) / 32;
+    DevObs *o = obs + j;
     int sx = 0, sy = 0;
     for (int a = 0; a < p.dim; ++a) {
         const int n = p.ncand[a];
@@ -505,25 +1163,36 @@ __global__ void k_potts_pcc_decide(const PottsDev p, int64_t F, uint64_t k, DevO
                 full = (cov[(size_t)id * W + w] & m) == m;
             }
             s |= full;
-            p.cid[(size_t)a * p.N + p.cand[(size_t)a * F + id]] = 0;
+            p.cid[(size_t)p.cand[(size_t)a * F + id] * p.dim + a] = 0;
         }
         s = __syncthreads_or(s);   // also: every check of this range has read its coverage
-        for (int64_t q = (int64_t)c0 * W + threadIdx.x; q < (int64_t)c1 * W; q += blockDim.x) cov[q] = 0u;
-        if (a == 0) sx |= s; else sy |= s;
+        for (int64_t qq = (int64_t)c0 * W + threadIdx.x; qq < (int64_t)c1 * W; qq += blockDim.x) cov[qq] = 0u;
+        if (a == 0) sx |= s;
+        else sy |= s;
     }
     if (threadIdx.x != 0) return;
-    if (sx) atomicOr(&obs->spans_x, 1);
-    if (sy) atomicOr(&obs->spans_y, 1);
+    if (sx) atomicOr(&o->spans_x, 1);
+    if (sy) atomicOr(&o->spans_y, 1);
     __threadfence();
     if (atomicAdd(p.ncand + 3, 1) != (int)gridDim.x - 1) return;
     __threadfence();   // the last block: every other block's flags are visible
-    const int fx = *(volatile int32_t *)&obs->spans_x, fy = *(volatile int32_t *)&obs->spans_y;
+    const int fx = *(volatile int32_t *)&o->spans_x, fy = *(volatile int32_t *)&o->spans_y;
+    const uint64_t k = sweep0 + (uint64_t)j;
     const uint64_t e = 8 + k / 1000;
     const uint64_t delta = (uint64_t)1 << (32 - (e < 20 ? e : 20));
     const uint64_t top = (uint64_t)1 << 32;
-    const uint64_t t = *p.thr_dev;
-    *p.thr_dev = (fx || fy) ? (t > delta ? t - delta : 0) : (t + delta < top ? t + delta : top);
+    const uint64_t tt = *p.thr_dev;
+    *p.thr_dev = (fx || fy) ? (tt > delta ? tt - delta : 0) : (tt + delta < top ? tt + delta : top);
     for (int a = 0; a < 4; ++a) p.ncand[a] = 0;
+}
+
+// ------------------------------------------------------------ small kernels
+__global__ void k_potts_hot_start(const PottsDev p)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    const U4 r = philox4x32_10((uint32_t)(i >> 2), 0u, 0u, STREAM_INIT, (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+    p.spin[i] = potts_state(u4_word(r, (int)(i & 3)), p.q);
 }
 
 // Sets *bad if any of the n states is >= q.
@@ -535,45 +1204,91 @@ __global__ void k_potts_check(const uint8_t *s, int64_t n, int q, int32_t *bad)
     if (__syncthreads_or(found) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
-unsigned blocks_of(int64_t n) { return (unsigned)((n + PT - 1) / PT); }
+// The tile kernels' dynamic shared-memory limit, raised once per device.
+constexpr int PREP_DEVICES = 64;
+cudaError_t potts_prepare()
+{
+    static std::mutex mu;
+    static bool done[PREP_DEVICES] = {};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= PREP_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    const void *fn[4] = {(const void *)k_ptile<2, 0>, (const void *)k_ptile<2, FEAT_TILE>,
+                         (const void *)k_ptile<3, 0>, (const void *)k_ptile<3, FEAT_TILE>};
+    const int bytes[4] = {(int)ptile_smem<2>(true), (int)ptile_smem<2>(true), (int)ptile_smem<3>(true),
+                          (int)ptile_smem<3>(true)};
+    for (int f = 0; f < 4 && err == cudaSuccess; ++f)
+        err = cudaFuncSetAttribute(fn[f], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[f]);
+    if (err == cudaSuccess) done[dev] = true;
+    return err;
+}
+
+template <int DIM>
+void launch_group(const PottsDev &p, int j, int nsweeps, uint64_t sweep0, DevObs *obs, cudaStream_t st)
+{
+    using G = PG<DIM>;
+    const bool pcc = (p.flags & RF_PCC) != 0;
+    const bool feat = (p.flags & (RF_PCC | RF_OPEN | RF_CSIZE)) != 0;
+    const unsigned tiles = (unsigned)p.ntiles;
+    const size_t smem = ptile_smem<DIM>(pcc);
+    if (feat)
+        k_ptile<DIM, FEAT_TILE><<<tiles, G::NT, smem, st>>>(p, j, nsweeps, sweep0, obs);
+    else
+        k_ptile<DIM, 0><<<tiles, G::NT, smem, st>>>(p, j, nsweeps, sweep0, obs);
+    if (j >= nsweeps) return;
+    k_pmerge_union<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
+    k_pmerge_jump<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
+    k_pmerge_resolve<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, sweep0, obs);
+    if (pcc) {
+        const int64_t F = DIM == 2 ? (int64_t)p.L : (int64_t)p.L * p.L;
+        const int64_t nc = (int64_t)p.ntiles * G::FT, nn = (int64_t)p.ntiles * G::S;
+        k_ppcc_candidates<DIM><<<(unsigned)((nc + PT - 1) / PT), PT, 0, st>>>(p, F);
+        k_ppcc_cover<DIM><<<(unsigned)((nn + PT - 1) / PT), PT, 0, st>>>(p);
+        k_ppcc_decide<<<PPCC_DECIDE, PT, 0, st>>>(p, F, j, sweep0, obs);
+    }
+}
 
 }  // namespace
 
 namespace swg {
 
+void potts_geometry(int dim, int L, PottsGeometry *g)
+{
+    const int tx = dim == 2 ? PG<2>::TX : PG<3>::TX, ty = dim == 2 ? PG<2>::TY : PG<3>::TY;
+    const int tz = dim == 2 ? PG<2>::TZ : PG<3>::TZ;
+    g->ntx = (L + tx - 1) / tx;
+    g->nty = (L + ty - 1) / ty;
+    g->ntz = dim == 2 ? 1 : (L + tz - 1) / tz;
+    g->ntiles = g->ntx * g->nty * g->ntz;
+    g->sites_per_tile = dim == 2 ? PG<2>::NS : PG<3>::NS;
+    g->slots = dim == 2 ? PG<2>::S : PG<3>::S;
+    g->cross_words = dim == 2 ? PG<2>::CW : PG<3>::CW;
+    g->pmask_words = dim == 2 ? PG<2>::PMW : PG<3>::PMW;
+}
+
 cudaError_t potts_enqueue_hot_start(const PottsDev &p, cudaStream_t st)
 {
-    k_potts_hot_start<<<blocks_of(p.N), PT, 0, st>>>(p);
+    cudaError_t e = potts_prepare();
+    if (e != cudaSuccess) return e;
+    k_potts_hot_start<<<(unsigned)((p.N + PT - 1) / PT), PT, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t potts_enqueue_sweep(const PottsDev &p, uint64_t sweep, DevObs *obs, cudaStream_t st)
+// The launches of one call of nsweeps sweeps: tile kernel j = 0 .. nsweeps,
+// each but the last followed by the merge of sweep j.
+cudaError_t potts_enqueue_sweeps(const PottsDev &p, int nsweeps, uint64_t sweep0, DevObs *obs, cudaStream_t st)
 {
-    const unsigned nb = blocks_of(p.N);
-    // one block per brick (2D: L <= 2^15, so at most 1024 bricks along an
-    // axis; 3D: L <= 2^10, at most 128)
-    if (p.dim == 2) {
-        using B = Brick<2>;
-        const dim3 g((unsigned)((p.L + B::BX - 1) / B::BX), (unsigned)((p.L + B::BY - 1) / B::BY), 1u);
-        k_potts_local<2><<<g, B::NT, 0, st>>>(p, sweep);
-        k_potts_cross<2><<<g, Faces<2>::NT, 0, st>>>(p);
-    } else {
-        using B = Brick<3>;
-        const unsigned nb3 = (unsigned)((p.L + B::BX - 1) / B::BX);
-        const dim3 g(nb3, nb3, nb3);
-        k_potts_local<3><<<g, B::NT, 0, st>>>(p, sweep);
-        k_potts_cross<3><<<g, Faces<3>::NT, 0, st>>>(p);
+    cudaError_t e = potts_prepare();
+    if (e != cudaSuccess) return e;
+    for (int j = 0; j <= nsweeps; ++j) {
+        if (p.dim == 2) launch_group<2>(p, j, nsweeps, sweep0, obs, st);
+        else launch_group<3>(p, j, nsweeps, sweep0, obs, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const unsigned ns = std::min(nb, MAX_BLOCKS);
-    k_potts_resolve<<<ns, PT, 0, st>>>(p, sweep, obs);
-    if (p.thr_dev) {   // PCC: the span test on the cluster roots, then the feedback
-        const int64_t F = p.dim == 2 ? (int64_t)p.L : (int64_t)p.L * p.L;
-        k_potts_pcc_cand<<<(unsigned)((F * p.dim + PT - 1) / PT), PT, 0, st>>>(p, F);
-        k_potts_pcc_cover<<<ns, PT, 0, st>>>(p, F);
-        k_potts_pcc_decide<<<POTTS_PCC_DECIDE, PT, 0, st>>>(p, F, sweep, obs);
-    }
-    k_potts_measure<<<ns, PT, 0, st>>>(p, obs);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t potts_enqueue_check(const uint8_t *s, int64_t n, int q, int32_t *bad, cudaStream_t st)
