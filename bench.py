@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: sweeps per step")
     ap.add_argument("--temperature", type=float, default=0.0, help="profiling only: another T")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--potts-case", default="",
+                    help="profiling only: --workload potts on one lattice, DIM,L,Q,T (e.g. 3,320,3,1.8164)")
     ap.add_argument("--tile-h", type=int, default=0, choices=[0, 32, 64, 96, 128],
                     help="rows per tile (0: the autotuner's choice for this L and T)")
     return ap.parse_args()
@@ -736,6 +738,9 @@ def run_potts(args):
              (2, 8192, 3, 1.0 / math.log(1.0 + math.sqrt(3.0))),
              (3, 512, 2, 2.2557),     # q=2 is Ising at J/2: 4.5115 / 2
              (3, 512, 3, 1.8164)]
+    if args.potts_case:
+        d, l, qq, tt = args.potts_case.split(",")
+        cases = [(int(d), int(l), int(qq), float(tt))]
     SW = 10
     stream = torch.cuda.Stream()
     clocks = ClockSampler(local)

@@ -259,15 +259,18 @@ __device__ void tile_label3(volatile int *par, const uint32_t (*X)[1], const uin
 template <int DIM>
 struct PSmem {
     using G = PG<DIM>;
-    int par[G::NR * G::PW];                 // union-find forest over run heads (padded rows)
+    union {
+        int par[G::NR * G::PW];             // start half: union-find forest over run heads (padded rows)
+        uint8_t fst[G::S];                  // finish half: new states of the tile's pieces, by slot
+    } f;
     uint8_t st[G::HZ][G::HY][G::RS];        // states; row TY, layer TZ and column tw: + halo
+    uint8_t qs[G::NR][G::TX];               // each site's state drawn from the QSPIN stream, for the
+                                            // clusters that end inside the tile (rows whose first site
+                                            // starts a Philox block)
     uint32_t bx[G::NR][G::TWW];             // +x bonds (bit x of word c: site 32 c + x)
     uint32_t by[G::NR][G::TWW];             // +y bonds
     uint32_t bz[DIM == 3 ? G::NR : 1][G::TWW];   // +z bonds
-    union {
-        uint8_t fst[G::S];                  // finish: new states of the tile's pieces, by slot
-        long long red[G::NW][4];            // the reduction that ends each half
-    } u;
+    long long red[G::NW][4];                // the reduction that ends each half
     uint32_t pm[G::S][G::PMW];              // PCC: coordinates each border piece occupies
 };
 
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
         }
         {
             const uint32_t *ns4 = reinterpret_cast<const uint32_t *>(p.nstate + nbase);
-            uint32_t *fs4 = reinterpret_cast<uint32_t *>(sm.u.fst);
+            uint32_t *fs4 = reinterpret_cast<uint32_t *>(sm.f.fst);
             for (int w = tid; w < S / 4; w += NT) fs4[w] = ns4[w];
         }
         // the + halo: new states of the neighbours' "-" face sites, through
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const uint32_t u = (wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
-                const uint32_t s = (u & CODE_BORDER) ? sm.u.fst[u & 0x7FFFu] : (u & 0xFFu);
+                const uint32_t s = (u & CODE_BORDER) ? sm.f.fst[u & 0x7FFFu] : (u & 0xFFu);
                 if (e < 4) lo |= s << (8 * e);
                 else hi |= s << (8 * (e - 4));
             }
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
         long long v[4] = {bs, mag, c2, 0};
         DevObs *o = obs + (j - 1);
         unsigned long long *const dst[4] = {&o->bond_sum, &o->mag, &o->csize2, nullptr};
-        block_sum_atomic<NT, 4>(v, dst, sm.u.red);
+        block_sum_atomic<NT, 4>(v, dst, sm.red);
         __syncthreads();
     }
 
@@ -501,6 +504,8 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
     // Step 1 (Sec. I): bonds between equal states.
     const bool any_bond = thr != 0;
     const uint32_t tm1 = (uint32_t)(thr - 1);
+    // every row starts a QSPIN block (4 divides L): the bond draws also fill qs
+    const bool qsm = any_bond && (uL & 3u) == 0;
     // row (y, z) from its random bond bits (rx, ry, rz: bit x of word c set
     // iff the link's Philox word is below the threshold)
     auto store_row = [&](int y, int z, const uint32_t (&rx)[TWW], const uint32_t (&ry)[TWW],
@@ -552,6 +557,18 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
                 const U4 r1 = philox4x32_10(b0 + 32, klo, khi, STREAM_BOND, k0, k1);
                 const U4 r2 = philox4x32_10(b2, klo, khi, STREAM_BOND, k0, k1);
                 const U4 r3 = philox4x32_10(b2 + 32, klo, khi, STREAM_BOND, k0, k1);
+                if (qsm) {
+                    // lane l: the QSPIN block of sites 4l .. 4l + 3 of each row
+                    const U4 s0 = philox4x32_10(((t.gbase + (uint32_t)y * uL) >> 2) + lane, klo, khi, STREAM_QSPIN, k0, k1);
+                    const U4 s2 = philox4x32_10(((t.gbase + (uint32_t)y2 * uL) >> 2) + lane, klo, khi, STREAM_QSPIN, k0, k1);
+                    *reinterpret_cast<uint32_t *>(&sm.qs[y][4 * lane]) =
+                        (uint32_t)potts_state(s0.x, q) | ((uint32_t)potts_state(s0.y, q) << 8) |
+                        ((uint32_t)potts_state(s0.z, q) << 16) | ((uint32_t)potts_state(s0.w, q) << 24);
+                    if (y2 < th)
+                        *reinterpret_cast<uint32_t *>(&sm.qs[y2][4 * lane]) =
+                            (uint32_t)potts_state(s2.x, q) | ((uint32_t)potts_state(s2.y, q) << 8) |
+                            ((uint32_t)potts_state(s2.z, q) << 16) | ((uint32_t)potts_state(s2.w, q) << 24);
+                }
                 uint32_t rh[TWW], rv[TWW], rh2[TWW], rv2[TWW];
                 draws_aligned(r0, r1, rh, rv);
                 draws_aligned(r2, r3, rh2, rv2);
@@ -584,8 +601,12 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
         // link string from four ballots (one per word of a block)
         const int nrows = th * td;
         auto bits_of = [&](const uint32_t (&B)[4], int l) { return (B[l & 3] >> (l >> 2)) & 1u; };
-        auto row_aligned = [&](const U4 &u, uint32_t (&rx)[1], uint32_t (&ry)[1], uint32_t (&rz)[1]) {
+        auto row_aligned = [&](const U4 &u, int r, uint32_t (&rx)[1], uint32_t (&ry)[1], uint32_t (&rz)[1]) {
             const bool act = lane < 24;
+            if (!act && r >= 0)   // lanes 24..31 drew the row's QSPIN blocks: four sites' states each
+                *reinterpret_cast<uint32_t *>(&sm.qs[r][4 * (lane - 24)]) =
+                    (uint32_t)potts_state(u.x, q) | ((uint32_t)potts_state(u.y, q) << 8) |
+                    ((uint32_t)potts_state(u.z, q) << 16) | ((uint32_t)potts_state(u.w, q) << 24);
             uint32_t B[4];
             B[0] = __ballot_sync(FULL, act && below(u.x, tm1));
             B[1] = __ballot_sync(FULL, act && below(u.y, tm1));
@@ -600,12 +621,17 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
             for (int rw = warp; rw < nrows; rw += 2 * NW) {
                 const int rw2 = rw + NW;
                 const int y = rw % th, z = rw / th, y2 = rw2 % th, z2 = rw2 / th;
-                const uint32_t m0 = 3u * (gidx(0, y, z) >> 2), m2 = 3u * (gidx(0, y2, z2) >> 2);
-                const U4 u0 = philox4x32_10(m0 + (uint32_t)lane, klo, khi, STREAM_BOND, k0, k1);
-                const U4 u2 = philox4x32_10(m2 + (uint32_t)lane, klo, khi, STREAM_BOND, k0, k1);
+                // lane b < 24: BOND block b of the row; lane 24 + b: QSPIN block b
+                const uint32_t i0 = gidx(0, y, z), i2 = gidx(0, y2, z2);
+                const bool bl = lane < 24;
+                const uint32_t st_ = bl ? STREAM_BOND : STREAM_QSPIN;
+                const uint32_t c0 = bl ? 3u * (i0 >> 2) + (uint32_t)lane : (i0 >> 2) + (uint32_t)(lane - 24);
+                const uint32_t c2 = bl ? 3u * (i2 >> 2) + (uint32_t)lane : (i2 >> 2) + (uint32_t)(lane - 24);
+                const U4 u0 = philox4x32_10(c0, klo, khi, st_, k0, k1);
+                const U4 u2 = philox4x32_10(c2, klo, khi, st_, k0, k1);
                 uint32_t rx[1], ry[1], rz[1], rx2[1], ry2[1], rz2[1];
-                row_aligned(u0, rx, ry, rz);
-                row_aligned(u2, rx2, ry2, rz2);
+                row_aligned(u0, y + G::TY * z, rx, ry, rz);
+                row_aligned(u2, rw2 < nrows ? y2 + G::TY * z2 : -1, rx2, ry2, rz2);
                 store_row(y, z, rx, ry, rz);
                 if (rw2 < nrows) store_row(y2, z2, rx2, ry2, rz2);
             }
@@ -682,9 +708,9 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
 
     // Step 2 inside the tile
     if constexpr (DIM == 2)
-        tile_label<64>(sm.par, sm.bx, sm.by, th, tw);
+        tile_label<64>(sm.f.par, sm.bx, sm.by, th, tw);
     else
-        tile_label3(sm.par, sm.bx, sm.by, sm.bz, tw, th, td);
+        tile_label3(sm.f.par, sm.bx, sm.by, sm.bz, tw, th, td);
 
     // One node per face site: key = global index of the piece's local root,
     // parent = the piece's first face slot (the representative).
@@ -696,13 +722,13 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
         rs[qq] = -1;
         if (s < S && slot_xyz<DIM>(s, t.e, x, y, z)) {
             const int r = y + G::TY * z, c = x >> 5;
-            rs[qq] = sroot(sm.par, head_of(run_heads(ih(r, c)), r * G::PW + 32 * c, x & 31));
+            rs[qq] = sroot(sm.f.par, head_of(run_heads(ih(r, c)), r * G::PW + 32 * c, x & 31));
         }
     }
     __syncthreads();
 #pragma unroll
     for (int qq = 0; qq < G::SPT; ++qq)
-        if (rs[qq] >= 0) atomicMin((int *)&sm.par[rs[qq]], (int)(INFO_BORDER | (uint32_t)(tid + qq * NT)));
+        if (rs[qq] >= 0) atomicMin((int *)&sm.f.par[rs[qq]], (int)(INFO_BORDER | (uint32_t)(tid + qq * NT)));
     __syncthreads();
 #pragma unroll
     for (int qq = 0; qq < G::SPT; ++qq) {
@@ -710,7 +736,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
         if (s >= S) break;
         const size_t node = nbase + s;
         if (rs[qq] >= 0) {
-            const int rep = sm.par[rs[qq]] & 0x7FFF;
+            const int rep = sm.f.par[rs[qq]] & 0x7FFF;
             p.npar[node] = (int32_t)(nbase + rep);
             p.nkey[node] = (int32_t)(gfor(rs[qq]) | (rep == s ? KEY_REP : 0u));
         } else {
@@ -732,16 +758,16 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
         for (uint32_t bits = run_heads(ih(r, c)); bits; bits &= bits - 1) {
             const int hx = __ffs(bits) - 1;
             const int hd = base + hx;
-            int x = hd, pp = sm.par[x];
+            int x = hd, pp = sm.f.par[x];
             while (pp != x && pp >= 0 && (uint32_t)pp < INFO_INTERIOR) {
                 x = pp;
-                pp = sm.par[x];
+                pp = sm.f.par[x];
             }
             if (x != hd) {
-                sm.par[hd] = x;
+                sm.f.par[hd] = x;
             } else if (pp == hd && 32 * c + hx < tw) {
-                const uint8_t s = cluster_state(gidx(32 * c + hx, y, z), klo, khi, k0, k1, q);
-                sm.par[hd] = (int)(INFO_INTERIOR | (uint32_t)s);
+                const uint8_t s = qsm ? sm.qs[r][32 * c + hx] : cluster_state(gidx(32 * c + hx, y, z), klo, khi, k0, k1, q);
+                sm.f.par[hd] = (int)(INFO_INTERIOR | (uint32_t)s);
                 ++ncl_interior;
             }
         }
@@ -761,9 +787,9 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
                 bits &= bits - 1;
                 if (hx >= vw) break;
                 const int nx = bits ? __ffs(bits) - 1 : 32;
-                const int v = sm.par[base + hx];
+                const int v = sm.f.par[base + hx];
                 const int root = (v < 0 || (uint32_t)v >= INFO_INTERIOR) ? base + hx : v;
-                atomicAdd((int *)&sm.par[root], (min(nx, vw) - hx) << 16);
+                atomicAdd((int *)&sm.f.par[root], (min(nx, vw) - hx) << 16);
             }
         }
         __syncthreads();
@@ -790,12 +816,12 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
             if (x >= tw) break;
             if (e == 0 || ((heads >> (x & 31)) & 1u)) {
                 const int hd = e == 0 ? head_of(heads, base, x & 31) : base + (x & 31);
-                const int v = sm.par[hd];
+                const int v = sm.f.par[hd];
                 if ((uint32_t)v >= INFO_INTERIOR) {   // records: negative or >= INFO_INTERIOR
                     info = v;
                     root = hd;
                 } else {
-                    info = sm.par[v];
+                    info = sm.f.par[v];
                     root = v;
                 }
             }
@@ -844,7 +870,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
             const int base = r * G::PW + 32 * c;
             const int vw = min(32, tw - 32 * c);
             for (uint32_t bits = run_heads(ih(r, c)) & valid_mask(0, vw); bits; bits &= bits - 1) {
-                const int v = sm.par[base + __ffs(bits) - 1];
+                const int v = sm.f.par[base + __ffs(bits) - 1];
                 if (v < 0) {   // piece size: bits 16-30 (bit 31 is the border flag)
                     p.psize[nbase + (v & 0x7FFF)] = (int32_t)(((uint32_t)v >> 16) & 0x7FFFu);
                 } else if ((uint32_t)v >= INFO_INTERIOR) {   // bits 16-29 (bit 30 is the flag)
@@ -857,7 +883,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
     long long v4[4] = {nb, ncl_interior, c2, 0};
     DevObs *o = obs + j;
     unsigned long long *const dst[4] = {&o->nbonds, &o->nclusters, &o->csize2, nullptr};
-    block_sum_atomic<NT, 4>(v4, dst, sm.u.red);
+    block_sum_atomic<NT, 4>(v4, dst, sm.red);
 }
 
 // ------------------------------------------------------------------ merge
