@@ -892,7 +892,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 5)
 // ------------------------------------------------------------------ merge
 template <int DIM>
 struct PMC {
-    static constexpr int MT = DIM == 2 ? 96 : 256;                  // threads per block
+    static constexpr int MT = DIM == 2 ? 96 : 512;                  // threads per block (measured best)
     static constexpr int EPT = (PG<DIM>::FT + MT - 1) / MT;        // crossing links per thread
     static constexpr int NPT = PG<DIM>::S / MT;                    // slots per thread
     static_assert(PG<DIM>::S % MT == 0, "merge launch shape");
@@ -900,13 +900,11 @@ struct PMC {
 
 // Master step 2 of Sec. II.A on the face nodes: link e of a tile joins slot
 // f of its + face along axis a to slot f of the - face of the next tile
-// along a (e = f, F0 + f, F0 + F1 + f for a = 0, 1, 2).  The block's links
-// first meet in a shared-memory forest over the pieces they touch (the
-// tile's own, ids [0, S); its + neighbour's along axis a, ids [(1 + a) S,
-// (2 + a) S)); only a link that joins two of those sets there goes on to
-// the global forest, union by key with the unions' finds advancing in lock
-// step.  A slot's piece: its own slot for a representative, else its
-// parent (its representative): each slot ends one link only.
+// along a (e = f, F0 + f, F0 + F1 + f for a = 0, 1, 2); union by key, the
+// finds of all of a thread's links advancing in lock step.  (A per-block
+// shared-memory forest that filters links joining pieces already joined, as
+// the Ising merge has, made the 3D merge slower: its pieces are small and
+// seldom meet twice.)
 template <int DIM>
 __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p)
 {
@@ -932,8 +930,6 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p)
             ax[qq] = a;
         }
     }
-    __shared__ int lp[(1 + DIM) * S];
-    for (int i = threadIdx.x; i < (1 + DIM) * S; i += MC::MT) lp[i] = i;
     int pa[MC::EPT], pb[MC::EPT], ka[MC::EPT], kb[MC::EPT];
 #pragma unroll
     for (int qq = 0; qq < MC::EPT; ++qq) {
@@ -943,17 +939,9 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p)
         ka[qq] = p.nkey[na[qq]];
         kb[qq] = p.nkey[nb[qq]];
     }
-    __syncthreads();
     bool live[MC::EPT];
 #pragma unroll
-    for (int qq = 0; qq < MC::EPT; ++qq) {
-        live[qq] = false;
-        if (na[qq] < 0) continue;
-        const int own = lt * S, nbr = nt[qq] * S;
-        const int la = ((uint32_t)ka[qq] & KEY_REP) ? na[qq] - own : pa[qq] - own;
-        const int lb = (1 + ax[qq]) * S + (((uint32_t)kb[qq] & KEY_REP) ? nb[qq] - nbr : pb[qq] - nbr);
-        live[qq] = sunite_linked(lp, la, lb);
-    }
+    for (int qq = 0; qq < MC::EPT; ++qq) live[qq] = na[qq] >= 0;
     // the remaining unions in lock step (path splitting on the way up; the
     // larger key's root is hung under the smaller by compare-and-swap)
     int xa[MC::EPT], xb[MC::EPT], sa[MC::EPT], sb[MC::EPT];
