@@ -53,6 +53,28 @@ def test_potts_larger_lattices(sw, orc):
     _compare(sw, orc, 2, 1024, 3, 1.0 / np.log(1 + np.sqrt(3)), seed=2, calls=(2,))
 
 
+# Tiles are 128 x 64 sites in 2D and 32 x 16 x 16 in 3D: lattices of several
+# tile columns whose last tile is ragged, sides that 4 does not divide (rows
+# then start inside a Philox block: per-site draws), and 2 mod 4.
+@pytest.mark.parametrize("L", [129, 130, 200, 257])
+def test_potts_2d_tiles(sw, orc, L):
+    _compare(sw, orc, 2, L, 3, 1.0 / np.log(1 + np.sqrt(3)), seed=L)
+
+
+@pytest.mark.parametrize("L", [33, 36, 40, 50, 65])
+def test_potts_3d_tiles(sw, orc, L):
+    _compare(sw, orc, 3, L, 3, 1.8164, seed=L, calls=(2, 1))
+
+
+def test_potts_no_bonds_and_all_states(sw, orc):
+    """T so high that the threshold is 0 (no bond: every site its own cluster)
+    and q = 256 (every byte value a state)."""
+    _compare(sw, orc, 2, 200, 5, 1e12, seed=3)
+    _compare(sw, orc, 3, 40, 2, 1e12, seed=4)
+    _compare(sw, orc, 2, 160, 256, 0.3, seed=5)
+    _compare(sw, orc, 3, 36, 256, 0.3, seed=6)
+
+
 def test_potts_set_spins_checks_states(sw):
     with sw.PottsLattice(3, 5, 3, T=1.0) as lat:
         s = np.zeros(125, np.uint8)

@@ -58,6 +58,20 @@ def test_potts_pcc_bit_exact(sw, orc, dim, L, n, open):
         assert flags.any() and not flags.all()
 
 
+@pytest.mark.parametrize("dim,L,n", [(2, 200, 120), (2, 130, 150), (3, 40, 60), (3, 50, 40), (3, 66, 20)])
+@pytest.mark.parametrize("open", [False, True])
+def test_potts_pcc_several_tiles(sw, orc, dim, L, n, open):
+    """Lattices of several tiles along every axis, ragged last tiles, sides
+    that 4 does not divide."""
+    _compare(sw, orc, dim, L, 3, seed=L + 1, calls=(n // 2, n - n // 2), open=open, pcc=True)
+
+
+@pytest.mark.parametrize("dim,L", [(2, 200), (2, 257), (3, 40), (3, 50)])
+def test_potts_open_several_tiles(sw, orc, dim, L):
+    for T in ((0.9, 1.2) if dim == 2 else (1.6, 2.2)):
+        _compare(sw, orc, dim, L, 2, T, seed=L, open=True)
+
+
 def test_potts_pcc_2d_L256(sw, orc):
     """A lattice of 8 x 8 warps per row pattern and 2^16 sites, 300 sweeps."""
     _compare(sw, orc, 2, 256, 3, seed=3, calls=(150, 150), pcc=True)
