@@ -942,6 +942,26 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p)
     bool live[MC::EPT];
 #pragma unroll
     for (int qq = 0; qq < MC::EPT; ++qq) live[qq] = na[qq] >= 0;
+    // First try, one compare-and-swap: hang the larger-key one of the two
+    // pieces' representatives under the other.  Every parent carries a smaller
+    // key than its children, so a root of key k holds no node of smaller key:
+    // if that representative is still a root, the two sets differ and the
+    // link joins them (its new parent need not be a root).
+#pragma unroll
+    for (int qq = 0; qq < MC::EPT; ++qq) {
+        if (!live[qq]) continue;
+        const bool ra = ((uint32_t)ka[qq] & KEY_REP) != 0u, rb = ((uint32_t)kb[qq] & KEY_REP) != 0u;
+        const int u = ra ? na[qq] : pa[qq], v = rb ? nb[qq] : pb[qq];
+        if (u == v) {
+            live[qq] = false;
+            continue;
+        }
+        const bool u_hi = ((uint32_t)ka[qq] & KEY_MASK) > ((uint32_t)kb[qq] & KEY_MASK);
+        const int hi = u_hi ? u : v, lo = u_hi ? v : u;
+        // a representative whose parent was read as another node is no root
+        const bool inner = u_hi ? (ra && pa[qq] != na[qq]) : (rb && pb[qq] != nb[qq]);
+        if (!inner && atomicCAS(p.npar + hi, hi, lo) == hi) live[qq] = false;
+    }
     // the remaining unions in lock step (path splitting on the way up; the
     // larger key's root is hung under the smaller by compare-and-swap)
     int xa[MC::EPT], xb[MC::EPT], sa[MC::EPT], sb[MC::EPT];
