@@ -1261,6 +1261,21 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT, 64 / ((MergeCfg<TH>::MT + 31
         const int lb = (right ? S : 2 * S) + (((uint32_t)kb[q] & KEY_REP) ? nb[q] - nbr : pb[q] - nbr);
         live[q] = sunite_linked(lp, la, lb);
     }
+    // First try, one compare-and-swap: hang the larger-key one of the two
+    // pieces' representatives under the other.  Every parent carries a smaller
+    // key than its children, so a root of key k holds no node of smaller key:
+    // if that representative is still a root, the two sets differ and the
+    // link joins them (its new parent need not be a root).
+#pragma unroll
+    for (int q = 0; q < MC::EPT; ++q) {
+        if (!live[q]) continue;
+        const bool ra = ((uint32_t)ka[q] & KEY_REP) != 0u, rb = ((uint32_t)kb[q] & KEY_REP) != 0u;
+        const int u = ra ? na[q] : pa[q], v = rb ? nb[q] : pb[q];
+        const bool u_hi = ((uint32_t)ka[q] & KEY_MASK) > ((uint32_t)kb[q] & KEY_MASK);
+        const int hi = u_hi ? u : v, lo = u_hi ? v : u;
+        const bool inner = u_hi ? (ra && pa[q] != na[q]) : (rb && pb[q] != nb[q]);
+        if (!inner && atomicCAS(R.npar + hi, hi, lo) == hi) live[q] = false;
+    }
     // The thread's remaining unions (gunite_by_key's steps) advance in lock
     // step, both finds of every link at once, so their L2 round trips
     // overlap: each pass climbs every find that is not at a root (path
