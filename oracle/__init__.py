@@ -136,6 +136,10 @@ def lib():
             L.swo_spans_nd.restype = ctypes.c_int
             L.swo_potts_run_pcc.argtypes = [i32, i32, i32, u64, u64, i32, i32, i32, i32, P, P, P, P, P]
             L.swo_potts_run_pcc.restype = ctypes.c_int
+            L.swo_potts_run_rules.argtypes = [i32, i32, i32, u64, u64, i32, i32, i32, i32, i32, P, P, P, P, P]
+            L.swo_potts_run_rules.restype = ctypes.c_int
+            L.swo_windings_nd.argtypes = [i32, i32, P, P]
+            L.swo_windings_nd.restype = ctypes.c_int
             L.swo_csize2.argtypes = [i32, P]
             L.swo_csize2.restype = i64
             L.swo_pcc_delta.argtypes = [u64]
@@ -341,6 +345,15 @@ def spans_nd(dim: int, L: int, lab: np.ndarray):
     return tuple(int(v) for v in out[:dim])
 
 
+def windings_nd(dim: int, L: int, bond: np.ndarray):
+    """Topological rule per axis: (winds x, winds y[, winds z])."""
+    bond = np.ascontiguousarray(bond, dtype=np.uint8)
+    out = np.zeros(3, dtype=np.int32)
+    if lib().swo_windings_nd(dim, L, _ptr(bond), _ptr(out)) != 0:
+        raise MemoryError("swo_windings_nd")
+    return tuple(int(v) for v in out[:dim])
+
+
 def label_nd(dim: int, L: int, bond: np.ndarray):
     bond = np.ascontiguousarray(bond, dtype=np.uint8)
     lab = np.empty(L ** dim, dtype=np.int32)
@@ -373,14 +386,15 @@ def potts_measure(dim: int, L: int, q: int, spin: np.ndarray, open: bool = False
 class PottsChain:
     """A q-state Potts lattice (d = 2 or 3) advanced by the oracle; open=True
     gives open boundaries, pcc=True the PCC feedback (the threshold starts at
-    2^31 and J, T are ignored)."""
+    2^31 and J, T are ignored), wind=True the topological rule for the span
+    flags (reported every sweep, and the feedback's criterion under PCC)."""
 
     def __init__(self, dim: int, L: int, q: int, J: float, T: float, seed: int, csize: bool = False,
-                 open: bool = False, pcc: bool = False):
+                 open: bool = False, pcc: bool = False, wind: bool = False):
         if dim not in (2, 3) or L < 2 or not 2 <= q <= 256:
             raise ValueError("dim in {2, 3}, L >= 2, 2 <= q <= 256")
         self.dim, self.L, self.q, self.seed, self.csize = int(dim), int(L), int(q), int(seed), bool(csize)
-        self.open, self.pcc = bool(open), bool(pcc)
+        self.open, self.pcc, self.wind = bool(open), bool(pcc), bool(wind)
         self.threshold = (1 << 31) if pcc else threshold_potts(J, T)
         self.sweep = 0
         self.spin = potts_hot_start(dim, L, q, seed)
@@ -392,11 +406,12 @@ class PottsChain:
         if nsweeps <= 0:
             return obs
         thr = np.array([self.threshold], dtype=np.uint64)
-        rc = lib().swo_potts_run_pcc(self.dim, self.L, self.q, self.seed, self.sweep, nsweeps,
-                                     1 if self.pcc else 0, 1 if self.open else 0, 1 if self.csize else 0,
-                                     _ptr(thr), _ptr(self.spin), _ptr(self.label), _ptr(self.bond), _ptr(obs))
+        rc = lib().swo_potts_run_rules(self.dim, self.L, self.q, self.seed, self.sweep, nsweeps,
+                                       1 if self.pcc else 0, 1 if self.open else 0, 1 if self.csize else 0,
+                                       1 if self.wind else 0, _ptr(thr), _ptr(self.spin), _ptr(self.label),
+                                       _ptr(self.bond), _ptr(obs))
         if rc != 0:
-            raise MemoryError("swo_potts_run_pcc")
+            raise MemoryError("swo_potts_run_rules")
         self.threshold = int(thr[0])
         self.sweep += nsweeps
         return obs

@@ -724,6 +724,80 @@ int swo_spans_nd(int32_t dim, int32_t L, const int32_t *label, int32_t *spans)
     return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Topological rule in d dimensions (Sec. III: the winding criterion stated
+ * for the periodic box of any dimension): a cluster winds around axis a iff
+ * it holds a closed path of bonds whose net displacement along a is a
+ * non-zero multiple of L.  As swo_windings does in 2D: every cluster is
+ * explored breadth first from its lowest site, each site getting an
+ * unwrapped position (each bond one lattice step, the periodic link included);
+ * a bond reaching an explored site at a position other than the predicted one
+ * closes a cycle with that displacement, and every cycle is a sum of such
+ * cycles.  wraps[a] = 1 iff some cluster winds around axis a (a < dim).
+ * ---------------------------------------------------------------------- */
+int swo_windings_nd(int32_t dim, int32_t L, const uint8_t *bond, int32_t *wraps)
+{
+    uint64_t N = nd_sites(dim, L), l = (uint64_t)L;
+    int64_t *u = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)N);
+    uint8_t *seen = (uint8_t *)calloc((size_t)N, 1);
+    uint64_t *queue = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
+    if (!u || !seen || !queue) {
+        free(u);
+        free(seen);
+        free(queue);
+        return -1;
+    }
+    for (int a = 0; a < 3; a++)
+        wraps[a] = 0;
+    uint64_t stride[3] = {1, l, l * l};
+    for (uint64_t s = 0; s < N; s++) {
+        if (seen[s])
+            continue;
+        uint64_t head = 0, tail = 0;
+        seen[s] = 1;
+        u[3 * s] = u[3 * s + 1] = u[3 * s + 2] = 0;
+        queue[tail++] = s;
+        while (head < tail) {
+            uint64_t i = queue[head++];
+            uint64_t c[3] = {i % l, (i / l) % l, dim == 3 ? i / (l * l) : 0};
+            /* the 2 dim links at site i: its own + link along each axis, and
+             * the + link of its - neighbour along each axis */
+            for (int a = 0; a < dim; a++) {
+                for (int side = 0; side < 2; side++) {
+                    uint64_t j;
+                    int has;
+                    if (side == 0) {
+                        j = c[a] + 1 == l ? i - c[a] * stride[a] : i + stride[a];
+                        has = (bond[i] >> a) & 1;
+                    } else {
+                        j = c[a] == 0 ? i + (l - 1) * stride[a] : i - stride[a];
+                        has = (bond[j] >> a) & 1;
+                    }
+                    if (!has)
+                        continue;
+                    int64_t p[3] = {u[3 * i], u[3 * i + 1], u[3 * i + 2]};
+                    p[a] += side == 0 ? 1 : -1;
+                    if (!seen[j]) {
+                        seen[j] = 1;
+                        u[3 * j] = p[0];
+                        u[3 * j + 1] = p[1];
+                        u[3 * j + 2] = p[2];
+                        queue[tail++] = j;
+                    } else {
+                        for (int b = 0; b < 3; b++)
+                            if (u[3 * j + b] != p[b])
+                                wraps[b] = 1;
+                    }
+                }
+            }
+        }
+    }
+    free(u);
+    free(seen);
+    free(queue);
+    return 0;
+}
+
 int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
                   int32_t csize, uint64_t thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs)
 {
@@ -733,6 +807,14 @@ int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t swe
 int swo_potts_run_pcc(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
                       int32_t pcc, int32_t open, int32_t csize, uint64_t *thr_io, uint8_t *spin, int32_t *label,
                       uint8_t *bond, swo_obs *obs)
+{
+    return swo_potts_run_rules(dim, L, q, seed, sweep0, nsweeps, pcc, open, csize, 0, thr_io, spin, label, bond,
+                               obs);
+}
+
+int swo_potts_run_rules(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
+                        int32_t pcc, int32_t open, int32_t csize, int32_t wind, uint64_t *thr_io, uint8_t *spin,
+                        int32_t *label, uint8_t *bond, swo_obs *obs)
 {
     uint64_t thr = *thr_io;
     uint64_t N = nd_sites(dim, L);
@@ -747,7 +829,15 @@ int swo_potts_run_pcc(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t
         o.threshold = thr;
         o.nbonds = swo_potts_bonds_open(dim, L, seed, k, thr, spin, b, open);
         o.nclusters = swo_label_nd(dim, L, b, label);
-        if (pcc) {
+        if (wind) {   /* the topological rule, reported every sweep */
+            int32_t w[3] = {0, 0, 0};
+            if (swo_windings_nd(dim, L, b, w) != 0) {
+                rc = -1;
+                break;
+            }
+            o.spans_x = w[0];
+            o.spans_y = w[1] | w[2];     /* y, or in 3D y or z */
+        } else if (pcc) {
             int32_t sp[3] = {0, 0, 0};
             if (swo_spans_nd(dim, L, label, sp) != 0) {
                 rc = -1;

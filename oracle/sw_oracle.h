@@ -151,6 +151,18 @@ int swo_spans_nd(int32_t dim, int32_t L, const int32_t *label, int32_t *spans);
 int swo_potts_run_pcc(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
                       int32_t pcc, int32_t open, int32_t csize, uint64_t *thr_io, uint8_t *spin, int32_t *label,
                       uint8_t *bond, swo_obs *obs);
+/* Topological rule in d = 2 or 3 dimensions (Sec. III): wraps[a] = 1 iff
+ * some cluster of the bond set winds around the box along axis a (holds a
+ * closed path of bonds whose net displacement along a is a non-zero multiple
+ * of L), for a < dim; wraps[2] = 0 in 2D.  Returns 0, or -1 when memory is
+ * short. */
+int swo_windings_nd(int32_t dim, int32_t L, const uint8_t *bond, int32_t *wraps);
+/* As swo_potts_run_pcc; wind != 0 switches the span test to the topological
+ * rule (swo_windings_nd) and reports it every sweep, PCC or not (spans_x:
+ * axis x; spans_y: axis y, in 3D y or z). */
+int swo_potts_run_rules(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
+                        int32_t pcc, int32_t open, int32_t csize, int32_t wind, uint64_t *thr_io, uint8_t *spin,
+                        int32_t *label, uint8_t *bond, swo_obs *obs);
 /* nsweeps sweeps at the fixed threshold thr (obs[].csize2 filled when csize). */
 int swo_potts_run(int32_t dim, int32_t L, int32_t q, uint64_t seed, uint64_t sweep0, int32_t nsweeps,
                   int32_t csize, uint64_t thr, uint8_t *spin, int32_t *label, uint8_t *bond, swo_obs *obs);
