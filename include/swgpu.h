@@ -142,15 +142,18 @@ int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags);
  * torus, d = 2 or 3, L^d <= 2^30 sites: the cluster update of Sec. I with
  * equal states bonding (H = -J sum delta(s_i, s_j), P = 1 - exp(-J/T); q = 2
  * is Ising at J/2) on the d-dimensional lattice the paper states its method
- * for (Sec. II).  A site-level path, slower than the tiled 2D Ising one.
- * Sites i = x + L y (+ L^2 z); link l = d i + dir (dir 0: +x, 1: +y, 2: +z)
+ * for (Sec. II), on the tiled design of the 2D Ising path (2D tiles of 128 x
+ * 64 sites, 3D tiles of 32 x 16 x 16).  Sites i = x + L y (+ L^2 z); link l = d i + dir (dir 0: +x, 1: +y, 2: +z)
  * draws word (l mod 4) of Philox(l/4, k, BOND); a cluster with root r takes
  * state floor(w q / 2^32), w = word (r mod 4) of Philox(r/4, k, stream 3);
  * the hot start is the same of word (i mod 4) of Philox(i/4, 0, INIT).
  * Observables: bond_sum = sum over links of (2 delta - 1), mag = sum over
- * sites of (q [s_i = 0] - 1).  flags: SW_FLAG_CSIZE and SW_FLAG_OPEN (open
+ * sites of (q [s_i = 0] - 1).  flags: SW_FLAG_CSIZE, SW_FLAG_OPEN (open
  * boundaries: the last coordinate along a direction has no + link, which
- * neither bonds nor enters bond_sum), or 0.  The other calls take the context
+ * neither bonds nor enters bond_sum) and SW_FLAG_WIND (the topological rule
+ * of Sec. III reported every sweep: spans_x = some cluster winds around the
+ * box along x, spans_y = along y, or in 3D along y or z), or 0.  The other
+ * calls take the context
  * as usual (spins, labels and bond bytes have L^d entries, bond bit dir);
  * pcc_step (on a lattice not made by pcc_create_potts) and sw_profile answer
  * SW_ERR_STATE.  Errors: SW_ERR_ARG, SW_ERR_NOMEM, SW_ERR_CUDA. */
@@ -164,7 +167,9 @@ int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, d
  * axis a when it occupies all L hyperplanes perpendicular to a (the
  * extension rule; under open boundaries, touching both faces).  Per sweep
  * spans_x reports the x axis and spans_y the y axis, or in 3D the y or the z
- * axis.  flags: SW_FLAG_CSIZE, SW_FLAG_OPEN or 0.  Errors as sw_create_potts. */
+ * axis.  With SW_FLAG_WIND the criterion is the topological rule instead
+ * (some cluster winds around the box along some axis).  flags: SW_FLAG_CSIZE,
+ * SW_FLAG_OPEN, SW_FLAG_WIND or 0.  Errors as sw_create_potts. */
 int pcc_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t seed, uint32_t flags);
 
 /* Release the context and all its device memory.  NULL is accepted. */

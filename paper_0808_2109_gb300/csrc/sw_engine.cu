@@ -262,6 +262,7 @@ struct sw_ctx {
     // nstate its representatives' new states
     bool is_potts = false;
     uint8_t *nstate = nullptr;
+    int4 *wlink = nullptr;   // a Potts lattice's node links under the topological rule
     PottsDev pd{};
     int64_t nsites = 0;   // L^d
 
@@ -293,7 +294,7 @@ void ctx_free(sw_ctx *c)
     c->ev_pool.clear();
     void *ptrs[] = {c->spin, c->label, c->code, c->bondbits, c->cross, c->npar, c->nkey,
                     c->nfinal, c->thr_dev, c->rep_dev, c->tile_rep, c->jbase, c->bond_bytes, c->obs,
-                    c->pmask, c->cid, c->cand, c->ncand, c->cov, c->psize, c->csize, c->nlink, c->nstate};
+                    c->pmask, c->cid, c->cand, c->ncand, c->cov, c->psize, c->csize, c->nlink, c->nstate, c->wlink};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -676,7 +677,8 @@ int potts_create(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t thr, 
 {
     if (!out) return SW_ERR_ARG;
     *out = nullptr;
-    if ((dim != 2 && dim != 3) || L < 2 || q < 2 || q > 256 || (flags & ~(SW_FLAG_CSIZE | SW_FLAG_OPEN)) != 0)
+    if ((dim != 2 && dim != 3) || L < 2 || q < 2 || q > 256 ||
+        (flags & ~(SW_FLAG_CSIZE | SW_FLAG_OPEN | SW_FLAG_WIND)) != 0)
         return SW_ERR_ARG;
     const int64_t N = dim == 2 ? (int64_t)L * L : (int64_t)L * L * L;
     if (N > ((int64_t)1 << 30)) return SW_ERR_ARG;
@@ -700,6 +702,7 @@ int potts_create(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t thr, 
     c->thr = thr;
     c->pcc = pcc;
     c->open = (flags & SW_FLAG_OPEN) != 0;
+    c->wind = (flags & SW_FLAG_WIND) != 0;
     if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     c->stream = c->own_stream;
     PottsGeometry g{};
@@ -719,11 +722,13 @@ int potts_create(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t thr, 
         if ((e = dalloc(&c->psize, nt * S)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&c->csize, nt * S)) != cudaSuccess) return fail(e);
     }
+    if (c->wind && (e = dalloc(&c->wlink, nt * S)) != cudaSuccess) return fail(e);
     PottsDev &p = c->pd;
     p.dim = dim;
     p.L = L;
     p.q = q;
-    p.flags = (pcc ? RF_PCC : 0) | (c->open ? RF_OPEN : 0) | ((flags & SW_FLAG_CSIZE) ? RF_CSIZE : 0);
+    p.flags = (pcc ? RF_PCC : 0) | (c->open ? RF_OPEN : 0) | ((flags & SW_FLAG_CSIZE) ? RF_CSIZE : 0) |
+              (c->wind ? RF_WIND : 0);
     p.ntx = g.ntx;
     p.nty = g.nty;
     p.ntz = g.ntz;
@@ -742,6 +747,7 @@ int potts_create(sw_ctx **out, int32_t dim, int32_t L, int32_t q, uint64_t thr, 
     p.nstate = c->nstate;
     p.psize = c->psize;
     p.csize = c->csize;
+    p.wlink = c->wlink;
     if (pcc) {
         // per node and axis the candidate ids of roots; per axis the
         // candidates of the face (F = L^(dim-1) sites), their counts and

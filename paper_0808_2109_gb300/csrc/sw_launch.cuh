@@ -39,7 +39,7 @@ inline int slots_of(int TH) { return 2 * TW + 2 * TH; }
 // the new state of a representative), and with RF_CSIZE the sizes of the
 // pieces and clusters at their nodes.
 struct PottsDev {
-    int32_t dim, L, q, flags;          // flags: RF_OPEN | RF_CSIZE | RF_PCC
+    int32_t dim, L, q, flags;          // flags: RF_OPEN | RF_CSIZE | RF_PCC | RF_WIND
     int32_t ntx, nty, ntz, ntiles;     // tiles along x, y, z (1 in 2D)
     int64_t N;
     uint64_t thr, seed;
@@ -51,6 +51,7 @@ struct PottsDev {
     uint32_t *nfinal;                  // ntiles * slots: root, or FINAL_ALIAS | a representative
     uint8_t *nstate;                   // ntiles * slots: a representative's new state
     int32_t *psize, *csize;            // ntiles * slots (RF_CSIZE only)
+    int4 *wlink;                       // RF_WIND: ntiles * slots node links {parent, dx, dy, dz}
     // PCC (null otherwise): the threshold lives on the device and follows the
     // feedback; per node and axis a < dim, a root's candidate id (cid, id + 2),
     // per border piece its occupied coordinates (pmask), per axis the

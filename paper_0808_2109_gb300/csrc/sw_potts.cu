@@ -889,6 +889,77 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 5)
     block_sum_atomic<NT, 4>(v4, dst, sm.red);
 }
 
+// ------------------------------------------------ topological rule (RF_WIND)
+// A cluster percolates when it winds around the box (Sec. III): some closed
+// path of its bonds has a non-zero net displacement.  Every node carries its
+// parent and its unwrapped displacement from that parent, one 16-byte word
+// changed by 16-byte compare-and-swap so that the four move together; a root
+// links to itself with displacement 0.  The displacements are exact: a set's
+// nodes lift to a connected set of at most N sites, so they stay below 2^30.
+struct alignas(16) WLink {
+    int32_t parent, dx, dy, dz;
+};
+
+__device__ __forceinline__ WLink wl_read(WLink *w)
+{
+    const WLink z{0, 0, 0, 0};
+    return atomicCAS(w, z, z);   // an atomic 16-byte read (rewrites an equal word)
+}
+
+// Root of x with pos(x) - pos(root); the walk halves the path (x's link is
+// moved to its grandparent with the summed displacement: a failed swap means
+// another walk moved it first).
+__device__ __forceinline__ int wfind3(WLink *wl, int x, int &ox, int &oy, int &oz)
+{
+    ox = oy = oz = 0;
+    WLink w = wl_read(wl + x);
+    while (w.parent != x) {
+        const WLink g = wl_read(wl + w.parent);
+        if (g.parent != w.parent) {
+            const WLink nw{g.parent, w.dx + g.dx, w.dy + g.dy, w.dz + g.dz};
+            atomicCAS(wl + x, w, nw);
+            ox += nw.dx;
+            oy += nw.dy;
+            oz += nw.dz;
+            x = g.parent;
+            w = wl_read(wl + x);
+        } else {
+            ox += w.dx;
+            oy += w.dy;
+            oz += w.dz;
+            x = w.parent;
+            w = g;
+        }
+    }
+    return x;
+}
+
+// The link from node a to node b steps +1 along axis ax.  Roots of the same
+// set: the cycle it closes has net displacement pos(a) + e_ax - pos(b) through
+// the tree, non-zero exactly when it winds (recorded per axis).  Else the root
+// of larger key hangs under the other with its displacement from it.
+__device__ __forceinline__ void wunite3(WLink *wl, const int32_t *key, int a, int b, int ax, DevObs *o)
+{
+    for (;;) {
+        int oax, oay, oaz, obx, oby, obz;
+        const int ra = wfind3(wl, a, oax, oay, oaz);
+        const int rb = wfind3(wl, b, obx, oby, obz);
+        // pos(rb) - pos(ra) = (pos(a) - off_a ... ) through the link: off_a + e_ax - off_b
+        const int cx = oax + (ax == 0) - obx, cy = oay + (ax == 1) - oby, cz = oaz + (ax == 2) - obz;
+        if (ra == rb) {
+            if (cx) atomicOr(&o->spans_x, 1);
+            if (cy || cz) atomicOr(&o->spans_y, 1);   // y, or in 3D y or z
+            return;
+        }
+        const bool a_lo = (uint32_t)key[ra] < (uint32_t)key[rb];
+        const int lo = a_lo ? ra : rb, hi = a_lo ? rb : ra;
+        const WLink root{hi, 0, 0, 0};
+        const WLink nl = a_lo ? WLink{lo, cx, cy, cz} : WLink{lo, -cx, -cy, -cz};
+        const WLink old = atomicCAS(wl + hi, root, nl);
+        if (old.parent == hi && old.dx == 0 && old.dy == 0 && old.dz == 0) return;
+    }
+}
+
 // ------------------------------------------------------------------ merge
 template <int DIM>
 struct PMC {
@@ -905,8 +976,8 @@ struct PMC {
 // shared-memory forest that filters links joining pieces already joined, as
 // the Ising merge has, made the 3D merge slower: its pieces are small and
 // seldom meet twice.)
-template <int DIM>
-__global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p)
+template <int DIM, bool W>
+__global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p, int j, DevObs *obs)
 {
     using G = PG<DIM>;
     using MC = PMC<DIM>;
@@ -929,6 +1000,13 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p)
             nb[qq] = nt[qq] * S + face_off<DIM>(a, 0) + f;
             ax[qq] = a;
         }
+    }
+    if (W && (p.flags & RF_WIND)) {
+        WLink *wl = reinterpret_cast<WLink *>(p.wlink);
+#pragma unroll
+        for (int qq = 0; qq < MC::EPT; ++qq)
+            if (na[qq] >= 0) wunite3(wl, p.nkey, na[qq], nb[qq], ax[qq], obs + j);
+        return;
     }
     int pa[MC::EPT], pb[MC::EPT], ka[MC::EPT], kb[MC::EPT];
 #pragma unroll
@@ -1010,12 +1088,50 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p)
     }
 }
 
-// One round of pointer jumping on the representatives' parents.
+// Topological rule: every node's link before the unions -- its parent from
+// the tile kernel (its piece's representative, or itself) and its
+// displacement from it, both sites of one tile.
 template <int DIM>
+__global__ void __launch_bounds__(PMC<DIM>::MT) k_pwind_init(const PottsDev p)
+{
+    using G = PG<DIM>;
+    using MC = PMC<DIM>;
+    const int lt = blockIdx.x, base = lt * G::S;
+    const PTile t = ptile_of<DIM>(p, lt);
+    WLink *wl = reinterpret_cast<WLink *>(p.wlink);
+#pragma unroll
+    for (int qq = 0; qq < MC::NPT; ++qq) {
+        const int s = threadIdx.x + qq * MC::MT, n = base + s;
+        const int rep = p.npar[n];
+        WLink w{n, 0, 0, 0};
+        int x, y, z, xr, yr, zr;
+        if ((uint32_t)p.nkey[n] != KEY_NONE && rep != n && slot_xyz<DIM>(s, t.e, x, y, z) &&
+            slot_xyz<DIM>(rep - base, t.e, xr, yr, zr))
+            w = WLink{rep, x - xr, y - yr, z - zr};
+        wl[n] = w;
+    }
+}
+
+// One round of pointer jumping on the representatives' parents.
+template <int DIM, bool W>
 __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_jump(const PottsDev p)
 {
     using MC = PMC<DIM>;
     const int base = blockIdx.x * PG<DIM>::S;
+    if (W && (p.flags & RF_WIND)) {
+        WLink *wl = reinterpret_cast<WLink *>(p.wlink);
+#pragma unroll
+        for (int qq = 0; qq < MC::NPT; ++qq) {
+            const int n = base + threadIdx.x + qq * MC::MT;
+            const uint32_t key = (uint32_t)p.nkey[n];
+            if (key == KEY_NONE || !(key & KEY_REP)) continue;
+            const WLink w = wl_read(wl + n);
+            if (w.parent == n) continue;
+            const WLink g = wl_read(wl + w.parent);
+            if (g.parent != w.parent) atomicCAS(wl + n, w, WLink{g.parent, w.dx + g.dx, w.dy + g.dy, w.dz + g.dz});
+        }
+        return;
+    }
     int pr[MC::NPT];
 #pragma unroll
     for (int qq = 0; qq < MC::NPT; ++qq) {
@@ -1038,20 +1154,26 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_jump(const PottsDev p)
 // representative stores FINAL_ALIAS | its parent (a representative of the
 // same cluster) for the neighbour's halo.  Counts the clusters that touch a
 // tile face (one root node each).
-template <int DIM>
+template <int DIM, bool W>
 __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_resolve(const PottsDev p, int j, uint64_t sweep0,
                                                                  DevObs *obs)
 {
     using MC = PMC<DIM>;
     const int base = blockIdx.x * PG<DIM>::S;
+    // under the topological rule the forest lives in the node links (their
+    // first word is the parent); npar keeps each node's representative
+    const bool wind = W && (p.flags & RF_WIND);
+    const int32_t *wpar = reinterpret_cast<const int32_t *>(p.wlink);
+    auto parent = [&](int x) { return wind ? gload(wpar + 4 * (size_t)x) : gload(p.npar + x); };
     uint32_t key[MC::NPT];
-    int r[MC::NPT], pr[MC::NPT];
+    int r[MC::NPT], pr[MC::NPT], rep[MC::NPT];
 #pragma unroll
     for (int qq = 0; qq < MC::NPT; ++qq) key[qq] = (uint32_t)p.nkey[base + threadIdx.x + qq * MC::MT];
 #pragma unroll
     for (int qq = 0; qq < MC::NPT; ++qq) {
         r[qq] = base + threadIdx.x + qq * MC::MT;
-        pr[qq] = gload(p.npar + r[qq]);
+        rep[qq] = gload(p.npar + r[qq]);
+        pr[qq] = wind ? parent(r[qq]) : rep[qq];
     }
     auto is_rep = [](uint32_t kk) { return kk != KEY_NONE && (kk & KEY_REP); };
     for (;;) {
@@ -1065,12 +1187,12 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_resolve(const PottsDev 
         if (!more) break;
 #pragma unroll
         for (int qq = 0; qq < MC::NPT; ++qq)
-            if (is_rep(key[qq])) pr[qq] = gload(p.npar + r[qq]);
+            if (is_rep(key[qq])) pr[qq] = parent(r[qq]);
     }
     const uint64_t k = sweep0 + (uint64_t)j;
     const uint32_t klo = (uint32_t)k, khi = (uint32_t)(k >> 32);
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
-    const bool pcc = (p.flags & RF_PCC) != 0;
+    const bool pcc = (p.flags & RF_PCC) != 0 && !wind;   // the extension rule's candidates read npar
     int nroots = 0;
 #pragma unroll
     for (int qq = 0; qq < MC::NPT; ++qq) {
@@ -1092,7 +1214,7 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_resolve(const PottsDev 
         } else if (minus_slot<DIM>(s)) {
             // its parent since the tile kernel (a representative), moved up
             // the same cluster by the unions' path splitting at most
-            p.nfinal[n] = key[qq] == KEY_NONE ? 0u : FINAL_ALIAS | (uint32_t)pr[qq];
+            p.nfinal[n] = key[qq] == KEY_NONE ? 0u : FINAL_ALIAS | (uint32_t)rep[qq];
         }
     }
     const int wb = threadIdx.x & ~31;
@@ -1276,10 +1398,22 @@ void launch_group(const PottsDev &p, int j, int nsweeps, uint64_t sweep0, DevObs
     else
         k_ptile<DIM, 0><<<tiles, G::NT, smem, st>>>(p, j, nsweeps, sweep0, obs);
     if (j >= nsweeps) return;
-    k_pmerge_union<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
-    k_pmerge_jump<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
-    k_pmerge_resolve<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, sweep0, obs);
-    if (pcc) {
+    const bool wind = (p.flags & RF_WIND) != 0;
+    if (wind) {
+        k_pwind_init<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
+        k_pmerge_union<DIM, true><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, obs);
+        k_pmerge_jump<DIM, true><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
+        k_pmerge_resolve<DIM, true><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, sweep0, obs);
+    } else {
+        k_pmerge_union<DIM, false><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, obs);
+        k_pmerge_jump<DIM, false><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
+        k_pmerge_resolve<DIM, false><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, sweep0, obs);
+    }
+    if (pcc && wind) {
+        // the flags are the windings the unions recorded: the feedback only
+        const int64_t F = DIM == 2 ? (int64_t)p.L : (int64_t)p.L * p.L;
+        k_ppcc_decide<<<PPCC_DECIDE, PT, 0, st>>>(p, F, j, sweep0, obs);
+    } else if (pcc) {
         const int64_t F = DIM == 2 ? (int64_t)p.L : (int64_t)p.L * p.L;
         const int64_t nc = (int64_t)p.ntiles * G::FT, nn = (int64_t)p.ntiles * G::S;
         k_ppcc_candidates<DIM><<<(unsigned)((nc + PT - 1) / PT), PT, 0, st>>>(p, F);

@@ -489,14 +489,16 @@ class Lattice:
 class PottsLattice:
     """A q-state Potts lattice on the d-dimensional torus (d = 2, 3), with
     open=True on the open d-dimensional box; pcc=True runs the PCC feedback
-    (the threshold starts at 2^31; T is then ignored)."""
+    (the threshold starts at 2^31; T is then ignored); wind=True reports the
+    topological rule (and feeds it back under PCC)."""
 
     def __init__(self, dim: int, L: int, q: int, *, J: float = 1.0, T: float = 1.0, seed: int = 1,
-                 csize: bool = False, open: bool = False, pcc: bool = False):
+                 csize: bool = False, open: bool = False, pcc: bool = False, wind: bool = False):
         self.dim, self.L, self.q = int(dim), int(L), int(q)
         self.N = self.L ** self.dim
         self.pcc = bool(pcc)
-        flags = (SW_FLAG_CSIZE if csize else 0) | (SW_FLAG_OPEN if open else 0)
+        flags = ((SW_FLAG_CSIZE if csize else 0) | (SW_FLAG_OPEN if open else 0)
+                 | (SW_FLAG_WIND if wind else 0))
         if pcc:
             self.h = pcc_create_potts(self.dim, self.L, self.q, seed, flags)
         else:
