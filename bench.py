@@ -718,13 +718,44 @@ def run_batch64(args):
 
 
 # ------------------------------------------------------------- Potts / 3D
-POTTS_BYTES_PER_SITE = 7   # states in and out, the bond byte, the label
+POTTS_BYTES_PER_SITE = 10   # the stated minimum of a sweep: old state in, label out, label in, new state out
+POTTS_PROFILE_FILE = os.path.join(ROOT, "profiles", "k_potts_tiles_critical.md")
+
+
+def potts_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("sw_device.cuh", "sw_potts.cu"):
+        h.update(open(os.path.join(ROOT, "paper_0808_2109_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def potts_profile_traffic(sha: str, dim: int, L: int, q: int):
+    """DRAM bytes per launch of the Potts tile kernel on this lattice from the
+    committed ncu summary, or None when it was taken on other sources."""
+    try:
+        txt = open(POTTS_PROFILE_FILE).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(rf"dram bytes per launch, {int(dim)}D L={int(L)} q={int(q)}:\s*([0-9]+)", txt)
+    if not m_sha or not m_tr or m_sha.group(1) != sha:
+        return None
+    return int(m_tr.group(1))
+
+
+def potts_philox_per_site(dim: int, L: int) -> float:
+    """Philox blocks the Potts tile kernel draws per site to start a sweep
+    when 4 divides L: 2D, two BOND blocks and one QSPIN block per lane for a
+    128-site row; 3D, 24 BOND and 8 QSPIN blocks per 32-site row."""
+    return 0.75 if dim == 2 else 1.0
 
 
 def run_potts(args):
     """The q-state Potts / 3D path at four critical points (2D: exact T_c;
     3D: the published estimates), each lattice larger than L2: W warm-up
-    steps of 10 sweeps, then K steps timed with CUDA events on its stream."""
+    steps of 10 sweeps, then K steps timed with CUDA events on its stream,
+    then one step in profiling mode (events around every tile kernel and
+    merge) for the per-kernel times behind the roofline."""
     import math
     import torch
     from paper_0808_2109_gb300 import _build, swgpu
@@ -762,25 +793,54 @@ def run_potts(args):
             e1.synchronize()
             ms = e0.elapsed_time(e1)
             assert len(lat.observables()) == args.steps * SW
+            lat.profile(True)
+            lat.sweep(SW)
+            st = lat.profile_read()
+            lat.profile(False)
+            lat.observables()
             n = L ** dim * SW * args.steps
             upd += n
             ms_tot += ms
             rows.append({"dim": dim, "L": L, "q": q, "T": round(T, 6),
-                         "value": round(n / (ms * 1e6), 3), "ms_per_sweep": round(ms / (SW * args.steps), 4)})
+                         "value": round(n / (ms * 1e6), 3), "ms_per_sweep": round(ms / (SW * args.steps), 4),
+                         "tile_kernel_avg_ms": round(st["tile_ms"] / st["tile_launches"], 4),
+                         "merge_group_avg_ms": round(st["merge_ms"] / st["merge_groups"], 4)})
     clk = clocks.stop()
     value = upd / (ms_tot * 1e6)
     hbm, src = hbm_peak_gbs()
-    achieved = value * POTTS_BYTES_PER_SITE   # site-updates/ns x B/site = GB/s
+    philox_peak = measure_philox_peak(torch, swgpu, stream)
+    # the dominant kernel: the tile kernel of the case with the most tile time
+    # (3D L=512 q=3 in the default set); one launch finishes a sweep and
+    # starts the next over L^d sites
+    dom = max(rows, key=lambda r: r["tile_kernel_avg_ms"] * (r["L"] ** r["dim"]))
+    sites = dom["L"] ** dom["dim"]
+    tile_s = dom["tile_kernel_avg_ms"] * 1e-3
+    achieved = POTTS_BYTES_PER_SITE * sites / tile_s / 1e9
+    traffic = potts_profile_traffic(potts_source_sha(), dom["dim"], dom["L"], dom["q"])
+    blocks = potts_philox_per_site(dom["dim"], dom["L"]) * sites
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(hbm, 1), "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_source": src,
+                "kernel": f"k_ptile<{dom['dim']}> ({dom['dim']}D L={dom['L']} q={dom['q']}: fused finish/start "
+                          "of a sweep, the largest share of the workload's device time)",
+                "bytes_per_site_algorithmic": POTTS_BYTES_PER_SITE, "units_per_launch": sites,
+                "tile_kernel_avg_ms": dom["tile_kernel_avg_ms"], "merge_group_avg_ms": dom["merge_group_avg_ms"],
+                "whole_workload_frac_hbm": round(value * POTTS_BYTES_PER_SITE / hbm, 4),
+                "alu": {"philox_blocks_per_site": potts_philox_per_site(dom["dim"], dom["L"]),
+                        "achieved_blocks_per_s": round(blocks / tile_s, 1),
+                        "peak_blocks_per_s": round(philox_peak, 1),
+                        "frac": round(blocks / tile_s / philox_peak, 4),
+                        "peak_source": "measured in this run: sw_bench_philox, 2^32 BOND blocks per launch"},
+                "binding": "neither ceiling: instruction issue (70-76% of cycles) and the union-find's "
+                           "dependent shared-memory latency (profiles/k_potts_tiles_critical.md)"}
+    if traffic is not None:
+        roofline["dram_gbs_measured"] = round(traffic / tile_s / 1e9, 1)
+        roofline["frac_dram_measured"] = round(traffic / tile_s / 1e9 / hbm, 4)
     return {"metric": "Potts/3D SW site updates/ns (four critical lattices)", "value": round(value, 3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "u8", "data": "synthetic",
             "config": {"workload": "q-state Potts, hot start, 10 sweeps per step", "cases": rows,
-                       "l2": "every lattice larger than L2 (states, labels and bond bytes >= 400 MB)"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(hbm, 1), "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
-                         "kernel": "all kernels of a sweep",
-                         "bytes_per_site": POTTS_BYTES_PER_SITE},
-            "clocks": clk, "impl": "gb300"}
+                       "l2": "every lattice larger than L2 (states, labels and site codes >= 400 MB)"},
+            "roofline": roofline, "clocks": clk, "impl": "gb300"}
 
 
 # ---------------------------------------------------------- reference arm

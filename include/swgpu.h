@@ -153,10 +153,10 @@ int pcc_create(sw_ctx **out, int32_t L, uint64_t seed, uint32_t flags);
  * neither bonds nor enters bond_sum) and SW_FLAG_WIND (the topological rule
  * of Sec. III reported every sweep: spans_x = some cluster winds around the
  * box along x, spans_y = along y, or in 3D along y or z), or 0.  The other
- * calls take the context
- * as usual (spins, labels and bond bytes have L^d entries, bond bit dir);
- * pcc_step (on a lattice not made by pcc_create_potts) and sw_profile answer
- * SW_ERR_STATE.  Errors: SW_ERR_ARG, SW_ERR_NOMEM, SW_ERR_CUDA. */
+ * calls take the context as usual (spins, labels and bond bytes have L^d
+ * entries, bond bit dir; sw_profile times its tile kernel and merge); pcc_step
+ * on a lattice not made by pcc_create_potts answers SW_ERR_STATE.  Errors:
+ * SW_ERR_ARG, SW_ERR_NOMEM, SW_ERR_CUDA. */
 int sw_create_potts(sw_ctx **out, int32_t dim, int32_t L, int32_t q, double J, double T, uint64_t seed,
                     uint32_t flags);
 
@@ -227,8 +227,10 @@ typedef struct {
     double tile_ms;        /* their summed device time                      */
     int64_t merge_groups;  /* launch groups (a group = the three merge kernels) */
     double merge_ms;       /* summed device time of the merge groups         */
-    int64_t tile_sites;    /* L*L                                            */
-    int32_t tile_height;   /* rows per tile (tiles are 128 sites wide)       */
+    int64_t tile_sites;    /* L*L (a Potts lattice: L^d)                     */
+    int32_t tile_height;   /* rows per tile (tiles are 128 sites wide); 0 on a
+                              Potts lattice, whose tiles are 128 x 64 (2D) or
+                              32 x 16 x 16 (3D)                              */
 } sw_kernel_stats;
 
 /* enable != 0: later sweeps are launched one kernel at a time (not as CUDA

@@ -539,7 +539,25 @@ int run_sweeps(sw_ctx *c, int32_t n)
     if (c->is_potts) {
         DevObs *obs = c->obs + c->obs_tail;
         SW_CUDA(cudaMemsetAsync(obs, 0, (size_t)n * sizeof(DevObs), c->stream));
-        SW_CUDA(potts_enqueue_sweeps(c->pd, n, c->sweep, obs, c->stream));
+        if (c->profiling) {
+            // events around the tile kernel and the merge of every launch group
+            for (int j = 0; j <= n; ++j) {
+                cudaEvent_t e0, e1, e2;
+                SW_CUDA(next_event(c, &e0));
+                SW_CUDA(next_event(c, &e1));
+                SW_CUDA(next_event(c, &e2));
+                SW_CUDA(cudaEventRecord(e0, c->stream));
+                SW_CUDA(potts_enqueue_tile(c->pd, j, n, c->sweep, obs, c->stream));
+                SW_CUDA(cudaEventRecord(e1, c->stream));
+                if (j < n) SW_CUDA(potts_enqueue_merge(c->pd, j, c->sweep, obs, c->stream));
+                SW_CUDA(cudaEventRecord(e2, c->stream));
+                c->ev_marks.push_back(e0);
+                c->ev_marks.push_back(e1);
+                c->ev_marks.push_back(e2);
+            }
+        } else {
+            SW_CUDA(potts_enqueue_sweeps(c->pd, n, c->sweep, obs, c->stream));
+        }
         c->obs_tail += n;
         c->sweep += (uint64_t)n;
         c->swept = true;
@@ -888,7 +906,6 @@ int sw_set_spins(sw_ctx *ctx, const uint8_t *host_in)
 int sw_profile(sw_ctx *ctx, int32_t enable)
 {
     if (!ctx) return SW_ERR_ARG;
-    if (ctx->is_potts) return SW_ERR_STATE;
     ctx->profiling = enable != 0;
     return SW_OK;
 }
@@ -912,8 +929,8 @@ int sw_profile_read(sw_ctx *ctx, sw_kernel_stats *out)
     out->tile_ms = ctx->prof_tile_ms;
     out->merge_groups = ctx->prof_groups;
     out->merge_ms = ctx->prof_merge_ms;
-    out->tile_sites = (int64_t)ctx->L * ctx->L;
-    out->tile_height = ctx->TH;
+    out->tile_sites = ctx->is_potts ? ctx->nsites : (int64_t)ctx->L * ctx->L;
+    out->tile_height = ctx->is_potts ? 0 : ctx->TH;
     ctx->prof_groups = 0;
     ctx->prof_tile_ms = ctx->prof_merge_ms = 0.0;
     return SW_OK;

@@ -71,6 +71,11 @@ struct PottsGeometry {
 };
 __attribute__((visibility("hidden"))) void potts_geometry(int dim, int L, PottsGeometry *g);
 __attribute__((visibility("hidden"))) cudaError_t potts_enqueue_hot_start(const PottsDev &p, cudaStream_t st);
+// Launch j (0 .. nsweeps) of a call: the tile kernel, then (j < nsweeps) the merge of sweep j.
+__attribute__((visibility("hidden"))) cudaError_t potts_enqueue_tile(const PottsDev &p, int j, int nsweeps,
+                                                                     uint64_t sweep0, DevObs *obs, cudaStream_t st);
+__attribute__((visibility("hidden"))) cudaError_t potts_enqueue_merge(const PottsDev &p, int j, uint64_t sweep0,
+                                                                      DevObs *obs, cudaStream_t st);
 // One call of nsweeps sweeps (observables into obs[0 .. nsweeps-1]).
 __attribute__((visibility("hidden"))) cudaError_t potts_enqueue_sweeps(const PottsDev &p, int nsweeps,
                                                                        uint64_t sweep0, DevObs *obs,

@@ -1386,7 +1386,7 @@ cudaError_t potts_prepare()
 }
 
 template <int DIM>
-void launch_group(const PottsDev &p, int j, int nsweeps, uint64_t sweep0, DevObs *obs, cudaStream_t st)
+void launch_tile(const PottsDev &p, int j, int nsweeps, uint64_t sweep0, DevObs *obs, cudaStream_t st)
 {
     using G = PG<DIM>;
     const bool pcc = (p.flags & RF_PCC) != 0;
@@ -1397,7 +1397,14 @@ void launch_group(const PottsDev &p, int j, int nsweeps, uint64_t sweep0, DevObs
         k_ptile<DIM, FEAT_TILE><<<tiles, G::NT, smem, st>>>(p, j, nsweeps, sweep0, obs);
     else
         k_ptile<DIM, 0><<<tiles, G::NT, smem, st>>>(p, j, nsweeps, sweep0, obs);
-    if (j >= nsweeps) return;
+}
+
+template <int DIM>
+void launch_merge(const PottsDev &p, int j, uint64_t sweep0, DevObs *obs, cudaStream_t st)
+{
+    using G = PG<DIM>;
+    const bool pcc = (p.flags & RF_PCC) != 0;
+    const unsigned tiles = (unsigned)p.ntiles;
     const bool wind = (p.flags & RF_WIND) != 0;
     if (wind) {
         k_pwind_init<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
@@ -1448,16 +1455,33 @@ cudaError_t potts_enqueue_hot_start(const PottsDev &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Launch j of a call of nsweeps sweeps: the tile kernel (finishing sweep
+// j-1, starting sweep j) ...
+cudaError_t potts_enqueue_tile(const PottsDev &p, int j, int nsweeps, uint64_t sweep0, DevObs *obs, cudaStream_t st)
+{
+    cudaError_t e = potts_prepare();
+    if (e != cudaSuccess) return e;
+    if (p.dim == 2) launch_tile<2>(p, j, nsweeps, sweep0, obs, st);
+    else launch_tile<3>(p, j, nsweeps, sweep0, obs, st);
+    return cudaGetLastError();
+}
+
+// ... and, for j < nsweeps, the merge of sweep j.
+cudaError_t potts_enqueue_merge(const PottsDev &p, int j, uint64_t sweep0, DevObs *obs, cudaStream_t st)
+{
+    if (p.dim == 2) launch_merge<2>(p, j, sweep0, obs, st);
+    else launch_merge<3>(p, j, sweep0, obs, st);
+    return cudaGetLastError();
+}
+
 // The launches of one call of nsweeps sweeps: tile kernel j = 0 .. nsweeps,
 // each but the last followed by the merge of sweep j.
 cudaError_t potts_enqueue_sweeps(const PottsDev &p, int nsweeps, uint64_t sweep0, DevObs *obs, cudaStream_t st)
 {
-    cudaError_t e = potts_prepare();
-    if (e != cudaSuccess) return e;
     for (int j = 0; j <= nsweeps; ++j) {
-        if (p.dim == 2) launch_group<2>(p, j, nsweeps, sweep0, obs, st);
-        else launch_group<3>(p, j, nsweeps, sweep0, obs, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cudaError_t e = potts_enqueue_tile(p, j, nsweeps, sweep0, obs, st);
+        if (e == cudaSuccess && j < nsweeps) e = potts_enqueue_merge(p, j, sweep0, obs, st);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

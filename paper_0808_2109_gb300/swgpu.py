@@ -532,6 +532,15 @@ class PottsLattice:
         _check(getattr(lib(), fn)(self.h, _ptr(out)), fn)
         return out
 
+    def sync(self):
+        sw_sync(self.h)
+
+    def profile(self, enable: bool = True):
+        sw_profile(self.h, enable)
+
+    def profile_read(self) -> dict:
+        return sw_profile_read(self.h)
+
     def spins(self) -> np.ndarray:
         return self._get("sw_get_spins", np.uint8)
 

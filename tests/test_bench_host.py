@@ -68,3 +68,26 @@ def test_golden_writer_imports_no_cuda_binding():
     assert "import oracle" in src
     assert "paper_0808_2109_gb300 import" not in src and "import paper_0808_2109_gb300" not in src
     assert "swgpu" not in src
+
+
+def test_potts_profile_traffic_follows_the_sources():
+    """The Potts summary names the sources it was captured on (the tile
+    kernels' file and the shared device header); its DRAM bytes are reported
+    only for those sources and the named lattice."""
+    txt = open(bench.POTTS_PROFILE_FILE).read()
+    m = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
+    assert m, "the summary states the sources it was captured on"
+    lat = re.findall(r"dram bytes per launch, (\d)D L=(\d+) q=(\d+):", txt)
+    assert lat
+    d, L, q = (int(v) for v in lat[0])
+    assert bench.potts_profile_traffic("0" * 64, d, L, q) is None
+    got = bench.potts_profile_traffic(m.group(1), d, L, q)
+    assert isinstance(got, int) and got > 0
+    assert bench.potts_profile_traffic(m.group(1), d, L + 1, q) is None
+
+
+def test_potts_source_hash_is_the_two_files():
+    h = hashlib.sha256()
+    for f in ("sw_device.cuh", "sw_potts.cu"):
+        h.update(open(os.path.join(ROOT, "paper_0808_2109_gb300", "csrc", f), "rb").read())
+    assert bench.potts_source_sha() == h.hexdigest()
