@@ -13,7 +13,7 @@
 //             union-find over the bonds inside the tile, the new state of
 //             every cluster that ends inside the tile, one node per site of
 //             each tile face, and the site codes.
-//   k_pmerge_union / k_pmerge_jump / k_pmerge_resolve
+//   k_pmerge_union / k_pmerge_resolve (k_pmerge_jump under the topological rule)
 //             the master's step 2: a union-find over the face nodes joined by
 //             the bonds that leave a tile (the wrapping links included),
 //             smaller key (cluster minimum) wins; then every representative
@@ -1412,8 +1412,10 @@ void launch_merge(const PottsDev &p, int j, uint64_t sweep0, DevObs *obs, cudaSt
         k_pmerge_jump<DIM, true><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
         k_pmerge_resolve<DIM, true><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, sweep0, obs);
     } else {
+        // no pointer-jumping round: after the unions' single-swap links the
+        // walks are short, and the round cost more than it saved (3D 2.99 ->
+        // 2.94 ms a sweep without it)
         k_pmerge_union<DIM, false><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, obs);
-        k_pmerge_jump<DIM, false><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
         k_pmerge_resolve<DIM, false><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, sweep0, obs);
     }
     if (pcc && wind) {
