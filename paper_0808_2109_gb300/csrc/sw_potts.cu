@@ -13,7 +13,8 @@
 //             union-find over the bonds inside the tile, the new state of
 //             every cluster that ends inside the tile, one node per site of
 //             each tile face, and the site codes.
-//   k_pmerge_union / k_pmerge_resolve (k_pmerge_jump under the topological rule)
+//   k_pmerge_union / k_pmerge_resolve (with k_pwind_init / k_pwind_jump under
+//             the topological rule)
 //             the master's step 2: a union-find over the face nodes joined by
 //             the bonds that leave a tile (the wrapping links included),
 //             smaller key (cluster minimum) wins; then every representative
@@ -1112,39 +1113,24 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pwind_init(const PottsDev p)
     }
 }
 
-// One round of pointer jumping on the representatives' parents.
-template <int DIM, bool W>
-__global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_jump(const PottsDev p)
+// Topological rule: one round of pointer jumping on the representatives'
+// links (the wind unions hang roots under roots, so the walks grow longer
+// than on the plain path, which has no such round).
+template <int DIM>
+__global__ void __launch_bounds__(PMC<DIM>::MT) k_pwind_jump(const PottsDev p)
 {
     using MC = PMC<DIM>;
     const int base = blockIdx.x * PG<DIM>::S;
-    if (W && (p.flags & RF_WIND)) {
-        WLink *wl = reinterpret_cast<WLink *>(p.wlink);
-#pragma unroll
-        for (int qq = 0; qq < MC::NPT; ++qq) {
-            const int n = base + threadIdx.x + qq * MC::MT;
-            const uint32_t key = (uint32_t)p.nkey[n];
-            if (key == KEY_NONE || !(key & KEY_REP)) continue;
-            const WLink w = wl_read(wl + n);
-            if (w.parent == n) continue;
-            const WLink g = wl_read(wl + w.parent);
-            if (g.parent != w.parent) atomicCAS(wl + n, w, WLink{g.parent, w.dx + g.dx, w.dy + g.dy, w.dz + g.dz});
-        }
-        return;
-    }
-    int pr[MC::NPT];
+    WLink *wl = reinterpret_cast<WLink *>(p.wlink);
 #pragma unroll
     for (int qq = 0; qq < MC::NPT; ++qq) {
         const int n = base + threadIdx.x + qq * MC::MT;
         const uint32_t key = (uint32_t)p.nkey[n];
-        const int pq = gload(p.npar + n);
-        pr[qq] = (key != KEY_NONE && (key & KEY_REP)) ? pq : -1;
-    }
-#pragma unroll
-    for (int qq = 0; qq < MC::NPT; ++qq) {
-        if (pr[qq] < 0) continue;
-        const int gp = gload(p.npar + pr[qq]);
-        if (gp != pr[qq]) *(volatile int32_t *)(p.npar + base + threadIdx.x + qq * MC::MT) = gp;
+        if (key == KEY_NONE || !(key & KEY_REP)) continue;
+        const WLink w = wl_read(wl + n);
+        if (w.parent == n) continue;
+        const WLink g = wl_read(wl + w.parent);
+        if (g.parent != w.parent) atomicCAS(wl + n, w, WLink{g.parent, w.dx + g.dx, w.dy + g.dy, w.dz + g.dz});
     }
 }
 
@@ -1409,7 +1395,7 @@ void launch_merge(const PottsDev &p, int j, uint64_t sweep0, DevObs *obs, cudaSt
     if (wind) {
         k_pwind_init<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
         k_pmerge_union<DIM, true><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, obs);
-        k_pmerge_jump<DIM, true><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
+        k_pwind_jump<DIM><<<tiles, PMC<DIM>::MT, 0, st>>>(p);
         k_pmerge_resolve<DIM, true><<<tiles, PMC<DIM>::MT, 0, st>>>(p, j, sweep0, obs);
     } else {
         // no pointer-jumping round: after the unions' single-swap links the
