@@ -351,10 +351,10 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 5)
             uint32_t *fs4 = reinterpret_cast<uint32_t *>(sm.f.s.fst);
             for (int w = tid; w < S / 4; w += NT) fs4[w] = ns4[w];
         }
-        // the + halo: new states of the neighbours' "-" face sites, through
-        // their finals (a representative's own, or an alias of one)
+        // the + halo: new states of the neighbours' "-" face sites (the merge
+        // gives every "-" face slot its cluster's state)
         constexpr int HPT = (G::FT + NT - 1) / NT;
-        uint32_t hf[HPT];
+        uint32_t hs[HPT];
         int hnode[HPT], hpos[HPT];
 #pragma unroll
         for (int qq = 0; qq < HPT; ++qq) {
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 5)
                     hpos[qq] = (td * G::HY + y) * G::RS + x;
                 }
             }
-            hf[qq] = hpos[qq] >= 0 ? p.nfinal[hnode[qq]] : 0u;
+            hs[qq] = hpos[qq] >= 0 ? p.nstate[hnode[qq]] : 0u;
         }
         __syncthreads();
         uint8_t *st = &sm.f.s.st[0][0][0];
@@ -424,9 +424,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 5)
         }
 #pragma unroll
         for (int qq = 0; qq < HPT; ++qq) {
-            if (hpos[qq] < 0) continue;
-            const uint32_t f = hf[qq];
-            st[hpos[qq]] = p.nstate[(f & FINAL_ALIAS) ? (size_t)(f & ~FINAL_ALIAS) : (size_t)hnode[qq]];
+            if (hpos[qq] >= 0) st[hpos[qq]] = (uint8_t)hs[qq];
         }
         __syncthreads();
         // observables of sweep j-1: every link that exists, every site
@@ -1057,14 +1055,16 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_union(const PottsDev p,
             if (!live[qq]) continue;
             const bool ra = pa[qq] == xa[qq], rb = pb[qq] == xb[qq];
             if (!ra || !rb) {
+                // path splitting rewrites representatives only: a slot that
+                // is not one keeps its own representative as its parent
                 if (!ra) {
                     if (sa[qq] >= 0) *(volatile int32_t *)(p.npar + sa[qq]) = pa[qq];
-                    sa[qq] = xa[qq];
+                    sa[qq] = ((uint32_t)ka[qq] & KEY_REP) ? xa[qq] : -1;
                     xa[qq] = pa[qq];
                 }
                 if (!rb) {
                     if (sb[qq] >= 0) *(volatile int32_t *)(p.npar + sb[qq]) = pb[qq];
-                    sb[qq] = xb[qq];
+                    sb[qq] = ((uint32_t)kb[qq] & KEY_REP) ? xb[qq] : -1;
                     xb[qq] = pb[qq];
                 }
                 more = true;
@@ -1137,9 +1137,9 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pwind_jump(const PottsDev p)
 // Every representative walks to its root r (key: the cluster's minimum site)
 // and stores the cluster's root and new state (Sec. I step 3); under PCC it
 // also points every node of its walk at r.  A "-" face slot that is not a
-// representative stores FINAL_ALIAS | its parent (a representative of the
-// same cluster) for the neighbour's halo.  Counts the clusters that touch a
-// tile face (one root node each).
+// representative then takes its representative's state (its parent, in the
+// same tile: the unions rewrite representatives only) for the neighbour's
+// halo.  Counts the clusters that touch a tile face (one root node each).
 template <int DIM, bool W>
 __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_resolve(const PottsDev p, int j, uint64_t sweep0,
                                                                  DevObs *obs)
@@ -1162,6 +1162,7 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_resolve(const PottsDev 
         pr[qq] = wind ? parent(r[qq]) : rep[qq];
     }
     auto is_rep = [](uint32_t kk) { return kk != KEY_NONE && (kk & KEY_REP); };
+    __shared__ uint8_t rst[PG<DIM>::S];   // the new state of each representative slot
     for (;;) {
         bool more = false;
 #pragma unroll
@@ -1195,13 +1196,20 @@ __global__ void __launch_bounds__(PMC<DIM>::MT) k_pmerge_resolve(const PottsDev 
             nroots += r[qq] == n;
             if (p.flags & RF_CSIZE) atomicAdd(p.csize + r[qq], p.psize[n]);
             const uint32_t rkey = (uint32_t)p.nkey[r[qq]] & KEY_MASK;
-            p.nstate[n] = cluster_state(rkey, klo, khi, k0, k1, p.q);
+            const uint8_t st = cluster_state(rkey, klo, khi, k0, k1, p.q);
+            p.nstate[n] = st;
+            rst[s] = st;
             p.nfinal[n] = rkey;
-        } else if (minus_slot<DIM>(s)) {
-            // its parent since the tile kernel (a representative), moved up
-            // the same cluster by the unions' path splitting at most
-            p.nfinal[n] = key[qq] == KEY_NONE ? 0u : FINAL_ALIAS | (uint32_t)rep[qq];
         }
+    }
+    __syncthreads();
+    // a "-" face slot that is not a representative (whose parent is still its
+    // own representative in this tile) takes its cluster's new state too: the
+    // neighbour's halo reads it with one load
+#pragma unroll
+    for (int qq = 0; qq < MC::NPT; ++qq) {
+        const int s = threadIdx.x + qq * MC::MT;
+        if (!is_rep(key[qq]) && key[qq] != KEY_NONE && minus_slot<DIM>(s)) p.nstate[base + s] = rst[rep[qq] - base];
     }
     const int wb = threadIdx.x & ~31;
     const unsigned wm = MC::MT - wb >= 32 ? 0xFFFFFFFFu : (1u << (MC::MT - wb)) - 1u;
