@@ -185,16 +185,10 @@ __device__ __forceinline__ uint32_t valid_mask(int c, int tw)
     return n >= 32 ? 0xFFFFFFFFu : (n <= 0 ? 0u : ((1u << n) - 1u));
 }
 
-// Resolved final (root | spin << 30) of an edge slot.  A representative
-// holds its own; any other top or left slot (the ones a neighbour reads for
-// its halo) holds FINAL_ALIAS | a representative of the same cluster.  Only nfinal is read: the tile kernel that reads a
+// Resolved final (root | spin << 30) of an edge slot: a representative holds
+// its cluster's, and so does every top or left slot (the ones a neighbour
+// reads for its halo).  Only nfinal is read: the tile kernel that reads a
 // neighbour's finals rewrites that neighbour's npar and nkey concurrently.
-constexpr uint32_t FINAL_ALIAS = 0x80000000u;
-__device__ __forceinline__ uint32_t node_final(const Replica &R, size_t node)
-{
-    const uint32_t f = R.nfinal[node];
-    return (f & FINAL_ALIAS) ? R.nfinal[f & ~FINAL_ALIAS] : f;
-}
 
 // ------------------------------------------------------------ tile geometry
 struct Tile {
@@ -620,8 +614,7 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         }
         for (int s = tid; s < S; s += NT) sm.u.finfo[s] = R.nfinal[(size_t)t.lt * S + s];
         // the halos' finals (new spins of the top row of the tile below and of
-        // the left column of the tile to the right), issued with the codes;
-        // an alias is followed once the loads are back
+        // the left column of the tile to the right), issued with the codes
         uint32_t fb = 0u, fr = 0u;
         if (warp < TWW && 32 * warp + lane < t.tw) fb = R.nfinal[(size_t)t.g_down * S + SL::TOP + 32 * warp + lane];
         if (tid < t.th) fr = R.nfinal[(size_t)t.g_right * S + SL::LEFT + tid];
@@ -672,11 +665,9 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         }
         // bottom halo row: new spins of the top row of the tile below
         if (warp < TWW) {
-            if (fb & FINAL_ALIAS) fb = R.nfinal[fb & ~FINAL_ALIAS];
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, (fb & FINAL_SPIN) != 0u);
             if (lane == 0) sm.sp[t.th][warp] = word;
         }
-        if (fr & FINAL_ALIAS) fr = R.nfinal[fr & ~FINAL_ALIAS];
         __syncthreads();
         // right halo column: new spins of the left column of the tile to the right
         if (fr & FINAL_SPIN) set_halo(tid);
@@ -1298,14 +1289,16 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT, 64 / ((MergeCfg<TH>::MT + 31
             if (!live[q]) continue;
             const bool ra = pa[q] == xa[q], rb = pb[q] == xb[q];
             if (!ra || !rb) {
+                // path splitting rewrites representatives only: a slot that
+                // is not one keeps its own representative as its parent
                 if (!ra) {
                     if (sa[q] >= 0) *(volatile int32_t *)(R.npar + sa[q]) = pa[q];
-                    sa[q] = xa[q];
+                    sa[q] = ((uint32_t)ka[q] & KEY_REP) ? xa[q] : -1;
                     xa[q] = pa[q];
                 }
                 if (!rb) {
                     if (sb[q] >= 0) *(volatile int32_t *)(R.npar + sb[q]) = pb[q];
-                    sb[q] = xb[q];
+                    sb[q] = ((uint32_t)kb[q] & KEY_REP) ? xb[q] : -1;
                     xb[q] = pb[q];
                 }
                 more = true;
@@ -1364,7 +1357,7 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_wind_init(const SweepArgs 
 // One round is best since the unions split their paths (L=16384, 64-row
 // tiles, merge per sweep with 0 / 1 / 2 / 3 rounds: 0.31 / 0.28 / 0.29 / 0.34
 // ms at T_c, 0.45 / 0.50 / 0.59 ms for 1 / 2 / 3 rounds at T = 2.0).
-// Other slots only alias their piece's representative.
+// Other slots keep their piece's representative as parent.
 constexpr int MERGE_JUMP_ROUNDS = 1;
 template <int TH, bool W>
 __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs a)
@@ -1416,9 +1409,9 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs
 // its root r (key: the cluster's minimum site index), writes r over every
 // node of the walk (full path compression: no union happens any more, so
 // every node on it has root r) and stores the cluster's root and new spin,
-// bit (root mod 128) of Philox(root/128, k, SPIN) (Sec. I step 3).  Any
-// other slot stores FINAL_ALIAS | its representative.  Counts the clusters
-// that touch a tile border (one root node each).
+// bit (root mod 128) of Philox(root/128, k, SPIN) (Sec. I step 3); a top or
+// left slot that is not a representative then copies its representative's.
+// Counts the clusters that touch a tile border (one root node each).
 template <int TH, bool W>
 __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepArgs a)
 {
@@ -1438,7 +1431,7 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
     for (int q = 0; q < MC::NPT; ++q) {
         r[q] = base + threadIdx.x + q * MC::MT;
         // a representative walks its forest; any other slot keeps its parent
-        // from the tile kernel (its representative) for the alias below
+        // from the tile kernel (its representative) for the copy below
         p[q] = (wind && (key[q] & KEY_REP)) ? parent(r[q]) : gload(R.npar + r[q]);
     }
     // the walks of the thread's representatives advance in lock step
@@ -1456,6 +1449,7 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
         for (int q = 0; q < MC::NPT; ++q)
             if (key[q] & KEY_REP) p[q] = parent(r[q]);
     }
+    __shared__ uint32_t rfin[MC::S];   // the finals of the representatives
     uint32_t rkey[MC::NPT];
 #pragma unroll
     for (int q = 0; q < MC::NPT; ++q) rkey[q] = (key[q] & KEY_REP) ? (uint32_t)R.nkey[r[q]] & KEY_MASK : 0u;
@@ -1496,15 +1490,20 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_resolve(const SweepA
             const int bit = rkey[q] & 127;
             const uint32_t spin = (u4_word(u, bit >> 5) >> (bit & 31)) & 1u;
             R.nfinal[n] = rkey[q] | (spin ? FINAL_SPIN : 0u);
-        } else if (threadIdx.x + q * MC::MT < Slots<TH>::BOTTOM ||
-                   (threadIdx.x + q * MC::MT >= Slots<TH>::LEFT && threadIdx.x + q * MC::MT < Slots<TH>::RIGHT)) {
-            // a top or left slot, whose final a neighbour's tile kernel reads
-            // for its halo: an alias of a representative (its parent since
-            // the tile kernel, moved up the same cluster by path halving at
-            // most); past the tile's sites, 0.  No kernel reads the final of
-            // any other slot that is not a representative.
-            R.nfinal[n] = key[q] == KEY_NONE ? 0u : FINAL_ALIAS | (uint32_t)p[q];
+            rfin[threadIdx.x + q * MC::MT] = R.nfinal[n];
         }
+    }
+    __syncthreads();
+    // a top or left slot that is not a representative, whose final a
+    // neighbour's tile kernel reads for its halo: its representative's (its
+    // parent since the tile kernel, in this tile: the unions rewrite
+    // representatives only); past the tile's sites, 0.  No kernel reads the
+    // final of any other slot that is not a representative.
+#pragma unroll
+    for (int q = 0; q < MC::NPT; ++q) {
+        const int s = threadIdx.x + q * MC::MT;
+        if (!(key[q] & KEY_REP) && (s < Slots<TH>::BOTTOM || (s >= Slots<TH>::LEFT && s < Slots<TH>::RIGHT)))
+            R.nfinal[base + s] = key[q] == KEY_NONE ? 0u : rfin[p[q] - base];
     }
     // every thread of the block gets here; the last warp may be partial
     const int wb = threadIdx.x & ~31;

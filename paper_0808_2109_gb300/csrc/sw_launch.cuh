@@ -48,7 +48,7 @@ struct PottsDev {
     uint16_t *code;                    // ntiles * sites-per-tile
     uint32_t *cross;                   // ntiles * cross words
     int32_t *npar, *nkey;              // ntiles * slots
-    uint32_t *nfinal;                  // ntiles * slots: root, or FINAL_ALIAS | a representative
+    uint32_t *nfinal;                  // ntiles * slots: a representative's cluster root
     uint8_t *nstate;                   // ntiles * slots: a representative's new state
     int32_t *psize, *csize;            // ntiles * slots (RF_CSIZE only)
     int4 *wlink;                       // RF_WIND: ntiles * slots node links {parent, dx, dy, dz}
