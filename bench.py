@@ -299,10 +299,15 @@ def cpu_baseline_batch(pool, jobs, sample_replicas: int = 64, sweeps: int = 20):
 
 def start_oracle_pool():
     """A spawn pool of one process per host core, for the all-cores oracle
-    baseline (started before any GPU call)."""
+    baseline (started before any GPU call).  Its workers are waited for here,
+    so that their start-up does not load the host cores while the end-to-end
+    step (host copies and the calls that issue them) is timed."""
     import multiprocessing as mp
     try:
-        return mp.get_context("spawn").Pool(os.cpu_count() or 1)
+        n = os.cpu_count() or 1
+        pool = mp.get_context("spawn").Pool(n)
+        pool.map(time.sleep, [0.05] * (4 * n), chunksize=1)   # every worker up and idle
+        return pool
     except OSError:
         return None
 
@@ -379,16 +384,27 @@ def run_gb300(args):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    part = [0.0, 0.0, 0.0]   # host wall time: upload + state check, sweeps + observables, download
     for _ in range(e2e_steps):
-        lat.set_spins(h_in)                  # host -> device: this step's input lattice
+        ta = time.perf_counter()
+        lat.set_spins(h_in)                  # host -> device: this step's input lattice (checked)
+        tb = time.perf_counter()
         lat.sweep(w.sweeps)
         o = lat.observables()                # device -> host: per-sweep observables
+        tc = time.perf_counter()
         swgpu.sw_get_spins(lat.h, w.L, h_out)  # device -> host: the resulting lattice
+        td = time.perf_counter()
+        part[0] += tb - ta
+        part[1] += tc - tb
+        part[2] += td - tc
         h_in, h_out = h_out, h_in
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": world * N * w.sweeps * e2e_steps / (e2e_s * 1e9), "unit": UNIT,
            "h2d_bytes_per_step": N, "d2h_bytes_per_step": N + w.sweeps * swgpu.OBS_DTYPE.itemsize,
-           "steps": e2e_steps}
+           "steps": e2e_steps,
+           "ms_per_step": {"upload_and_check": round(1e3 * part[0] / e2e_steps, 3),
+                           "sweeps_and_observables": round(1e3 * part[1] / e2e_steps, 3),
+                           "download": round(1e3 * part[2] / e2e_steps, 3)}}
     del o
     lat.close()
 
