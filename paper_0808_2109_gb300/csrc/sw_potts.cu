@@ -268,6 +268,7 @@ struct PSmem {
         struct {
             uint8_t fst[G::S];              // finish half: new states of the tile's pieces, by slot
             uint8_t st[G::HZ][G::HY][G::RS];   // states; row TY, layer TZ and column tw: + halo
+            alignas(16) uint16_t code[G::NS];  // finish half: the tile's site codes
         } s;
     } f;
     uint8_t qs[G::NR][G::TX];               // each site's state drawn from the QSPIN stream
@@ -277,6 +278,21 @@ struct PSmem {
     long long red[G::NW][4];                // the reduction that ends each half
     uint32_t pm[G::S][G::PMW];              // PCC: coordinates each border piece occupies
 };
+
+static_assert(sizeof(PSmem<2>::f) == sizeof(int) * PG<2>::NR * PG<2>::PW, "the finish half fits the forest's space");
+static_assert(sizeof(PSmem<3>::f) == sizeof(int) * PG<3>::NR * PG<3>::PW, "the finish half fits the forest's space");
+
+// 16 bytes from global to shared memory without passing through registers
+// (completed by cp_async_wait_all before a barrier)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 template <int DIM>
 constexpr size_t ptile_smem(bool pcc)
@@ -338,13 +354,15 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 5)
     if (fin) {
         // ---- finish sweep j-1: every site's new state
         const bool last = j == nsweeps;
-        uint4 cv[G::NQ];
+        // the tile's codes, 8 sites per 16-byte asynchronous copy straight
+        // into shared memory (the forest's space, free until the labelling)
         const uint4 *code4 = reinterpret_cast<const uint4 *>(code);
+        uint4 *scode4 = reinterpret_cast<uint4 *>(sm.f.s.code);
 #pragma unroll
         for (int qq = 0; qq < G::NQ; ++qq) {
             int x, y, z;
             const int idx = tid + qq * NT;
-            cv[qq] = group(idx, x, y, z) ? code4[idx] : make_uint4(0u, 0u, 0u, 0u);
+            if (group(idx, x, y, z)) cp_async16(scode4 + idx, code4 + idx);
         }
         {
             const uint32_t *ns4 = reinterpret_cast<const uint32_t *>(p.nstate + nbase);
@@ -382,6 +400,7 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 5)
             }
             hs[qq] = hpos[qq] >= 0 ? p.nstate[hnode[qq]] : 0u;
         }
+        cp_async_wait_all();
         __syncthreads();
         uint8_t *st = &sm.f.s.st[0][0][0];
 #pragma unroll
@@ -389,7 +408,8 @@ __global__ void __launch_bounds__(PG<DIM>::NT, 5)
             int x, y, z;
             const int idx = tid + qq * NT;
             if (!group(idx, x, y, z)) continue;
-            const uint32_t wv[4] = {cv[qq].x, cv[qq].y, cv[qq].z, cv[qq].w};
+            const uint4 cq = scode4[idx];
+            const uint32_t wv[4] = {cq.x, cq.y, cq.z, cq.w};
             uint32_t lo = 0u, hi = 0u;
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
