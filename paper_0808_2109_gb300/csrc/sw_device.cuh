@@ -515,10 +515,23 @@ __device__ __forceinline__ void block_sum_atomic(long long (&v)[K], unsigned lon
     }
 }
 
+// 16 bytes from global to shared memory without passing through registers
+// (completed by cp_async_wait_all before a barrier)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // ------------------------------------------------------------ shared layout
 template <int TH>
 struct TileSmem {
-    int par[TH * PW];               // union-find forest over run heads (padded rows)
+    int par[TH * PW];               // union-find forest over run heads (padded rows); in the
+                                    // finish half, the tile's site codes (TH * TW * 2 bytes)
     uint32_t sp[TH + 1][TWW];       // spins as bits, row TH = halo row; in a tile narrower
                                     // than TW, bit tw of a row = the halo column
     uint32_t spx[TH / 32];          // halo column of a full-width tile: bit y = row y
@@ -604,13 +617,14 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         // ---- finish sweep k-1: resolve every site's cluster and flip it
         const int jf = j - 1;
         const bool last = j == R.nsweeps;
-        // the tile's codes, 8 sites per 16-byte load, all issued up front
-        uint4 cv[NQ];
+        // the tile's codes, 8 sites per 16-byte asynchronous copy straight
+        // into shared memory (the forest's space, unused until the labelling)
         const uint4 *code4 = reinterpret_cast<const uint4 *>(code);
+        uint4 *scode4 = reinterpret_cast<uint4 *>(sm.par);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int idx = tid + q * NT;
-            cv[q] = ((idx * 8) / TW < t.th) ? code4[idx] : make_uint4(0u, 0u, 0u, 0u);
+            if ((idx * 8) / TW < t.th) cp_async16(scode4 + idx, code4 + idx);
         }
         for (int s = tid; s < S; s += NT) sm.u.finfo[s] = R.nfinal[(size_t)t.lt * S + s];
         // the halos' finals (new spins of the top row of the tile below and of
@@ -619,13 +633,15 @@ __global__ void __launch_bounds__(TileCfg<TH>::NT, TileCfg<TH>::MINB) k_tile(con
         if (warp < TWW && 32 * warp + lane < t.tw) fb = R.nfinal[(size_t)t.g_down * S + SL::TOP + 32 * warp + lane];
         if (tid < t.th) fr = R.nfinal[(size_t)t.g_right * S + SL::LEFT + tid];
         for (int w = tid; w < TH / 32; w += NT) sm.spx[w] = 0u;
+        cp_async_wait_all();
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int idx = tid + q * NT;
             const int y = (idx * 8) / TW, xb = (idx * 8) % TW;
             if (y >= t.th) continue;
-            const uint32_t wv[4] = {cv[q].x, cv[q].y, cv[q].z, cv[q].w};
+            const uint4 cq = scode4[idx];
+            const uint32_t wv[4] = {cq.x, cq.y, cq.z, cq.w};
             uint32_t bits = 0;
 #pragma unroll
             for (int e = 0; e < 8; ++e) {

@@ -282,18 +282,6 @@ struct PSmem {
 static_assert(sizeof(PSmem<2>::f) == sizeof(int) * PG<2>::NR * PG<2>::PW, "the finish half fits the forest's space");
 static_assert(sizeof(PSmem<3>::f) == sizeof(int) * PG<3>::NR * PG<3>::PW, "the finish half fits the forest's space");
 
-// 16 bytes from global to shared memory without passing through registers
-// (completed by cp_async_wait_all before a barrier)
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
 template <int DIM>
 constexpr size_t ptile_smem(bool pcc)
 {
