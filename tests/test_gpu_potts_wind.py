@@ -75,3 +75,20 @@ def test_potts_wind_checkpoint_resumes(sw, orc):
     with sw.PottsLattice(dim, L, q, seed=5, pcc=True) as c:   # another kind of lattice refuses it
         with pytest.raises(sw.SwError):
             c.load(blob)
+
+
+@pytest.mark.parametrize("dim,L,pcc,open,wind", [(2, 130, True, False, False), (3, 40, True, False, False),
+                                                 (2, 130, True, True, False), (3, 36, True, True, False),
+                                                 (2, 130, False, True, True), (3, 36, True, True, True)])
+def test_potts_feature_combinations(sw, orc, dim, L, pcc, open, wind):
+    """Cluster sizes with PCC, open boundaries and the topological rule in
+    combination, on lattices of several tiles: every field bit for bit."""
+    T = 1.0 if dim == 2 else 1.8
+    ref = orc.PottsChain(dim, L, 3, 1.0, T, 9, csize=True, pcc=pcc, open=open, wind=wind)
+    with sw.PottsLattice(dim, L, 3, T=T, seed=9, csize=True, pcc=pcc, open=open, wind=wind) as lat:
+        for n in (7, 5):
+            lat.sweep(n)
+            assert_obs_equal(lat.observables(), ref.run(n), FIELDS)
+            np.testing.assert_array_equal(lat.spins(), ref.spin)
+            np.testing.assert_array_equal(lat.labels(), ref.label)
+        assert lat.state()["threshold"] == ref.threshold
