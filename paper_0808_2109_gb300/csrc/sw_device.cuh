@@ -167,17 +167,6 @@ __device__ __forceinline__ bool below(uint32_t u, uint32_t t_minus_1)
     return u <= t_minus_1;
 }
 
-// Spread the low 16 bits of v to the even bit positions.
-__device__ __forceinline__ uint32_t spread16(uint32_t v)
-{
-    v &= 0xFFFFu;
-    v = (v | (v << 8)) & 0x00FF00FFu;
-    v = (v | (v << 4)) & 0x0F0F0F0Fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
-    return v;
-}
-
 // Mask of the valid sites (x < tw) in word c of a tile row.
 __device__ __forceinline__ uint32_t valid_mask(int c, int tw)
 {
