@@ -11,7 +11,7 @@
 //            shared-memory union-find over the bonds inside the tile, the new
 //            spin of every cluster that does not touch the tile border, and
 //            one "node" per border site (the master's "new lattice").
-//   k_merge_union / k_merge_compress / k_merge_final
+//   k_merge_union / k_merge_jump / k_merge_resolve
 //            the master's step 2 (Sec. II.A): union-find over the border
 //            nodes joined by the bonds that cross tile edges, including the
 //            periodic wrap; the root of a global cluster is the minimum site
@@ -1355,7 +1355,7 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_wind_init(const SweepArgs 
 
 // Pointer jumping over the representatives (every parent replaced by its
 // grandparent, MERGE_JUMP_ROUNDS times) between the unions and the
-// compression: it cuts the depth of the chains that unions across many tiles
+// resolve: it cuts the depth of the chains that unions across many tiles
 // leave behind.  The rounds run in one launch, so a round may read a parent
 // that its own thread has already moved up; every value read is still an
 // ancestor, and the resolve kernel walks to the root whatever depth is left.
@@ -1411,9 +1411,9 @@ __global__ void __launch_bounds__(MergeCfg<TH>::MT) k_merge_jump(const SweepArgs
 }
 
 // Resolve every node once the unions are done: each representative walks to
-// its root r (key: the cluster's minimum site index), writes r over every
-// node of the walk (full path compression: no union happens any more, so
-// every node on it has root r) and stores the cluster's root and new spin,
+// its root r (key: the cluster's minimum site index), for PCC lattices writes
+// r over every node of the walk (full path compression: no union happens any
+// more, so every node on it has root r) and stores the cluster's root and new spin,
 // bit (root mod 128) of Philox(root/128, k, SPIN) (Sec. I step 3); a top or
 // left slot that is not a representative then copies its representative's.
 // Counts the clusters that touch a tile border (one root node each).

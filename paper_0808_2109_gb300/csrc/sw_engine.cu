@@ -57,9 +57,9 @@ void launch_tile(const SweepArgs &a, bool pcc, int feat, cudaStream_t st)
         k_tile<TH, 0><<<a.n_tiles, TileCfg<TH>::NT, smem, st>>>(a);
 }
 
-// The merge of launch group j: unions across tile edges, pointer jumping,
-// compression; for PCC lattices the span test and the feedback; then every
-// node's resolved root and new spin.
+// The merge of launch group j: unions across tile edges, one round of
+// pointer jumping, every node's resolved root and new spin; then for PCC
+// lattices the span test and the feedback.
 template <int TH, bool W>
 void launch_merge_w(const SweepArgs &a, bool pcc, int n_reps, cudaStream_t st)
 {
